@@ -1,0 +1,417 @@
+#!/usr/bin/env python
+"""Throughput of the integer HyGT forward + inverse on GB300.
+
+One step = integer forward HyGT then integer inverse HyGT over every block
+of the workload (default: 8x8 blocks, N = 64, 2 rounds, 105 sets,
+4,194,304 Laplacian int16 blocks), inputs resident in HBM.  Prints one JSON
+line (rank 0).  ``--impl reference`` times the CPU oracle on a bounded
+sample of the same workload instead.
+
+Launch: ``python bench.py [--gpus N --steps K --warmup W]``; for N > 1 under
+``torch.distributed.run`` (one process per GPU, NCCL).  Blocks are
+independent, so every rank transforms its own full batch (weak scaling) and
+there is no collective on the data path; the barrier and the max-over-ranks
+reduction of the timed region are the only communication.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "HyGT blocks/s (fwd+inv, int32 bit-exact) & % HBM roofline vs dense-KLT on same GB300"
+DEFAULT_WORKLOAD = "hygt8x8_r2_s105"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the timed oracle sample (for profiling runs)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- distributed
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def shard_blocks(nblocks: int, rank: int, world: int, weak: bool = True):
+    """Blocks a rank transforms: the full batch under weak scaling, else a
+    contiguous 1/world share (remainder to the lowest ranks)."""
+    if weak:
+        return 0, nblocks
+    base, rem = divmod(nblocks, world)
+    start = rank * base + min(rank, rem)
+    return start, base + (1 if rank < rem else 0)
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+            os.unlink(self.path)
+        except OSError:
+            return None
+        if not rows:
+            return None
+
+        def num(s):
+            try:
+                return float(s)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        top = max(sm) if sm else 0
+        loaded = [s for s in sm if s >= 0.5 * top] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- helpers
+def gpu_smi_id(dev, local):
+    """nvidia-smi selector of this CUDA device: its UUID when torch exposes
+    it (nvidia-smi indices ignore CUDA_VISIBLE_DEVICES), else the index."""
+    try:
+        import torch
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(local)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2505_21728_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(os.path.basename(p).encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources (a line 'bench-traffic: kernel=... workload=...
+    sha=... bytes_per_launch=...' in profiles/*.md); else None."""
+    sha = kernel_source_sha()
+    for p in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        with open(p) as f:
+            for line in f:
+                if not line.startswith("bench-traffic:"):
+                    continue
+                kv = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
+                if kv.get("kernel") == kernel and kv.get("workload") == workload \
+                        and kv.get("sha") == sha:
+                    return int(float(kv["bytes_per_launch"]))
+    return None
+
+
+# ---------------------------------------------------------------- CPU oracle leg
+def oracle_sample(w, data, nblk):
+    """Times the oracle's integer forward + inverse on the first nblk blocks."""
+    import oracle
+    oracle.build()
+    x = data["x"][:nblk]
+    s = None if data["sets"] is None else data["sets"][:nblk]
+    t0 = time.perf_counter()
+    y, st1 = oracle.fwd_int(x, data["angle_idx"], w.log2n, w.rounds, data["perms"], s)
+    _, st2 = oracle.inv_int(y, data["angle_idx"], w.log2n, w.rounds, data["perms"], s)
+    dt = time.perf_counter() - t0
+    if st1 or st2:
+        raise RuntimeError("oracle reported status %d/%d" % (st1, st2))
+    return dt, oracle.num_threads()
+
+
+def cpu_baseline(w, data, target_s=10.0):
+    nblk = min(w.nblocks, 16384)
+    dt, cores = oracle_sample(w, data, nblk)
+    # grow the sample to about target_s of wall time
+    want = int(nblk * target_s / max(dt, 1e-3))
+    nblk2 = max(nblk, min(w.nblocks, want))
+    if nblk2 > nblk:
+        dt, cores = oracle_sample(w, data, nblk2)
+        nblk = nblk2
+    return {"value": nblk / dt, "unit": "blocks/s", "cores": cores, "kind": "oracle",
+            "sample": "integer forward + inverse of the first %d blocks of %s "
+                      "(C oracle, int64 arithmetic, OpenMP over blocks), %.1f s"
+                      % (nblk, w.name, dt)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2505_21728_gb300 import workloads
+    w = workloads.get(args.workload)
+    nblk = min(w.nblocks, 65536)
+    data = {"x": w.blocks(0, nblk), "sets": w.set_indices()[:nblk]}
+    data["angle_idx"], data["perms"] = w.params()
+    for _ in range(args.warmup):
+        oracle_sample(w, data, nblk)
+    times = []
+    cores = 1
+    for _ in range(args.steps):
+        dt, cores = oracle_sample(w, data, nblk)
+        times.append(dt)
+    total = sum(times)
+    value = nblk * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "blocks/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": w.name, "nblocks_per_step": nblk, "N": w.N, "rounds": w.rounds,
+                   "sets": w.num_sets},
+        "cpu_baseline": {"value": value, "unit": "blocks/s", "cores": cores, "kind": "oracle",
+                         "sample": "first %d blocks of %s per step" % (nblk, w.name)},
+        "e2e": {"value": value, "unit": "blocks/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU leg
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    from paper_2505_21728_gb300 import build
+    build.build()
+    from paper_2505_21728_gb300 import hygt, workloads
+
+    w = workloads.get(args.workload)
+    data = w.generate()
+    start, count = shard_blocks(w.nblocks, rank, world, weak=True)
+    x_np = data["x"][start:start + count]
+    s_np = data["sets"][start:start + count]
+    plan = hygt.Plan(w.log2n, w.rounds, data["angle_idx"], data["perms"])
+    N = w.N
+    d_x = torch.from_numpy(x_np).to(dev)
+    d_s = torch.from_numpy(s_np.view(np.int16)).to(dev)
+    d_y = torch.empty((count, N), dtype=torch.int32, device=dev)
+    d_xr = torch.empty((count, N), dtype=torch.int16, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.forward(d_x, d_s, out=d_y)
+        plan.inverse(d_y, d_s, out=d_xr)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    K = args.steps
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K + 1)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(gpu_smi_id(dev, local))
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t_start.record(stream)
+    ev[0].record(stream)
+    for k in range(K):
+        plan.forward(d_x, d_s, out=d_y)
+        ev[2 * k + 1].record(stream)
+        plan.inverse(d_y, d_s, out=d_xr)
+        ev[2 * k + 2].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clock_info = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    fwd_ms = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(K)]
+    inv_ms = [ev[2 * k + 1].elapsed_time(ev[2 * k + 2]) for k in range(K)]
+    total_ms = max_over_ranks(total_ms, world, dev)
+
+    blocks_total = count * world * K
+    value = blocks_total / (total_ms / 1000.0)
+
+    # roofline of the dominant kernel (algorithmic bytes / average duration)
+    bytes_per_launch = count * (2 * N + 4 * N + 2)  # same for forward and inverse
+    f_avg, i_avg = statistics.mean(fwd_ms), statistics.mean(inv_ms)
+    dom_name, dom_ms = ("hygt_int_forward", f_avg) if f_avg >= i_avg else ("hygt_int_inverse", i_avg)
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_per_launch / (dom_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": ncu_traffic(dom_name, w.name),
+                "kernel": dom_name, "peak_source": peak_kind,
+                "fwd_ms": f_avg, "inv_ms": i_avg,
+                "bytes_per_launch": bytes_per_launch}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": world,
+        "steps": K, "warmup": max(3, args.warmup), "ms_per_step": total_ms / K,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": w.name, "nblocks": count, "N": N, "rounds": w.rounds,
+                   "sets": w.num_sets, "parallelism": "dp%d" % world,
+                   "l2": "inputs larger than L2 (%.0f MB read + %.0f MB written per step "
+                         "vs %d MB L2), no flush" % (count * 6 * N / 1e6, count * 6 * N / 1e6,
+                                                     L2_BYTES >> 20),
+                   "description": w.description},
+        "roofline": roofline,
+        "gpu_launches": 2 * K,
+        "clocks": clock_info,
+    }
+
+    if not args.no_e2e:
+        line["e2e"] = e2e_leg(plan, x_np, s_np, N, dev, stream, world)
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, data)
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def e2e_leg(plan, x_np, s_np, N, dev, stream, world, steps=5):
+    """Same metric through the public API with host buffers: every step
+    copies the blocks and set indices host->device (pinned), runs forward and
+    inverse, and copies the coefficients and reconstructed blocks back."""
+    import numpy as np
+    import torch
+    count = x_np.shape[0]
+    h_x = torch.from_numpy(x_np).pin_memory()
+    h_s = torch.from_numpy(s_np.view(np.int16)).pin_memory()
+    h_y = torch.empty((count, N), dtype=torch.int32).pin_memory()
+    h_xr = torch.empty((count, N), dtype=torch.int16).pin_memory()
+    d_x = torch.empty((count, N), dtype=torch.int16, device=dev)
+    d_s = torch.empty((count,), dtype=torch.int16, device=dev)
+    d_y = torch.empty((count, N), dtype=torch.int32, device=dev)
+    d_xr = torch.empty((count, N), dtype=torch.int16, device=dev)
+
+    def step():
+        d_x.copy_(h_x, non_blocking=True)
+        d_s.copy_(h_s, non_blocking=True)
+        plan.forward(d_x, d_s, out=d_y)
+        plan.inverse(d_y, d_s, out=d_xr)
+        h_y.copy_(d_y, non_blocking=True)
+        h_xr.copy_(d_xr, non_blocking=True)
+
+    step()
+    torch.cuda.synchronize(dev)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    a.record(stream)
+    for _ in range(steps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = max_over_ranks(a.elapsed_time(b), world, dev)
+    return {"value": count * world * steps / (ms / 1000.0), "unit": "blocks/s",
+            "h2d_bytes_per_step": count * (2 * N + 2), "d2h_bytes_per_step": count * 6 * N,
+            "steps": steps}
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,155 @@
+/*
+ * hygt.h -- C ABI of libhygt.so, the GB300 (sm_103a) implementation of the
+ * Hypercube-Givens Transform (HyGT) of Said et al., "Highly Efficient
+ * Non-Separable Transforms for Next Generation Video Coding".
+ *
+ * Definitions (Sec. II-IV of the paper):
+ *   - A block is a vector of N = 2^log2n residual values (Sec. II: the
+ *     residual vector r; a 4x4 block is N = 16, an 8x8 block N = 64, a 16x16
+ *     block N = 256), stored contiguously in raster order.
+ *   - Each block carries a transform-set index (Sec. II: the classification
+ *     index c, sent as side information; Sec. VI: 35 intra modes x 3
+ *     candidates = 105 sets per block size, or no secondary transform).
+ *     HYGT_SKIP_SET selects "no transform" (identity).
+ *   - A set is R rounds (Sec. IV, Fig. 2).  Round r is log2n passes; pass p
+ *     rotates every pair (m, n = m + 2^p), m with bit p clear, numbered
+ *     j = 0..N/2-1 by increasing m (Sec. IV, Fig. 3 and Fig. 4), by its own
+ *     angle theta[set][r][p][j] (R N log2(N) / 2 angles per set, Sec. IV):
+ *     (a, b) -> (cos*a + sin*b, -sin*a + cos*b) (Givens matrix, Sec. IV).
+ *   - After round r an optional permutation slot gathers v'[i] = v[perm[r][i]]
+ *     (the optional sorting pass of Fig. 2, allowed after every round).
+ *   - The inverse applies the passes in reverse order with negated angles
+ *     and undoes each permutation (Sec. III inverse product; Sec. IV).
+ *   - Integer path (Sec. IV, Fig. 5, "on-the-fly conversion" and the
+ *     integer-arithmetic requirement): an angle index q of angle_bits bits
+ *     stands for theta = 2*pi*q / 2^angle_bits and is converted to the
+ *     multipliers c = round(2^f cos theta), s = round(2^f sin theta),
+ *     f = frac_bits; every butterfly output is rounded half up,
+ *     floor((c*a + s*b + 2^(f-1)) / 2^f), in int32.  The inverse uses (c, -s).
+ *
+ * Conventions:
+ *   - Device pointers (prefix d_) are global-memory pointers on the current
+ *     device, owned by the caller, 16-byte aligned; otherwise HYGT_ERR_ARG.
+ *     Host pointers (prefix h_) are read during the call only.
+ *   - Compute calls are asynchronous on `stream` (NULL = legacy default
+ *     stream).  Argument errors are returned synchronously, before any
+ *     launch; a launch failure returns HYGT_ERR_CUDA.
+ *   - d_status (nullable) is a device int the caller zero-initialises.  A
+ *     condition detected on the device (a set index >= num_sets that is not
+ *     HYGT_SKIP_SET) writes its hygt_status code there (first error wins)
+ *     and that block's output is all zeros.  Kernels never trap or abort.
+ *   - A plan owns its device tables until hygt_destroy.  A plan may be used
+ *     from several streams at once; it is never modified by compute calls.
+ */
+#ifndef HYGT_H
+#define HYGT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st *hygt_stream;
+
+/* Opaque plan: one block size, one round count, num_sets parameter sets. */
+typedef struct hygt_plan_s *hygt_plan;
+
+typedef enum hygt_status {
+  HYGT_OK = 0,
+  HYGT_ERR_ARG = 1,         /* bad argument (shape, pointer, alignment, permutation) */
+  HYGT_ERR_CUDA = 2,        /* a CUDA runtime call or launch failed */
+  HYGT_ERR_OOM = 3,         /* device allocation failed */
+  HYGT_ERR_SET_INDEX = 4,   /* device: set index >= num_sets and != HYGT_SKIP_SET */
+  HYGT_ERR_UNSUPPORTED = 6  /* plan kind does not support this call */
+} hygt_status;
+
+#define HYGT_SKIP_SET 0xFFFFu
+#define HYGT_MAX_LOG2N 8
+#define HYGT_MAX_ROUNDS 8
+
+/*
+ * Build a plan for the integer path (Sec. IV, Fig. 5) and the FP32 path on
+ * the same angles.
+ *   log2n       1..8 (N = 2..256).
+ *   rounds      1..8.
+ *   num_sets    1..65535.
+ *   h_angle_idx host uint8 [num_sets][rounds][log2n][N/2]: angle indices q,
+ *               each < 2^angle_bits (one byte per parameter, Sec. IV).
+ *   h_perms     host uint16 [num_sets][rounds][N] gather permutations (slot r
+ *               applied after round r), or NULL for none.  Each slot must be
+ *               a permutation of 0..N-1.
+ *   angle_bits  1..8.   frac_bits 1..10.
+ * The FP32 path of this plan uses cos/sin of theta = 2*pi*q / 2^angle_bits,
+ * evaluated in FP64 on the host and rounded to FP32.
+ * Allocates the plan's device tables on the current device (synchronous).
+ */
+hygt_status hygt_create(hygt_plan *out, int log2n, int rounds, int num_sets,
+                        const uint8_t *h_angle_idx, const uint16_t *h_perms,
+                        int angle_bits, int frac_bits);
+
+/*
+ * Build a plan for the FP32 path with free angles (the parametrisation
+ * optimised in Sec. V).  h_theta is host float [num_sets][rounds][log2n][N/2]
+ * in radians; h_perms as for hygt_create.  Integer calls on such a plan
+ * return HYGT_ERR_UNSUPPORTED.
+ */
+hygt_status hygt_create_float(hygt_plan *out, int log2n, int rounds, int num_sets,
+                              const float *h_theta, const uint16_t *h_perms);
+
+/* Release the plan's device tables (synchronises the device). NULL is a no-op. */
+void hygt_destroy(hygt_plan plan);
+
+/*
+ * Integer forward HyGT (Sec. IV): d_x int16 [nblocks][N] -> d_y int32
+ * [nblocks][N].  d_set: uint16 [nblocks] set indices, or NULL for set 0 on
+ * every block.  A block with HYGT_SKIP_SET is copied (widened).
+ * For every int16 input the int32 intermediates cannot overflow.
+ */
+hygt_status hygt_forward(hygt_plan plan, const int16_t *d_x, int32_t *d_y,
+                         const uint16_t *d_set, int64_t nblocks, hygt_stream stream,
+                         int *d_status);
+
+/*
+ * Integer inverse HyGT (Sec. III inverse product, Sec. IV negative angles):
+ * d_y int32 [nblocks][N] -> d_x int16 [nblocks][N], saturated to
+ * [-32768, 32767].  A block with HYGT_SKIP_SET is narrowed with saturation.
+ * Precondition: each block's L2 norm is at most 2^21, which holds for every
+ * output of hygt_forward on int16 input; beyond it int32 arithmetic may wrap
+ * (the call still completes, without a fault).
+ */
+hygt_status hygt_inverse(hygt_plan plan, const int32_t *d_y, int16_t *d_x,
+                         const uint16_t *d_set, int64_t nblocks, hygt_stream stream,
+                         int *d_status);
+
+/* FP32 forward / inverse HyGT: float [nblocks][N] -> float [nblocks][N]
+   (no rounding between passes).  Set handling as for the integer calls. */
+hygt_status hygt_forward_f32(hygt_plan plan, const float *d_x, float *d_y,
+                             const uint16_t *d_set, int64_t nblocks, hygt_stream stream,
+                             int *d_status);
+hygt_status hygt_inverse_f32(hygt_plan plan, const float *d_y, float *d_x,
+                             const uint16_t *d_set, int64_t nblocks, hygt_stream stream,
+                             int *d_status);
+
+/* Plan shape: any out-pointer may be NULL. */
+hygt_status hygt_plan_info(hygt_plan plan, int *log2n, int *rounds, int *num_sets,
+                           int *is_float);
+
+/*
+ * Bytes of transform parameters at one byte per angle (Sec. IV: R N log2(N)/2
+ * angles per set; "one byte per parameter"), for num_sets sets.
+ * Returns 0 for out-of-range arguments.  Host only.
+ */
+size_t hygt_param_bytes(int log2n, int rounds, int num_sets);
+
+/* Static English text for a status code. */
+const char *hygt_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYGT_H */

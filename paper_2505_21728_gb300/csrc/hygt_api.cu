@@ -1,0 +1,318 @@
+// hygt_api.cu -- C ABI of libhygt.so: plan builder (host) and launch entry
+// points.  See include/hygt.h for the contract of every call.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/hygt.h"
+#include "hygt_launch.cuh"
+
+struct hygt_plan_s {
+  int log2n = 0, rounds = 0, num_sets = 0;
+  int angle_bits = 0, frac_bits = 0;
+  int is_float = 0;  // 1: free FP32 angles only (no integer tables)
+  int device = 0;
+  void* d_tab_int = nullptr;  // uint32 (c | s << 16) per pair
+  size_t tab_int_bytes = 0;   // padded to 16
+  void* d_tab_f32 = nullptr;  // float2 (cos, sin) per pair
+  size_t tab_f32_bytes = 0;
+  uint8_t* d_perm = nullptr;  // uint8 [S][R][N]
+  size_t perm_bytes = 0;
+  unsigned perm_mask = 0;
+};
+
+namespace hygt {
+
+DeviceInfo device_info(int device) {
+  static std::mutex mu;
+  static std::vector<DeviceInfo> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  if ((int)cache.size() <= device) cache.resize(device + 1);
+  DeviceInfo& d = cache[device];
+  if (d.sms == 0) {
+    cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, device);
+    cudaDeviceGetAttribute(&d.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (d.sms <= 0) d.sms = 1;
+  }
+  return d;
+}
+
+}  // namespace hygt
+
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+size_t pad16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+void free_plan(hygt_plan p) {
+  if (!p) return;
+  if (p->d_tab_int) cudaFree(p->d_tab_int);
+  if (p->d_tab_f32) cudaFree(p->d_tab_f32);
+  if (p->d_perm) cudaFree(p->d_perm);
+  delete p;
+}
+
+hygt_status upload(void** dst, const void* src, size_t bytes, size_t padded) {
+  if (cudaMalloc(dst, padded) != cudaSuccess) {
+    *dst = nullptr;
+    cudaGetLastError();
+    return HYGT_ERR_OOM;
+  }
+  if (padded > bytes && cudaMemset(*dst, 0, padded) != cudaSuccess) return HYGT_ERR_CUDA;
+  if (cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return HYGT_ERR_CUDA;
+  return HYGT_OK;
+}
+
+bool shape_ok(int log2n, int rounds, int num_sets) {
+  return log2n >= 1 && log2n <= HYGT_MAX_LOG2N && rounds >= 1 && rounds <= HYGT_MAX_ROUNDS &&
+         num_sets >= 1 && num_sets <= 65535;
+}
+
+// Validates the permutation slots (each a permutation of 0..N-1) and
+// narrows them to uint8; identity slots are left out of *mask so the
+// kernels skip them.  Host only: no CUDA call.
+hygt_status check_perms(int log2n, int rounds, int num_sets, const uint16_t* h_perms,
+                        std::vector<uint8_t>* out, unsigned* mask) {
+  *mask = 0;
+  if (!h_perms) return HYGT_OK;
+  const int N = 1 << log2n;
+  const size_t count = (size_t)num_sets * rounds * N;
+  out->assign(count, 0);
+  std::vector<int> seen(N);
+  for (int s = 0; s < num_sets; ++s) {
+    for (int r = 0; r < rounds; ++r) {
+      const uint16_t* src = h_perms + ((size_t)s * rounds + r) * N;
+      std::fill(seen.begin(), seen.end(), 0);
+      bool identity = true;
+      for (int i = 0; i < N; ++i) {
+        if (src[i] >= N || seen[src[i]]) return HYGT_ERR_ARG;
+        seen[src[i]] = 1;
+        if (src[i] != i) identity = false;
+        (*out)[((size_t)s * rounds + r) * N + i] = (uint8_t)src[i];
+      }
+      if (!identity) *mask |= 1u << r;
+    }
+  }
+  return HYGT_OK;
+}
+
+hygt_status upload_perms(hygt_plan p, const std::vector<uint8_t>& perm, unsigned mask) {
+  p->perm_mask = mask;
+  if (!mask) return HYGT_OK;
+  p->perm_bytes = pad16(perm.size());
+  return upload(reinterpret_cast<void**>(&p->d_perm), perm.data(), perm.size(), p->perm_bytes);
+}
+
+hygt_status check_io(hygt_plan plan, const void* in, const void* out, int64_t nblocks) {
+  if (!plan || nblocks < 0) return HYGT_ERR_ARG;
+  if (nblocks == 0) return HYGT_OK;
+  if (!in || !out || !aligned16(in) || !aligned16(out)) return HYGT_ERR_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HYGT_ERR_CUDA;
+  if (dev != plan->device) return HYGT_ERR_ARG;
+  return HYGT_OK;
+}
+
+hygt::Params base_params(hygt_plan plan, const void* in, void* out, const uint16_t* d_set,
+                         int64_t nblocks, int* d_status, bool fp) {
+  hygt::Params p{};
+  p.in = in;
+  p.out = out;
+  p.set = d_set;
+  p.nblocks = nblocks;
+  p.tab = fp ? plan->d_tab_f32 : plan->d_tab_int;
+  const size_t tb = fp ? plan->tab_f32_bytes : plan->tab_int_bytes;
+  p.tab_bytes = tb > (size_t)INT32_MAX ? 0 : (int)tb;  // 0: never staged
+  p.perm = plan->d_perm;
+  p.perm_bytes = (int)plan->perm_bytes;
+  p.perm_mask = plan->perm_mask;
+  p.rounds = plan->rounds;
+  p.num_sets = plan->num_sets;
+  p.frac_bits = plan->frac_bits;
+  p.status = d_status;
+  return p;
+}
+
+hygt_status to_status(cudaError_t e) {
+  if (e == cudaSuccess) return HYGT_OK;
+  if (e == cudaErrorMemoryAllocation) return HYGT_ERR_OOM;
+  return HYGT_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+hygt_status hygt_create(hygt_plan* out, int log2n, int rounds, int num_sets,
+                        const uint8_t* h_angle_idx, const uint16_t* h_perms, int angle_bits,
+                        int frac_bits) {
+  if (!out) return HYGT_ERR_ARG;
+  *out = nullptr;
+  if (!shape_ok(log2n, rounds, num_sets) || !h_angle_idx) return HYGT_ERR_ARG;
+  if (angle_bits < 1 || angle_bits > 8 || frac_bits < 1 || frac_bits > 10) return HYGT_ERR_ARG;
+  const int N = 1 << log2n;
+  const size_t pairs = (size_t)num_sets * rounds * log2n * (N / 2);
+  const int nq = 1 << angle_bits;
+  for (size_t i = 0; i < pairs; ++i)
+    if (h_angle_idx[i] >= nq) return HYGT_ERR_ARG;
+  std::vector<uint8_t> perm;
+  unsigned mask = 0;
+  if (check_perms(log2n, rounds, num_sets, h_perms, &perm, &mask) != HYGT_OK) return HYGT_ERR_ARG;
+
+  // Multiplier table of the on-the-fly conversion: c, s = round(2^f cos/sin).
+  std::vector<int> ct(nq), st(nq);
+  std::vector<float> cf(nq), sf(nq);
+  const double scale = std::ldexp(1.0, frac_bits);
+  for (int q = 0; q < nq; ++q) {
+    const double th = kTwoPi * (double)q / (double)nq;
+    ct[q] = (int)std::lround(scale * std::cos(th));
+    st[q] = (int)std::lround(scale * std::sin(th));
+    cf[q] = (float)std::cos(th);
+    sf[q] = (float)std::sin(th);
+  }
+  std::vector<uint32_t> ti(pairs);
+  std::vector<float> tf(2 * pairs);
+  for (size_t i = 0; i < pairs; ++i) {
+    const int q = h_angle_idx[i];
+    ti[i] = ((uint32_t)ct[q] & 0xffffu) | ((uint32_t)st[q] << 16);
+    tf[2 * i] = cf[q];
+    tf[2 * i + 1] = sf[q];
+  }
+
+  hygt_plan p = new (std::nothrow) hygt_plan_s();
+  if (!p) return HYGT_ERR_OOM;
+  p->log2n = log2n;
+  p->rounds = rounds;
+  p->num_sets = num_sets;
+  p->angle_bits = angle_bits;
+  p->frac_bits = frac_bits;
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    delete p;
+    return HYGT_ERR_CUDA;
+  }
+  hygt_status s = HYGT_OK;
+  p->tab_int_bytes = pad16(pairs * 4);
+  s = upload(&p->d_tab_int, ti.data(), pairs * 4, p->tab_int_bytes);
+  if (s == HYGT_OK) {
+    p->tab_f32_bytes = pad16(pairs * 8);
+    s = upload(&p->d_tab_f32, tf.data(), pairs * 8, p->tab_f32_bytes);
+  }
+  if (s == HYGT_OK) s = upload_perms(p, perm, mask);
+  if (s != HYGT_OK) {
+    free_plan(p);
+    return s;
+  }
+  *out = p;
+  return HYGT_OK;
+}
+
+hygt_status hygt_create_float(hygt_plan* out, int log2n, int rounds, int num_sets,
+                              const float* h_theta, const uint16_t* h_perms) {
+  if (!out) return HYGT_ERR_ARG;
+  *out = nullptr;
+  if (!shape_ok(log2n, rounds, num_sets) || !h_theta) return HYGT_ERR_ARG;
+  const int N = 1 << log2n;
+  const size_t pairs = (size_t)num_sets * rounds * log2n * (N / 2);
+  std::vector<float> tf(2 * pairs);
+  for (size_t i = 0; i < pairs; ++i) {
+    const double th = (double)h_theta[i];
+    if (!std::isfinite(th)) return HYGT_ERR_ARG;
+    tf[2 * i] = (float)std::cos(th);
+    tf[2 * i + 1] = (float)std::sin(th);
+  }
+  std::vector<uint8_t> perm;
+  unsigned mask = 0;
+  if (check_perms(log2n, rounds, num_sets, h_perms, &perm, &mask) != HYGT_OK) return HYGT_ERR_ARG;
+  hygt_plan p = new (std::nothrow) hygt_plan_s();
+  if (!p) return HYGT_ERR_OOM;
+  p->log2n = log2n;
+  p->rounds = rounds;
+  p->num_sets = num_sets;
+  p->is_float = 1;
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    delete p;
+    return HYGT_ERR_CUDA;
+  }
+  p->tab_f32_bytes = pad16(pairs * 8);
+  hygt_status s = upload(&p->d_tab_f32, tf.data(), pairs * 8, p->tab_f32_bytes);
+  if (s == HYGT_OK) s = upload_perms(p, perm, mask);
+  if (s != HYGT_OK) {
+    free_plan(p);
+    return s;
+  }
+  *out = p;
+  return HYGT_OK;
+}
+
+void hygt_destroy(hygt_plan plan) { free_plan(plan); }
+
+hygt_status hygt_forward(hygt_plan plan, const int16_t* d_x, int32_t* d_y, const uint16_t* d_set,
+                         int64_t nblocks, hygt_stream stream, int* d_status) {
+  hygt_status s = check_io(plan, d_x, d_y, nblocks);
+  if (s != HYGT_OK || nblocks == 0) return s;
+  if (plan->is_float) return HYGT_ERR_UNSUPPORTED;
+  hygt::Params p = base_params(plan, d_x, d_y, d_set, nblocks, d_status, false);
+  return to_status(hygt::launch_int_fwd(plan->log2n, p, (cudaStream_t)stream));
+}
+
+hygt_status hygt_inverse(hygt_plan plan, const int32_t* d_y, int16_t* d_x, const uint16_t* d_set,
+                         int64_t nblocks, hygt_stream stream, int* d_status) {
+  hygt_status s = check_io(plan, d_y, d_x, nblocks);
+  if (s != HYGT_OK || nblocks == 0) return s;
+  if (plan->is_float) return HYGT_ERR_UNSUPPORTED;
+  hygt::Params p = base_params(plan, d_y, d_x, d_set, nblocks, d_status, false);
+  return to_status(hygt::launch_int_inv(plan->log2n, p, (cudaStream_t)stream));
+}
+
+hygt_status hygt_forward_f32(hygt_plan plan, const float* d_x, float* d_y, const uint16_t* d_set,
+                             int64_t nblocks, hygt_stream stream, int* d_status) {
+  hygt_status s = check_io(plan, d_x, d_y, nblocks);
+  if (s != HYGT_OK || nblocks == 0) return s;
+  hygt::Params p = base_params(plan, d_x, d_y, d_set, nblocks, d_status, true);
+  return to_status(hygt::launch_f32_fwd(plan->log2n, p, (cudaStream_t)stream));
+}
+
+hygt_status hygt_inverse_f32(hygt_plan plan, const float* d_y, float* d_x, const uint16_t* d_set,
+                             int64_t nblocks, hygt_stream stream, int* d_status) {
+  hygt_status s = check_io(plan, d_y, d_x, nblocks);
+  if (s != HYGT_OK || nblocks == 0) return s;
+  hygt::Params p = base_params(plan, d_y, d_x, d_set, nblocks, d_status, true);
+  return to_status(hygt::launch_f32_inv(plan->log2n, p, (cudaStream_t)stream));
+}
+
+hygt_status hygt_plan_info(hygt_plan plan, int* log2n, int* rounds, int* num_sets, int* is_float) {
+  if (!plan) return HYGT_ERR_ARG;
+  if (log2n) *log2n = plan->log2n;
+  if (rounds) *rounds = plan->rounds;
+  if (num_sets) *num_sets = plan->num_sets;
+  if (is_float) *is_float = plan->is_float;
+  return HYGT_OK;
+}
+
+size_t hygt_param_bytes(int log2n, int rounds, int num_sets) {
+  if (log2n < 1 || log2n > 16 || rounds < 1 || num_sets < 1) return 0;
+  const size_t N = (size_t)1 << log2n;
+  return (size_t)num_sets * (size_t)rounds * N * (size_t)log2n / 2;
+}
+
+const char* hygt_status_string(int status) {
+  switch (status) {
+    case HYGT_OK: return "ok";
+    case HYGT_ERR_ARG: return "invalid argument";
+    case HYGT_ERR_CUDA: return "CUDA runtime error";
+    case HYGT_ERR_OOM: return "device allocation failed";
+    case HYGT_ERR_SET_INDEX: return "set index out of range";
+    case HYGT_ERR_UNSUPPORTED: return "operation not supported by this plan";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,234 @@
+"""Thin Python binding of libhygt.so (argument marshalling only).
+
+The functions named ``hygt_*`` mirror the C ABI in ``include/hygt.h`` one to
+one and take raw device pointers (ints) and a CUDA stream handle.  ``Plan``
+wraps a plan handle and accepts torch CUDA tensors: it checks dtypes,
+shapes and devices, then passes ``data_ptr()`` and the current stream to the
+C entry point.  Every step of the transform runs in the CUDA kernels of the
+library; there is no other implementation behind this module.  Importing it
+raises if the library has not been built for this machine.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import SO
+
+HYGT_OK = 0
+HYGT_ERR_ARG = 1
+HYGT_ERR_CUDA = 2
+HYGT_ERR_OOM = 3
+HYGT_ERR_SET_INDEX = 4
+HYGT_ERR_UNSUPPORTED = 6
+HYGT_SKIP_SET = 0xFFFF
+
+
+class HygtError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__("%s: %s (status %d)" % (where, hygt_status_string(code), code))
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(SO):
+        raise ImportError("libhygt.so is not built (%s); run "
+                          "paper_2505_21728_gb300.build.build() first" % SO)
+    L = ctypes.CDLL(SO)
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    L.hygt_create.argtypes = [ctypes.POINTER(P), i32, i32, i32, P, P, i32, i32]
+    L.hygt_create.restype = i32
+    L.hygt_create_float.argtypes = [ctypes.POINTER(P), i32, i32, i32, P, P]
+    L.hygt_create_float.restype = i32
+    L.hygt_destroy.argtypes = [P]
+    L.hygt_destroy.restype = None
+    for name in ("hygt_forward", "hygt_inverse", "hygt_forward_f32", "hygt_inverse_f32"):
+        f = getattr(L, name)
+        f.argtypes = [P, P, P, P, i64, P, P]
+        f.restype = i32
+    L.hygt_plan_info.argtypes = [P] + [ctypes.POINTER(i32)] * 4
+    L.hygt_plan_info.restype = i32
+    L.hygt_param_bytes.argtypes = [i32, i32, i32]
+    L.hygt_param_bytes.restype = ctypes.c_size_t
+    L.hygt_status_string.argtypes = [i32]
+    L.hygt_status_string.restype = ctypes.c_char_p
+    return L
+
+
+_lib = _load()
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(code: int, where: str) -> None:
+    if code != HYGT_OK:
+        raise HygtError(code, where)
+
+
+# ---------------------------------------------------------------- C ABI, 1:1
+def hygt_status_string(code: int) -> str:
+    return _lib.hygt_status_string(int(code)).decode()
+
+
+def hygt_param_bytes(log2n: int, rounds: int, num_sets: int) -> int:
+    return int(_lib.hygt_param_bytes(log2n, rounds, num_sets))
+
+
+def hygt_create(log2n, rounds, num_sets, angle_idx, perms=None, angle_bits=8, frac_bits=8):
+    """Returns (status, plan handle); angle_idx uint8, perms uint16 or None."""
+    a = np.ascontiguousarray(angle_idx, dtype=np.uint8)
+    p = None if perms is None else np.ascontiguousarray(perms, dtype=np.uint16)
+    h = ctypes.c_void_p()
+    st = _lib.hygt_create(ctypes.byref(h), log2n, rounds, num_sets, _np_ptr(a), _np_ptr(p),
+                          angle_bits, frac_bits)
+    return int(st), h.value
+
+
+def hygt_create_float(log2n, rounds, num_sets, theta, perms=None):
+    t = np.ascontiguousarray(theta, dtype=np.float32)
+    p = None if perms is None else np.ascontiguousarray(perms, dtype=np.uint16)
+    h = ctypes.c_void_p()
+    st = _lib.hygt_create_float(ctypes.byref(h), log2n, rounds, num_sets, _np_ptr(t), _np_ptr(p))
+    return int(st), h.value
+
+
+def hygt_destroy(plan) -> None:
+    _lib.hygt_destroy(plan)
+
+
+def hygt_forward(plan, d_x, d_y, d_set, nblocks, stream, d_status):
+    return int(_lib.hygt_forward(plan, d_x, d_y, d_set, nblocks, stream, d_status))
+
+
+def hygt_inverse(plan, d_y, d_x, d_set, nblocks, stream, d_status):
+    return int(_lib.hygt_inverse(plan, d_y, d_x, d_set, nblocks, stream, d_status))
+
+
+def hygt_forward_f32(plan, d_x, d_y, d_set, nblocks, stream, d_status):
+    return int(_lib.hygt_forward_f32(plan, d_x, d_y, d_set, nblocks, stream, d_status))
+
+
+def hygt_inverse_f32(plan, d_y, d_x, d_set, nblocks, stream, d_status):
+    return int(_lib.hygt_inverse_f32(plan, d_y, d_x, d_set, nblocks, stream, d_status))
+
+
+def hygt_plan_info(plan):
+    vals = [ctypes.c_int() for _ in range(4)]
+    _check(_lib.hygt_plan_info(plan, *[ctypes.byref(v) for v in vals]), "hygt_plan_info")
+    return tuple(v.value for v in vals)
+
+
+# ---------------------------------------------------------------- torch wrapper
+def _stream_handle(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def _dptr(t, dtype, shape_last=None, name="tensor"):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if shape_last is not None and (t.dim() != 2 or t.shape[1] != shape_last):
+        raise ValueError("%s must have shape [nblocks, %d]" % (name, shape_last))
+    return t.data_ptr()
+
+
+class Plan:
+    """A transform plan on the current CUDA device.
+
+    ``Plan(log2n, rounds, angle_idx, perms)`` builds an integer plan (its
+    FP32 calls use the same angles); ``Plan.from_theta(...)`` builds an FP32
+    plan with free angles.
+    """
+
+    def __init__(self, log2n, rounds, angle_idx=None, perms=None, angle_bits=8, frac_bits=8,
+                 _handle=None, _num_sets=None):
+        self.log2n = int(log2n)
+        self.rounds = int(rounds)
+        self.N = 1 << self.log2n
+        if _handle is not None:
+            self.handle = _handle
+            self.num_sets = _num_sets
+            return
+        a = np.ascontiguousarray(angle_idx, dtype=np.uint8)
+        self.num_sets = a.size // (self.rounds * self.log2n * (self.N // 2))
+        st, h = hygt_create(self.log2n, self.rounds, self.num_sets, a, perms, angle_bits, frac_bits)
+        _check(st, "hygt_create")
+        self.handle = h
+
+    @classmethod
+    def from_theta(cls, log2n, rounds, theta, perms=None):
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        N = 1 << log2n
+        S = t.size // (rounds * log2n * (N // 2))
+        st, h = hygt_create_float(log2n, rounds, S, t, perms)
+        _check(st, "hygt_create_float")
+        return cls(log2n, rounds, _handle=h, _num_sets=S)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            hygt_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _call(self, fn, name, x, out, sets, in_dtype, out_dtype, status, stream):
+        import torch
+        nb = x.shape[0] if x.dim() == 2 else 0
+        px = _dptr(x, in_dtype, self.N, "input")
+        po = _dptr(out, out_dtype, self.N, "output")
+        if out.shape[0] != nb:
+            raise ValueError("output has %d blocks, input %d" % (out.shape[0], nb))
+        ps = None
+        if sets is not None:
+            ps = _dptr(sets, torch.int16 if sets.dtype == torch.int16 else torch.uint16, None, "sets")
+            if sets.numel() != nb:
+                raise ValueError("sets must have one entry per block")
+        pst = None if status is None else _dptr(status, torch.int32, None, "status")
+        _check(fn(self.handle, px, po, ps, nb, _stream_handle(stream), pst), name)
+        return out
+
+    def forward(self, x, sets=None, out=None, status=None, stream=None):
+        """int16 [B, N] -> int32 [B, N] (integer HyGT)."""
+        import torch
+        if out is None:
+            out = torch.empty(x.shape, dtype=torch.int32, device=x.device)
+        return self._call(hygt_forward, "hygt_forward", x, out, sets, torch.int16, torch.int32,
+                          status, stream)
+
+    def inverse(self, y, sets=None, out=None, status=None, stream=None):
+        """int32 [B, N] -> int16 [B, N] (integer inverse HyGT, saturated)."""
+        import torch
+        if out is None:
+            out = torch.empty(y.shape, dtype=torch.int16, device=y.device)
+        return self._call(hygt_inverse, "hygt_inverse", y, out, sets, torch.int32, torch.int16,
+                          status, stream)
+
+    def forward_f32(self, x, sets=None, out=None, status=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+        return self._call(hygt_forward_f32, "hygt_forward_f32", x, out, sets, torch.float32,
+                          torch.float32, status, stream)
+
+    def inverse_f32(self, y, sets=None, out=None, status=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(y.shape, dtype=torch.float32, device=y.device)
+        return self._call(hygt_inverse_f32, "hygt_inverse_f32", y, out, sets, torch.float32,
+                          torch.float32, status, stream)

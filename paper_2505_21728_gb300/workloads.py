@@ -1,0 +1,87 @@
+"""Named synthetic workloads shaped like the paper's transform settings.
+
+Block sizes follow Sec. VI (4x4 and 8x8 secondary transforms, 35 intra
+modes x 3 candidates = 105 sets); the 16x16 size extends the same
+construction.  Residuals are Laplacian int16 values (the shape of
+prediction residuals), drawn by ``inputs`` with fixed seeds.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import inputs
+
+
+@dataclass
+class Workload:
+    name: str
+    log2n: int
+    rounds: int
+    num_sets: int
+    nblocks: int
+    scale: float
+    clip: tuple
+    seed: int = 0
+    skip_frac: float = 0.0
+    description: str = ""
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def N(self) -> int:
+        return 1 << self.log2n
+
+    def params(self):
+        q = inputs.angle_indices(self.num_sets, self.rounds, self.log2n, seed=self.seed)
+        perms = inputs.permutations(self.num_sets, self.rounds, self.N, seed=self.seed)
+        return q, perms
+
+    def blocks(self, first: int = 0, count: int | None = None) -> np.ndarray:
+        return inputs.laplacian_blocks(self.nblocks, self.N, self.scale, self.clip[0],
+                                       self.clip[1], seed=self.seed, first_block=first,
+                                       count=count)
+
+    def set_indices(self) -> np.ndarray | None:
+        if self.num_sets == 1 and self.skip_frac == 0:
+            return np.zeros(self.nblocks, np.uint16)
+        return inputs.set_indices(self.nblocks, self.num_sets, seed=self.seed,
+                                  skip_frac=self.skip_frac)
+
+    def generate(self) -> dict:
+        q, perms = self.params()
+        return {"angle_idx": q, "perms": perms, "x": self.blocks(), "sets": self.set_indices()}
+
+    def bytes_fwd_inv(self) -> int:
+        """Algorithmic HBM bytes of one forward + inverse: int16 in and int32
+        out, then int32 in and int16 out, plus the 2-byte set index read in
+        each direction."""
+        return self.nblocks * (2 * self.N + 4 * self.N + 2) * 2
+
+
+_REGISTRY = {
+    "hygt4x4_r2": Workload(
+        "hygt4x4_r2", log2n=4, rounds=2, num_sets=1, nblocks=65536, scale=12.0,
+        clip=(-512, 511), seed=0,
+        description="4x4 non-separable HyGT (N=16), 2 rounds, one set, 65,536 Laplace(12) "
+                    "int16 blocks clipped to [-512, 511]"),
+    "hygt8x8_r2_s105": Workload(
+        "hygt8x8_r2_s105", log2n=6, rounds=2, num_sets=105, nblocks=4194304, scale=8.0,
+        clip=(-1024, 1023), seed=0,
+        description="8x8 non-separable HyGT (N=64), 2 rounds, 105 sets (35 modes x 3), "
+                    "4,194,304 Laplace(8) int16 blocks clipped to [-1024, 1023], set index "
+                    "uniform over 0..104"),
+    "hygt16x16_r3_s16": Workload(
+        "hygt16x16_r3_s16", log2n=8, rounds=3, num_sets=16, nblocks=16777216, scale=4.0,
+        clip=(-2048, 2047), seed=0,
+        description="16x16 non-separable HyGT (N=256), 3 rounds, 16 sets, 16,777,216 "
+                    "Laplace(4) int16 blocks clipped to [-2048, 2047]"),
+}
+
+
+def get(name: str) -> Workload:
+    return _REGISTRY[name]
+
+
+def names():
+    return sorted(_REGISTRY)
