@@ -213,18 +213,21 @@ def oracle_sample(w, data, nblk):
 
 
 def cpu_baseline(w, data, target_s=10.0):
+    """The oracle, as it stands, on a bounded sample: the first blocks of the
+    workload (all of it if it is small enough), repeated to about target_s."""
     nblk = min(w.nblocks, 16384)
     dt, cores = oracle_sample(w, data, nblk)
-    # grow the sample to about target_s of wall time
-    want = int(nblk * target_s / max(dt, 1e-3))
-    nblk2 = max(nblk, min(w.nblocks, want))
-    if nblk2 > nblk:
-        dt, cores = oracle_sample(w, data, nblk2)
-        nblk = nblk2
-    return {"value": nblk / dt, "unit": "blocks/s", "cores": cores, "kind": "oracle",
-            "sample": "integer forward + inverse of the first %d blocks of %s "
+    per_block = dt / nblk
+    nblk = int(min(w.nblocks, max(nblk, target_s / max(per_block, 1e-12))))
+    reps = max(1, int(round(target_s / max(per_block * nblk, 1e-9))))
+    total = 0.0
+    for _ in range(reps):
+        dt, cores = oracle_sample(w, data, nblk)
+        total += dt
+    return {"value": nblk * reps / total, "unit": "blocks/s", "cores": cores, "kind": "oracle",
+            "sample": "integer forward + inverse of the first %d blocks of %s, %d time(s) "
                       "(C oracle, int64 arithmetic, OpenMP over blocks), %.1f s"
-                      % (nblk, w.name, dt)}
+                      % (nblk, w.name, reps, total)}
 
 
 def run_reference(args, rank, world):
@@ -286,17 +289,18 @@ def run_ours(args, rank, world, local):
     d_y = torch.empty((count, N), dtype=torch.int32, device=dev)
     d_xr = torch.empty((count, N), dtype=torch.int16, device=dev)
     stream = torch.cuda.current_stream(dev)
+    batch = hygt.Batch(plan, count, device=dev)
 
-    def step():
-        plan.forward(d_x, d_s, out=d_y)
-        plan.inverse(d_y, d_s, out=d_xr)
-
-    for _ in range(max(3, args.warmup)):
-        step()
+    # One step: bucket the batch by set, forward, inverse (5 kernels).
+    K = args.steps
+    W = max(3, args.warmup)
+    for _ in range(W):
+        batch.build(d_s)
+        batch.forward(d_x, out=d_y)
+        batch.inverse(d_y, out=d_xr)
     torch.cuda.synchronize(dev)
 
-    K = args.steps
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K + 1)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * K + 1)]
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(gpu_smi_id(dev, local))
@@ -307,17 +311,20 @@ def run_ours(args, rank, world, local):
     t_start.record(stream)
     ev[0].record(stream)
     for k in range(K):
-        plan.forward(d_x, d_s, out=d_y)
-        ev[2 * k + 1].record(stream)
-        plan.inverse(d_y, d_s, out=d_xr)
-        ev[2 * k + 2].record(stream)
+        batch.build(d_s)
+        ev[3 * k + 1].record(stream)
+        batch.forward(d_x, out=d_y)
+        ev[3 * k + 2].record(stream)
+        batch.inverse(d_y, out=d_xr)
+        ev[3 * k + 3].record(stream)
     t_end.record(stream)
     torch.cuda.synchronize(dev)
     barrier(world)
     clock_info = clocks.stop()
     total_ms = t_start.elapsed_time(t_end)
-    fwd_ms = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(K)]
-    inv_ms = [ev[2 * k + 1].elapsed_time(ev[2 * k + 2]) for k in range(K)]
+    build_ms = [ev[3 * k].elapsed_time(ev[3 * k + 1]) for k in range(K)]
+    fwd_ms = [ev[3 * k + 1].elapsed_time(ev[3 * k + 2]) for k in range(K)]
+    inv_ms = [ev[3 * k + 2].elapsed_time(ev[3 * k + 3]) for k in range(K)]
     total_ms = max_over_ranks(total_ms, world, dev)
 
     blocks_total = count * world * K
@@ -326,29 +333,37 @@ def run_ours(args, rank, world, local):
     # roofline of the dominant kernel (algorithmic bytes / average duration)
     bytes_per_launch = count * (2 * N + 4 * N + 2)  # same for forward and inverse
     f_avg, i_avg = statistics.mean(fwd_ms), statistics.mean(inv_ms)
-    dom_name, dom_ms = ("hygt_int_forward", f_avg) if f_avg >= i_avg else ("hygt_int_inverse", i_avg)
+    dom_name, dom_ms = (("hygt_batch_forward", f_avg) if f_avg >= i_avg
+                        else ("hygt_batch_inverse", i_avg))
     peak, peak_kind = measured_peaks()
     achieved = bytes_per_launch / (dom_ms / 1000.0) / 1e9
+    step_bytes = 2 * bytes_per_launch
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": ncu_traffic(dom_name, w.name),
                 "kernel": dom_name, "peak_source": peak_kind,
-                "fwd_ms": f_avg, "inv_ms": i_avg,
-                "bytes_per_launch": bytes_per_launch}
+                "bytes_per_launch": bytes_per_launch,
+                "fwd_ms": f_avg, "inv_ms": i_avg, "schedule_ms": statistics.mean(build_ms),
+                "step_frac": (step_bytes / (total_ms / K / 1000.0) / 1e9) / peak}
+
+    # context: the direct (unbucketed) kernels on the same data
+    direct = direct_path_ms(plan, d_x, d_s, d_y, d_xr, stream)
 
     line = {
         "metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": world,
-        "steps": K, "warmup": max(3, args.warmup), "ms_per_step": total_ms / K,
+        "steps": K, "warmup": W, "ms_per_step": total_ms / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
         "config": {"workload": w.name, "nblocks": count, "N": N, "rounds": w.rounds,
                    "sets": w.num_sets, "parallelism": "dp%d" % world,
+                   "step": "bucket blocks by set, integer forward, integer inverse",
                    "l2": "inputs larger than L2 (%.0f MB read + %.0f MB written per step "
                          "vs %d MB L2), no flush" % (count * 6 * N / 1e6, count * 6 * N / 1e6,
                                                      L2_BYTES >> 20),
                    "description": w.description},
         "roofline": roofline,
-        "gpu_launches": 2 * K,
+        "gpu_launches": 5 * K,
         "clocks": clock_info,
+        "direct_path": direct,
     }
 
     if not args.no_e2e:
@@ -364,10 +379,31 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def direct_path_ms(plan, d_x, d_s, d_y, d_xr, stream, steps=5):
+    """Forward and inverse through the unbucketed kernels (hygt_forward /
+    hygt_inverse), for context."""
+    import torch
+    plan.forward(d_x, d_s, out=d_y)
+    plan.inverse(d_y, d_s, out=d_xr)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fw, iv = [], []
+    for _ in range(steps):
+        ev[0].record(stream)
+        plan.forward(d_x, d_s, out=d_y)
+        ev[1].record(stream)
+        plan.inverse(d_y, d_s, out=d_xr)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        fw.append(ev[0].elapsed_time(ev[1]))
+        iv.append(ev[1].elapsed_time(ev[2]))
+    return {"fwd_ms": statistics.mean(fw), "inv_ms": statistics.mean(iv)}
+
+
 def e2e_leg(plan, x_np, s_np, N, dev, stream, world, steps=5):
     """Same metric through the public API with host buffers: every step
-    copies the blocks and set indices host->device (pinned), runs forward and
-    inverse, and copies the coefficients and reconstructed blocks back."""
+    copies the blocks and set indices host->device (pinned), buckets them,
+    runs forward and inverse, and copies the coefficients and reconstructed
+    blocks back."""
     import numpy as np
     import torch
     count = x_np.shape[0]
@@ -380,11 +416,15 @@ def e2e_leg(plan, x_np, s_np, N, dev, stream, world, steps=5):
     d_y = torch.empty((count, N), dtype=torch.int32, device=dev)
     d_xr = torch.empty((count, N), dtype=torch.int16, device=dev)
 
+    from paper_2505_21728_gb300 import hygt
+    batch = hygt.Batch(plan, count, device=dev)
+
     def step():
         d_x.copy_(h_x, non_blocking=True)
         d_s.copy_(h_s, non_blocking=True)
-        plan.forward(d_x, d_s, out=d_y)
-        plan.inverse(d_y, d_s, out=d_xr)
+        batch.build(d_s)
+        batch.forward(d_x, out=d_y)
+        batch.inverse(d_y, out=d_xr)
         h_y.copy_(d_y, non_blocking=True)
         h_xr.copy_(d_xr, non_blocking=True)
 

@@ -134,6 +134,37 @@ hygt_status hygt_inverse_f32(hygt_plan plan, const float *d_y, float *d_x,
                              const uint16_t *d_set, int64_t nblocks, hygt_stream stream,
                              int *d_status);
 
+/*
+ * Set-bucketed batch path for the integer transform (same results as
+ * hygt_forward / hygt_inverse, bit for bit).  The per-block set index is the
+ * classification index of Sec. II; blocks are first bucketed by set so that
+ * each group of 32 blocks shares its multipliers, then transformed.
+ *
+ *   hygt_batch_workspace_bytes  device bytes of the schedule for nblocks
+ *                               blocks (0 if nblocks is out of range).
+ *   hygt_batch_build            buckets d_set (uint16 [nblocks]; NULL = set 0)
+ *                               into the caller's workspace d_work (16-byte
+ *                               aligned, >= the bytes above), async on stream.
+ *   hygt_forward_batch /        transform with a schedule built for the same
+ *   hygt_inverse_batch          plan set count and nblocks (a schedule built
+ *                               for other sizes makes the call write
+ *                               HYGT_ERR_ARG to d_status and no output).  One
+ *                               schedule serves any number of forward and
+ *                               inverse calls while d_set is unchanged.
+ * nblocks <= 2^30.  Block sizes N <= 64 (log2n <= 6); larger plans return
+ * HYGT_ERR_UNSUPPORTED from the transform calls.  Skip and bad set indices
+ * behave as in hygt_forward / hygt_inverse.
+ */
+size_t hygt_batch_workspace_bytes(hygt_plan plan, int64_t nblocks);
+hygt_status hygt_batch_build(hygt_plan plan, const uint16_t *d_set, int64_t nblocks,
+                             void *d_work, size_t work_bytes, hygt_stream stream);
+hygt_status hygt_forward_batch(hygt_plan plan, const void *d_work, const int16_t *d_x,
+                               int32_t *d_y, int64_t nblocks, hygt_stream stream,
+                               int *d_status);
+hygt_status hygt_inverse_batch(hygt_plan plan, const void *d_work, const int32_t *d_y,
+                               int16_t *d_x, int64_t nblocks, hygt_stream stream,
+                               int *d_status);
+
 /* Plan shape: any out-pointer may be NULL. */
 hygt_status hygt_plan_info(hygt_plan plan, int *log2n, int *rounds, int *num_sets,
                            int *is_float);

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/hygt.h"
+#include "hygt_batch.cuh"
 #include "hygt_launch.cuh"
 
 struct hygt_plan_s {
@@ -24,6 +25,8 @@ struct hygt_plan_s {
   uint8_t* d_perm = nullptr;  // uint8 [S][R][N]
   size_t perm_bytes = 0;
   unsigned perm_mask = 0;
+  void* d_gtab = nullptr;     // int4 (c, s - c, -(c + s), s) per pair, batch path
+  int* d_poff = nullptr;      // int32 [S][R][N] gather indices, batch path
 };
 
 namespace hygt {
@@ -47,6 +50,9 @@ DeviceInfo device_info(int device) {
 namespace {
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
+// Largest batch of the bucketed path: slots are int32 and each of the
+// num_sets + 2 buckets may add 31 padding slots.
+constexpr int64_t kBatchMaxBlocks = (int64_t)1 << 30;
 
 size_t pad16(size_t b) { return (b + 15) & ~(size_t)15; }
 
@@ -57,6 +63,8 @@ void free_plan(hygt_plan p) {
   if (p->d_tab_int) cudaFree(p->d_tab_int);
   if (p->d_tab_f32) cudaFree(p->d_tab_f32);
   if (p->d_perm) cudaFree(p->d_perm);
+  if (p->d_gtab) cudaFree(p->d_gtab);
+  if (p->d_poff) cudaFree(p->d_poff);
   delete p;
 }
 
@@ -180,11 +188,16 @@ hygt_status hygt_create(hygt_plan* out, int log2n, int rounds, int num_sets,
   }
   std::vector<uint32_t> ti(pairs);
   std::vector<float> tf(2 * pairs);
+  std::vector<int> tg(4 * pairs);  // batch path: (c, s - c, -(c + s), s)
   for (size_t i = 0; i < pairs; ++i) {
     const int q = h_angle_idx[i];
     ti[i] = ((uint32_t)ct[q] & 0xffffu) | ((uint32_t)st[q] << 16);
     tf[2 * i] = cf[q];
     tf[2 * i + 1] = sf[q];
+    tg[4 * i] = ct[q];
+    tg[4 * i + 1] = st[q] - ct[q];
+    tg[4 * i + 2] = -(ct[q] + st[q]);
+    tg[4 * i + 3] = st[q];
   }
 
   hygt_plan p = new (std::nothrow) hygt_plan_s();
@@ -205,7 +218,12 @@ hygt_status hygt_create(hygt_plan* out, int log2n, int rounds, int num_sets,
     p->tab_f32_bytes = pad16(pairs * 8);
     s = upload(&p->d_tab_f32, tf.data(), pairs * 8, p->tab_f32_bytes);
   }
+  if (s == HYGT_OK) s = upload(&p->d_gtab, tg.data(), pairs * 16, pairs * 16);
   if (s == HYGT_OK) s = upload_perms(p, perm, mask);
+  if (s == HYGT_OK && mask) {
+    std::vector<int> po(perm.begin(), perm.end());
+    s = upload(reinterpret_cast<void**>(&p->d_poff), po.data(), po.size() * 4, po.size() * 4);
+  }
   if (s != HYGT_OK) {
     free_plan(p);
     return s;
@@ -286,6 +304,61 @@ hygt_status hygt_inverse_f32(hygt_plan plan, const float* d_y, float* d_x, const
   if (s != HYGT_OK || nblocks == 0) return s;
   hygt::Params p = base_params(plan, d_y, d_x, d_set, nblocks, d_status, true);
   return to_status(hygt::launch_f32_inv(plan->log2n, p, (cudaStream_t)stream));
+}
+
+size_t hygt_batch_workspace_bytes(hygt_plan plan, int64_t nblocks) {
+  if (!plan || nblocks < 0 || nblocks > kBatchMaxBlocks) return 0;
+  return hygt::batch_layout(plan->num_sets, nblocks).total;
+}
+
+hygt_status hygt_batch_build(hygt_plan plan, const uint16_t* d_set, int64_t nblocks, void* d_work,
+                             size_t work_bytes, hygt_stream stream) {
+  if (!plan || nblocks < 0 || nblocks > kBatchMaxBlocks || !d_work || !aligned16(d_work))
+    return HYGT_ERR_ARG;
+  if (work_bytes < hygt::batch_layout(plan->num_sets, nblocks).total) return HYGT_ERR_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HYGT_ERR_CUDA;
+  if (dev != plan->device) return HYGT_ERR_ARG;
+  return to_status(hygt::batch_build(d_set, nblocks, plan->num_sets, d_work, (cudaStream_t)stream));
+}
+
+static hygt_status batch_call(hygt_plan plan, const void* d_work, const void* in, void* out,
+                              int64_t nblocks, hygt_stream stream, int* d_status, bool inverse) {
+  hygt_status s = check_io(plan, in, out, nblocks);
+  if (s != HYGT_OK || nblocks == 0) return s;
+  if (plan->is_float) return HYGT_ERR_UNSUPPORTED;
+  if (plan->log2n > 6) return HYGT_ERR_UNSUPPORTED;
+  if (!d_work || !aligned16(d_work) || nblocks > kBatchMaxBlocks) return HYGT_ERR_ARG;
+  const hygt::BatchLayout L = hygt::batch_layout(plan->num_sets, nblocks);
+  const char* w = static_cast<const char*>(d_work);
+  hygt::BatchParams p{};
+  p.in = in;
+  p.out = out;
+  p.order = reinterpret_cast<const int*>(w + L.order);
+  p.starts = reinterpret_cast<const int*>(w + L.starts);
+  p.meta = reinterpret_cast<const int*>(w + L.meta);
+  p.nblocks = nblocks;
+  p.gtab = static_cast<const int4*>(plan->d_gtab);
+  p.poff = plan->d_poff;
+  p.perm_mask = plan->perm_mask;
+  p.rounds = plan->rounds;
+  p.num_sets = plan->num_sets;
+  p.frac_bits = plan->frac_bits;
+  p.status = d_status;
+  const bool perms = plan->d_poff != nullptr;
+  cudaError_t e = inverse ? hygt::launch_batch_inv(plan->log2n, p, perms, nblocks, (cudaStream_t)stream)
+                          : hygt::launch_batch_fwd(plan->log2n, p, perms, nblocks, (cudaStream_t)stream);
+  return to_status(e);
+}
+
+hygt_status hygt_forward_batch(hygt_plan plan, const void* d_work, const int16_t* d_x, int32_t* d_y,
+                               int64_t nblocks, hygt_stream stream, int* d_status) {
+  return batch_call(plan, d_work, d_x, d_y, nblocks, stream, d_status, false);
+}
+
+hygt_status hygt_inverse_batch(hygt_plan plan, const void* d_work, const int32_t* d_y, int16_t* d_x,
+                               int64_t nblocks, hygt_stream stream, int* d_status) {
+  return batch_call(plan, d_work, d_y, d_x, nblocks, stream, d_status, true);
 }
 
 hygt_status hygt_plan_info(hygt_plan plan, int* log2n, int* rounds, int* num_sets, int* is_float) {

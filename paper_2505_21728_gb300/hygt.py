@@ -48,6 +48,14 @@ def _load() -> ctypes.CDLL:
         f = getattr(L, name)
         f.argtypes = [P, P, P, P, i64, P, P]
         f.restype = i32
+    L.hygt_batch_workspace_bytes.argtypes = [P, i64]
+    L.hygt_batch_workspace_bytes.restype = ctypes.c_size_t
+    L.hygt_batch_build.argtypes = [P, P, i64, P, ctypes.c_size_t, P]
+    L.hygt_batch_build.restype = i32
+    for name in ("hygt_forward_batch", "hygt_inverse_batch"):
+        f = getattr(L, name)
+        f.argtypes = [P, P, P, P, i64, P, P]
+        f.restype = i32
     L.hygt_plan_info.argtypes = [P] + [ctypes.POINTER(i32)] * 4
     L.hygt_plan_info.restype = i32
     L.hygt_param_bytes.argtypes = [i32, i32, i32]
@@ -114,6 +122,22 @@ def hygt_forward_f32(plan, d_x, d_y, d_set, nblocks, stream, d_status):
 
 def hygt_inverse_f32(plan, d_y, d_x, d_set, nblocks, stream, d_status):
     return int(_lib.hygt_inverse_f32(plan, d_y, d_x, d_set, nblocks, stream, d_status))
+
+
+def hygt_batch_workspace_bytes(plan, nblocks):
+    return int(_lib.hygt_batch_workspace_bytes(plan, nblocks))
+
+
+def hygt_batch_build(plan, d_set, nblocks, d_work, work_bytes, stream):
+    return int(_lib.hygt_batch_build(plan, d_set, nblocks, d_work, work_bytes, stream))
+
+
+def hygt_forward_batch(plan, d_work, d_x, d_y, nblocks, stream, d_status):
+    return int(_lib.hygt_forward_batch(plan, d_work, d_x, d_y, nblocks, stream, d_status))
+
+
+def hygt_inverse_batch(plan, d_work, d_y, d_x, nblocks, stream, d_status):
+    return int(_lib.hygt_inverse_batch(plan, d_work, d_y, d_x, nblocks, stream, d_status))
 
 
 def hygt_plan_info(plan):
@@ -232,3 +256,57 @@ class Plan:
             out = torch.empty(y.shape, dtype=torch.float32, device=y.device)
         return self._call(hygt_inverse_f32, "hygt_inverse_f32", y, out, sets, torch.float32,
                           torch.float32, status, stream)
+
+
+class Batch:
+    """A set-bucketed schedule of ``nblocks`` blocks for one plan.
+
+    ``build(sets)`` buckets the per-block set indices on the device (into a
+    workspace tensor this object owns); ``forward`` / ``inverse`` then run the
+    bucketed kernels.  Rebuild whenever the set indices change.
+    """
+
+    def __init__(self, plan: Plan, nblocks: int, device=None):
+        import torch
+        self.plan = plan
+        self.nblocks = int(nblocks)
+        nbytes = hygt_batch_workspace_bytes(plan.handle, self.nblocks)
+        if nbytes == 0:
+            raise HygtError(HYGT_ERR_ARG, "hygt_batch_workspace_bytes")
+        self.work = torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+    def build(self, sets=None, stream=None):
+        import torch
+        ps = None
+        if sets is not None:
+            ps = _dptr(sets, torch.int16 if sets.dtype == torch.int16 else torch.uint16, None, "sets")
+            if sets.numel() != self.nblocks:
+                raise ValueError("sets must have one entry per block")
+        _check(hygt_batch_build(self.plan.handle, ps, self.nblocks, self.work.data_ptr(),
+                                self.work.numel(), _stream_handle(stream)), "hygt_batch_build")
+        return self
+
+    def _run(self, fn, name, x, out, in_dtype, out_dtype, status, stream):
+        import torch
+        if x.shape[0] != self.nblocks or out.shape[0] != self.nblocks:
+            raise ValueError("batch built for %d blocks" % self.nblocks)
+        px = _dptr(x, in_dtype, self.plan.N, "input")
+        po = _dptr(out, out_dtype, self.plan.N, "output")
+        pst = None if status is None else _dptr(status, torch.int32, None, "status")
+        _check(fn(self.plan.handle, self.work.data_ptr(), px, po, self.nblocks,
+                  _stream_handle(stream), pst), name)
+        return out
+
+    def forward(self, x, out=None, status=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(x.shape, dtype=torch.int32, device=x.device)
+        return self._run(hygt_forward_batch, "hygt_forward_batch", x, out, torch.int16,
+                         torch.int32, status, stream)
+
+    def inverse(self, y, out=None, status=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(y.shape, dtype=torch.int16, device=y.device)
+        return self._run(hygt_inverse_batch, "hygt_inverse_batch", y, out, torch.int32,
+                         torch.int16, status, stream)

@@ -1,0 +1,104 @@
+"""Parity of the set-bucketed batch path (hygt_batch_build + hygt_forward_batch /
+hygt_inverse_batch) with the CPU oracle: bit-exact, including skip and
+out-of-range set indices, ragged batch sizes and a stale schedule."""
+import numpy as np
+import pytest
+
+from paper_2505_21728_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _t(a):
+    import torch
+    if a.dtype == np.uint16:
+        a = a.view(np.int16)
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run_batch(gpu, log2n, rounds, q, perms, x, sets):
+    import torch
+    plan = gpu.Plan(log2n, rounds, q, perms)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    b = gpu.Batch(plan, x.shape[0]).build(None if sets is None else _t(sets))
+    y = b.forward(_t(x), status=st)
+    xr = b.inverse(y, status=st)
+    return y.cpu().numpy(), xr.cpu().numpy(), int(st.item())
+
+
+@pytest.mark.parametrize("log2n", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("rounds,perm_kind", [(1, "none"), (2, "between"), (3, "all")])
+def test_batch_parity(gpu, orc, log2n, rounds, perm_kind):
+    N = 1 << log2n
+    S, B = 9, 5003
+    q = inputs.angle_indices(S, rounds, log2n, seed=log2n + 7 * rounds)
+    perms = None if perm_kind == "none" else inputs.permutations(
+        S, rounds, N, seed=3, between_rounds_only=(perm_kind == "between"))
+    x = inputs.laplacian_blocks(B, N, 50.0, -32768, 32767, seed=log2n)
+    sets = inputs.set_indices(B, S, seed=log2n, skip_frac=0.1)
+    y, xr, st = run_batch(gpu, log2n, rounds, q, perms, x, sets)
+    ye, _ = orc.fwd_int(x, q, log2n, rounds, perms, sets)
+    xe, _ = orc.inv_int(ye, q, log2n, rounds, perms, sets)
+    assert st == 0
+    assert np.array_equal(y, ye)
+    assert np.array_equal(xr, xe)
+
+
+@pytest.mark.parametrize("B", [1, 31, 32, 33, 1000])
+def test_batch_ragged_and_bad_sets(gpu, orc, B):
+    log2n, rounds, S = 6, 2, 105
+    q = inputs.angle_indices(S, rounds, log2n, seed=2)
+    perms = inputs.permutations(S, rounds, 64, seed=2)
+    x = inputs.laplacian_blocks(B, 64, 8.0, -1024, 1023, seed=B)
+    sets = inputs.set_indices(B, S, seed=B, skip_frac=0.1)
+    if B > 20:
+        sets[3] = 200
+        sets[B - 1] = S
+    y, xr, st = run_batch(gpu, log2n, rounds, q, perms, x, sets)
+    ye, ste = orc.fwd_int(x, q, log2n, rounds, perms, sets)
+    xe, _ = orc.inv_int(ye, q, log2n, rounds, perms, sets)
+    assert st == (4 if B > 20 else 0) and ste == (orc.ERR_SET if B > 20 else 0)
+    assert np.array_equal(y, ye) and np.array_equal(xr, xe)
+
+
+def test_batch_no_sets_one_set(gpu, orc):
+    log2n, rounds = 4, 2
+    q = inputs.angle_indices(1, rounds, log2n, seed=0)
+    perms = inputs.permutations(1, rounds, 16, seed=0)
+    x = inputs.laplacian_blocks(4097, 16, 12.0, -512, 511, seed=0)
+    y, xr, st = run_batch(gpu, log2n, rounds, q, perms, x, None)
+    ye, _ = orc.fwd_int(x, q, log2n, rounds, perms)
+    xe, _ = orc.inv_int(ye, q, log2n, rounds, perms)
+    assert st == 0 and np.array_equal(y, ye) and np.array_equal(xr, xe)
+
+
+def test_batch_schedule_size_mismatch_reports(gpu):
+    import torch
+    q = inputs.angle_indices(3, 2, 6, seed=0)
+    plan = gpu.Plan(6, 2, q)
+    x = _t(inputs.laplacian_blocks(100, 64, 8.0, -1024, 1023, seed=0))
+    sets = _t(inputs.set_indices(100, 3, seed=0))
+    b = gpu.Batch(plan, 100).build(sets)
+    # a schedule for 100 blocks used for 64 blocks: status ERR_ARG, output untouched
+    b64 = gpu.Batch(plan, 64)
+    b64.work.copy_(b.work[:b64.work.numel()])
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    out = torch.full((64, 64), 7, dtype=torch.int32, device="cuda")
+    b64.forward(x[:64], out=out, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == gpu.HYGT_ERR_ARG
+    assert bool((out == 7).all())
+
+
+def test_batch_workload_8x8_full(gpu, orc):
+    """The benchmark's launch configuration on all 4,194,304 blocks."""
+    from paper_2505_21728_gb300 import workloads
+    w = workloads.get("hygt8x8_r2_s105")
+    d = w.generate()
+    y, xr, st = run_batch(gpu, w.log2n, w.rounds, d["angle_idx"], d["perms"], d["x"], d["sets"])
+    ye, ste = orc.fwd_int(d["x"], d["angle_idx"], w.log2n, w.rounds, d["perms"], d["sets"])
+    assert st == 0 and ste == 0
+    assert np.array_equal(y, ye)
+    del ye
+    xe, _ = orc.inv_int(y, d["angle_idx"], w.log2n, w.rounds, d["perms"], d["sets"])
+    assert np.array_equal(xr, xe)
