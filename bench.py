@@ -45,6 +45,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the timed oracle sample (for profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    ap.add_argument("--nblocks", type=int, default=0,
+                    help="use only the first N blocks of the workload (profiling cases)")
     return ap.parse_args()
 
 
@@ -278,6 +280,8 @@ def run_ours(args, rank, world, local):
     from paper_2505_21728_gb300 import hygt, workloads
 
     w = workloads.get(args.workload)
+    if args.nblocks:
+        w = workloads.truncated(w, args.nblocks)
     data = w.generate()
     start, count = shard_blocks(w.nblocks, rank, world, weak=True)
     x_np = data["x"][start:start + count]

@@ -138,7 +138,7 @@ hygt_status hygt_inverse_f32(hygt_plan plan, const float *d_y, float *d_x,
  * Set-bucketed batch path for the integer transform (same results as
  * hygt_forward / hygt_inverse, bit for bit).  The per-block set index is the
  * classification index of Sec. II; blocks are first bucketed by set so that
- * each group of 32 blocks shares its multipliers, then transformed.
+ * the blocks of each warp share their multipliers, then transformed.
  *
  *   hygt_batch_workspace_bytes  device bytes of the schedule for nblocks
  *                               blocks (0 if nblocks is out of range).
@@ -151,9 +151,8 @@ hygt_status hygt_inverse_f32(hygt_plan plan, const float *d_y, float *d_x,
  *                               HYGT_ERR_ARG to d_status and no output).  One
  *                               schedule serves any number of forward and
  *                               inverse calls while d_set is unchanged.
- * nblocks <= 2^30.  Block sizes N <= 64 (log2n <= 6); larger plans return
- * HYGT_ERR_UNSUPPORTED from the transform calls.  Skip and bad set indices
- * behave as in hygt_forward / hygt_inverse.
+ * nblocks <= 2^30, every block size of hygt_create.  Skip and bad set
+ * indices behave as in hygt_forward / hygt_inverse.
  */
 size_t hygt_batch_workspace_bytes(hygt_plan plan, int64_t nblocks);
 hygt_status hygt_batch_build(hygt_plan plan, const uint16_t *d_set, int64_t nblocks,

@@ -34,10 +34,12 @@ __global__ void __launch_bounds__(kBucketThreads) batch_count(const uint16_t* __
       if (hist[i]) atomicAdd(&counts[i], hist[i]);
 }
 
-// Pass 2 (one CTA): padded exclusive scan of the counts into the bucket
-// starts and scatter cursors; writes -1 into the padding slots.
+// Pass 2 (one CTA): exclusive scan of the counts, each padded to a multiple
+// of the task size `group`, into the bucket starts and scatter cursors;
+// writes -1 into the padding slots.
 __global__ void __launch_bounds__(1024) batch_scan(const int* __restrict__ counts, int num_sets,
-                                                  long long nblocks, int* __restrict__ starts,
+                                                  long long nblocks, int group,
+                                                  int* __restrict__ starts,
                                                   int* __restrict__ cursor, int* __restrict__ meta,
                                                   int* __restrict__ order) {
   __shared__ long long part[1024];
@@ -47,7 +49,8 @@ __global__ void __launch_bounds__(1024) batch_scan(const int* __restrict__ count
   __syncthreads();
   for (int base = 0; base < nb; base += blockDim.x) {
     const int k = base + threadIdx.x;
-    const long long padded = (k < nb) ? (long long)((counts[k] + 31) & ~31) : 0;
+    const long long padded =
+        (k < nb) ? (long long)((counts[k] + group - 1) / group) * group : 0;
     part[threadIdx.x] = padded;
     __syncthreads();
     for (int d = 1; d < (int)blockDim.x; d <<= 1) {  // inclusive Hillis-Steele scan
@@ -68,9 +71,10 @@ __global__ void __launch_bounds__(1024) batch_scan(const int* __restrict__ count
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    meta[0] = (int)(carry / 32);
+    meta[0] = (int)(carry / group);
     meta[1] = (int)nblocks;
     meta[2] = num_sets;
+    meta[3] = group;
     starts[nb] = (int)carry;
   }
 }
@@ -120,13 +124,13 @@ __global__ void __launch_bounds__(kBucketThreads) batch_scatter(const uint16_t* 
   }
 }
 
-cudaError_t batch_build(const uint16_t* d_set, long long nblocks, int num_sets, void* d_work,
-                        cudaStream_t stream) {
+cudaError_t batch_build(const uint16_t* d_set, long long nblocks, int num_sets, int group,
+                        void* d_work, cudaStream_t stream) {
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
   const DeviceInfo info = device_info(dev);
-  const BatchLayout L = batch_layout(num_sets, nblocks);
+  const BatchLayout L = batch_layout(num_sets, nblocks, group);
   char* w = static_cast<char*>(d_work);
   int* counts = reinterpret_cast<int*>(w + L.counts);
   int* starts = reinterpret_cast<int*>(w + L.starts);
@@ -141,7 +145,8 @@ cudaError_t batch_build(const uint16_t* d_set, long long nblocks, int num_sets, 
   if (g1 < 1) g1 = 1;
   batch_count<<<(unsigned)g1, kBucketThreads, local ? 4 * L.nb : 0, stream>>>(d_set, nblocks,
                                                                             num_sets, counts);
-  batch_scan<<<1, 1024, 0, stream>>>(counts, num_sets, nblocks, starts, cursor, meta, order);
+  batch_scan<<<1, 1024, 0, stream>>>(counts, num_sets, nblocks, group, starts, cursor, meta,
+                                     order);
   long long g3 = (nblocks + kBucketTile - 1) / kBucketTile;
   if (g3 > 4LL * info.sms) g3 = 4LL * info.sms;
   if (g3 < 1) g3 = 1;
@@ -151,14 +156,20 @@ cudaError_t batch_build(const uint16_t* d_set, long long nblocks, int num_sets, 
 }
 
 template <int LOG2N, int KIND>
-static cudaError_t launch_batch_sized(const BatchParams& p, bool perms, long long nblocks,
-                                      cudaStream_t stream) {
+static cudaError_t launch_batch_sized(BatchParams p, cudaStream_t stream) {
   auto kern = hygt_batch_kernel<LOG2N, KIND>;
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
   const DeviceInfo info = device_info(dev);
-  const size_t smem = perms ? (size_t)(1 << LOG2N) * kBatchThreads * 4 : 0;
+  constexpr int G = batch_group(LOG2N);
+  const size_t pbuf = (size_t)(kBatchThreads / 32) * G * perm_region_words(LOG2N) * 4;
+  const size_t set_bytes = (size_t)p.set_words * 4;
+  long long fit = ((long long)info.max_smem_optin - (long long)pbuf) / (long long)set_bytes;
+  if (fit > 64) fit = 64;
+  if (fit < 0) fit = 0;
+  p.max_cached_sets = (int)fit;
+  const size_t smem = pbuf + (size_t)fit * set_bytes;
   static std::atomic<int> attr_set{0};
   if ((int)smem > attr_set.load()) {
     err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -169,8 +180,8 @@ static cudaError_t launch_batch_sized(const BatchParams& p, bool perms, long lon
   err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBatchThreads, smem);
   if (err != cudaSuccess) return err;
   if (occ < 1) occ = 1;
-  const long long per_cta = (long long)(kBatchThreads / 32) * 32;
-  long long need = (nblocks + per_cta - 1) / per_cta + 1;
+  const long long per_cta = (long long)(kBatchThreads / 32) * G;
+  long long need = (p.nblocks + per_cta - 1) / per_cta + 1;
   long long grid = (long long)occ * info.sms;
   if (need < grid) grid = need;
   kern<<<(unsigned)grid, kBatchThreads, smem, stream>>>(p);
@@ -178,27 +189,26 @@ static cudaError_t launch_batch_sized(const BatchParams& p, bool perms, long lon
 }
 
 template <int KIND>
-static cudaError_t launch_batch(int log2n, const BatchParams& p, bool perms, long long nblocks,
-                                cudaStream_t stream) {
+static cudaError_t launch_batch(int log2n, const BatchParams& p, cudaStream_t stream) {
   switch (log2n) {
-    case 1: return launch_batch_sized<1, KIND>(p, perms, nblocks, stream);
-    case 2: return launch_batch_sized<2, KIND>(p, perms, nblocks, stream);
-    case 3: return launch_batch_sized<3, KIND>(p, perms, nblocks, stream);
-    case 4: return launch_batch_sized<4, KIND>(p, perms, nblocks, stream);
-    case 5: return launch_batch_sized<5, KIND>(p, perms, nblocks, stream);
-    case 6: return launch_batch_sized<6, KIND>(p, perms, nblocks, stream);
+    case 1: return launch_batch_sized<1, KIND>(p, stream);
+    case 2: return launch_batch_sized<2, KIND>(p, stream);
+    case 3: return launch_batch_sized<3, KIND>(p, stream);
+    case 4: return launch_batch_sized<4, KIND>(p, stream);
+    case 5: return launch_batch_sized<5, KIND>(p, stream);
+    case 6: return launch_batch_sized<6, KIND>(p, stream);
+    case 7: return launch_batch_sized<7, KIND>(p, stream);
+    case 8: return launch_batch_sized<8, KIND>(p, stream);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_batch_fwd(int log2n, const BatchParams& p, bool perms, long long nblocks,
-                             cudaStream_t stream) {
-  return launch_batch<0>(log2n, p, perms, nblocks, stream);
+cudaError_t launch_batch_fwd(int log2n, const BatchParams& p, cudaStream_t stream) {
+  return launch_batch<0>(log2n, p, stream);
 }
 
-cudaError_t launch_batch_inv(int log2n, const BatchParams& p, bool perms, long long nblocks,
-                             cudaStream_t stream) {
-  return launch_batch<1>(log2n, p, perms, nblocks, stream);
+cudaError_t launch_batch_inv(int log2n, const BatchParams& p, cudaStream_t stream) {
+  return launch_batch<1>(log2n, p, stream);
 }
 
 }  // namespace hygt

@@ -25,8 +25,8 @@ struct hygt_plan_s {
   uint8_t* d_perm = nullptr;  // uint8 [S][R][N]
   size_t perm_bytes = 0;
   unsigned perm_mask = 0;
-  void* d_gtab = nullptr;     // int4 (c, s - c, -(c + s), s) per pair, batch path
-  int* d_poff = nullptr;      // int32 [S][R][N] gather indices, batch path
+  int* d_ktab = nullptr;      // batch path: per-set tables [S][ktab_words]
+  int ktab_words = 0;         // words per set, padded to a multiple of 4
 };
 
 namespace hygt {
@@ -63,8 +63,7 @@ void free_plan(hygt_plan p) {
   if (p->d_tab_int) cudaFree(p->d_tab_int);
   if (p->d_tab_f32) cudaFree(p->d_tab_f32);
   if (p->d_perm) cudaFree(p->d_perm);
-  if (p->d_gtab) cudaFree(p->d_gtab);
-  if (p->d_poff) cudaFree(p->d_poff);
+  if (p->d_ktab) cudaFree(p->d_ktab);
   delete p;
 }
 
@@ -117,6 +116,49 @@ hygt_status upload_perms(hygt_plan p, const std::vector<uint8_t>& perm, unsigned
   if (!mask) return HYGT_OK;
   p->perm_bytes = pad16(perm.size());
   return upload(reinterpret_cast<void**>(&p->d_perm), perm.data(), perm.size(), p->perm_bytes);
+}
+
+// Per-set tables of the batch kernels (layout: hygt::SetTableShape).  Register
+// passes store (c, s - c, -(c + s)); lane passes store (c, s) for the m sides
+// then (c, -s) for the n sides; then the permutation gather sources as byte
+// offsets in a block's permutation region.
+void build_ktab(int log2n, int rounds, int num_sets, const uint8_t* q, const std::vector<int>& ct,
+                const std::vector<int>& st, const std::vector<uint8_t>& perm, unsigned mask,
+                std::vector<int>* out, int* words) {
+  const int N = 1 << log2n;
+  const hygt::SetTableShape sh{log2n, hygt::batch_log2e(log2n), rounds, mask ? 1 : 0};
+  const int w = (sh.set_words() + 3) & ~3;
+  *words = w;
+  out->assign((size_t)num_sets * w, 0);
+  for (int s = 0; s < num_sets; ++s) {
+    int* t = out->data() + (size_t)s * w;
+    for (int r = 0; r < rounds; ++r) {
+      for (int p = 0; p < log2n; ++p) {
+        int* row = t + r * sh.round_words() + sh.pass_offset(p);
+        const uint8_t* qa = q + (((size_t)s * rounds + r) * log2n + p) * (N / 2);
+        for (int j = 0; j < N / 2; ++j) {
+          const int c = ct[qa[j]], sn = st[qa[j]];
+          if (p < sh.log2e) {
+            row[3 * j] = c;
+            row[3 * j + 1] = sn - c;
+            row[3 * j + 2] = -(c + sn);
+          } else {
+            row[2 * j] = c;  // m side
+            row[2 * j + 1] = sn;
+            row[N + 2 * j] = c;  // n side
+            row[N + 2 * j + 1] = -sn;
+          }
+        }
+      }
+      if (mask) {
+        int* prow = t + sh.perm_offset(r);
+        for (int i = 0; i < N; ++i) {
+          const int src = perm.empty() ? i : perm[((size_t)s * rounds + r) * N + i];
+          prow[i] = 4 * hygt::perm_word(src);
+        }
+      }
+    }
+  }
 }
 
 hygt_status check_io(hygt_plan plan, const void* in, const void* out, int64_t nblocks) {
@@ -188,16 +230,11 @@ hygt_status hygt_create(hygt_plan* out, int log2n, int rounds, int num_sets,
   }
   std::vector<uint32_t> ti(pairs);
   std::vector<float> tf(2 * pairs);
-  std::vector<int> tg(4 * pairs);  // batch path: (c, s - c, -(c + s), s)
   for (size_t i = 0; i < pairs; ++i) {
     const int q = h_angle_idx[i];
     ti[i] = ((uint32_t)ct[q] & 0xffffu) | ((uint32_t)st[q] << 16);
     tf[2 * i] = cf[q];
     tf[2 * i + 1] = sf[q];
-    tg[4 * i] = ct[q];
-    tg[4 * i + 1] = st[q] - ct[q];
-    tg[4 * i + 2] = -(ct[q] + st[q]);
-    tg[4 * i + 3] = st[q];
   }
 
   hygt_plan p = new (std::nothrow) hygt_plan_s();
@@ -218,11 +255,11 @@ hygt_status hygt_create(hygt_plan* out, int log2n, int rounds, int num_sets,
     p->tab_f32_bytes = pad16(pairs * 8);
     s = upload(&p->d_tab_f32, tf.data(), pairs * 8, p->tab_f32_bytes);
   }
-  if (s == HYGT_OK) s = upload(&p->d_gtab, tg.data(), pairs * 16, pairs * 16);
   if (s == HYGT_OK) s = upload_perms(p, perm, mask);
-  if (s == HYGT_OK && mask) {
-    std::vector<int> po(perm.begin(), perm.end());
-    s = upload(reinterpret_cast<void**>(&p->d_poff), po.data(), po.size() * 4, po.size() * 4);
+  if (s == HYGT_OK) {
+    std::vector<int> kt;
+    build_ktab(log2n, rounds, num_sets, h_angle_idx, ct, st, perm, mask, &kt, &p->ktab_words);
+    s = upload(reinterpret_cast<void**>(&p->d_ktab), kt.data(), kt.size() * 4, kt.size() * 4);
   }
   if (s != HYGT_OK) {
     free_plan(p);
@@ -308,18 +345,20 @@ hygt_status hygt_inverse_f32(hygt_plan plan, const float* d_y, float* d_x, const
 
 size_t hygt_batch_workspace_bytes(hygt_plan plan, int64_t nblocks) {
   if (!plan || nblocks < 0 || nblocks > kBatchMaxBlocks) return 0;
-  return hygt::batch_layout(plan->num_sets, nblocks).total;
+  return hygt::batch_layout(plan->num_sets, nblocks, hygt::batch_group(plan->log2n)).total;
 }
 
 hygt_status hygt_batch_build(hygt_plan plan, const uint16_t* d_set, int64_t nblocks, void* d_work,
                              size_t work_bytes, hygt_stream stream) {
   if (!plan || nblocks < 0 || nblocks > kBatchMaxBlocks || !d_work || !aligned16(d_work))
     return HYGT_ERR_ARG;
-  if (work_bytes < hygt::batch_layout(plan->num_sets, nblocks).total) return HYGT_ERR_ARG;
+  const int group = hygt::batch_group(plan->log2n);
+  if (work_bytes < hygt::batch_layout(plan->num_sets, nblocks, group).total) return HYGT_ERR_ARG;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return HYGT_ERR_CUDA;
   if (dev != plan->device) return HYGT_ERR_ARG;
-  return to_status(hygt::batch_build(d_set, nblocks, plan->num_sets, d_work, (cudaStream_t)stream));
+  return to_status(
+      hygt::batch_build(d_set, nblocks, plan->num_sets, group, d_work, (cudaStream_t)stream));
 }
 
 static hygt_status batch_call(hygt_plan plan, const void* d_work, const void* in, void* out,
@@ -327,9 +366,9 @@ static hygt_status batch_call(hygt_plan plan, const void* d_work, const void* in
   hygt_status s = check_io(plan, in, out, nblocks);
   if (s != HYGT_OK || nblocks == 0) return s;
   if (plan->is_float) return HYGT_ERR_UNSUPPORTED;
-  if (plan->log2n > 6) return HYGT_ERR_UNSUPPORTED;
   if (!d_work || !aligned16(d_work) || nblocks > kBatchMaxBlocks) return HYGT_ERR_ARG;
-  const hygt::BatchLayout L = hygt::batch_layout(plan->num_sets, nblocks);
+  const hygt::BatchLayout L =
+      hygt::batch_layout(plan->num_sets, nblocks, hygt::batch_group(plan->log2n));
   const char* w = static_cast<const char*>(d_work);
   hygt::BatchParams p{};
   p.in = in;
@@ -338,16 +377,17 @@ static hygt_status batch_call(hygt_plan plan, const void* d_work, const void* in
   p.starts = reinterpret_cast<const int*>(w + L.starts);
   p.meta = reinterpret_cast<const int*>(w + L.meta);
   p.nblocks = nblocks;
-  p.gtab = static_cast<const int4*>(plan->d_gtab);
-  p.poff = plan->d_poff;
+  p.tmax = L.tmax;
+  p.ktab = plan->d_ktab;
+  p.set_words = plan->ktab_words;
   p.perm_mask = plan->perm_mask;
+  p.perms = plan->perm_mask ? 1 : 0;
   p.rounds = plan->rounds;
   p.num_sets = plan->num_sets;
   p.frac_bits = plan->frac_bits;
   p.status = d_status;
-  const bool perms = plan->d_poff != nullptr;
-  cudaError_t e = inverse ? hygt::launch_batch_inv(plan->log2n, p, perms, nblocks, (cudaStream_t)stream)
-                          : hygt::launch_batch_fwd(plan->log2n, p, perms, nblocks, (cudaStream_t)stream);
+  cudaError_t e = inverse ? hygt::launch_batch_inv(plan->log2n, p, (cudaStream_t)stream)
+                          : hygt::launch_batch_fwd(plan->log2n, p, (cudaStream_t)stream);
   return to_status(e);
 }
 

@@ -1,22 +1,30 @@
 // hygt_batch.cuh -- set-bucketed integer HyGT (sm_103a).
 //
 // A batch is first bucketed by transform set (counting sort of block ids;
-// every bucket padded to a multiple of 32 with id -1), so that each warp
-// task is 32 blocks that share one set.  The multipliers of that set are
-// then warp-uniform: every lane reads the same address (one broadcast
-// transaction), and a thread holds a whole block (N <= 64) so every
-// hypercube pass is a register butterfly.
+// every bucket padded to a multiple of G blocks with id -1), so that every
+// warp task is G blocks sharing one set.  The kernels then see warp-uniform
+// multipliers.  Because the warps of a CTA walk consecutive tasks of the
+// sorted order, a CTA's tasks span only a few sets: the CTA copies those
+// sets' multipliers into shared memory once, and every lane reads them by
+// broadcast.
 //
-// Butterfly.  The rotation of (a, b) by the integer multipliers (c, s) is
-// computed with three multiplications instead of four:
+// Mapping.  A block of N = 2^LOG2N values is held by L = N / E lanes with
+// E = min(N, 32) consecutive values per lane (element e = lane * E + i in
+// register i), so G = 32 / L blocks per warp.
+//   - Pass p < LOG2E pairs two registers of a lane (register butterfly).
+//   - Pass p >= LOG2E pairs lane l with lane l ^ 2^(p - LOG2E): each lane
+//     fetches its partner's value with __shfl_xor_sync and computes its own
+//     output, y = c * own +/- s * partner.
+//   - The permutation slot after a round goes through the block's region of
+//     a shared-memory buffer.
+//
+// Register butterfly with three multiplications:
 //     k   = c (a + b) + 2^(f-1)
 //     y_m = (k + (s - c) b) >> f        (= (c a + s b + 2^(f-1)) >> f)
 //     y_n = (k - (c + s) a) >> f        (= (c b - s a + 2^(f-1)) >> f)
-// The table stores (c, d1 = s - c, d2 = -(c + s)); the inverse rotation
-// (c, -s) uses the same entries with d1 and d2 exchanged.  The arithmetic is
-// done modulo 2^32: the sums equal the direct products modulo 2^32, so the
-// result is exact whenever the direct formula fits in int32 (always, for
-// int16 input; see the inverse precondition in hygt.h).
+// evaluated modulo 2^32, so it equals the direct formula whenever that fits
+// in int32.  The inverse rotation (c, -s) uses the same entries with
+// d1 = s - c and d2 = -(c + s) exchanged.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -26,180 +34,363 @@
 
 namespace hygt {
 
-constexpr int kBatchThreads = 512;   // threads per CTA of the batch transform
+constexpr int kBatchThreads = 768;   // threads per CTA of the batch transform
 constexpr int kBucketThreads = 512;  // threads per CTA of the bucketing kernels
 constexpr int kBucketTile = 8192;    // blocks per CTA tile in the scatter pass
 
+__host__ __device__ constexpr int batch_log2e(int log2n) { return log2n < 5 ? log2n : 5; }
+// Blocks per warp task for block size 2^log2n.
+__host__ __device__ constexpr int batch_group(int log2n) {
+  return 32 >> (log2n - batch_log2e(log2n));
+}
+
 // Workspace layout (all offsets in bytes, 16-byte aligned sections):
 //   counts [nb]     int32  blocks per bucket (bucket S = skip, S + 1 = bad set)
-//   starts [nb + 1] int32  first slot of each bucket (padded to 32); starts[nb] = total
+//   starts [nb + 1] int32  first slot of each bucket (padded to G); starts[nb] = total
 //   cursor [nb]     int32  scatter cursor per bucket
-//   meta   [4]      int32  warp tasks (total / 32), nblocks, num_sets
-//   order  [32 * tmax] int32 block id per slot, -1 for padding
+//   meta   [4]      int32  warp tasks (total / G), nblocks, num_sets, G
+//   order  [G * tmax] int32 block id per slot, -1 for padding
 struct BatchLayout {
   int nb;           // buckets = S + 2
+  int group;        // G
   long long tmax;   // max warp tasks
   size_t counts, starts, cursor, meta, order, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline BatchLayout batch_layout(int num_sets, long long nblocks) {
+__host__ __device__ inline BatchLayout batch_layout(int num_sets, long long nblocks, int group) {
   BatchLayout L;
   L.nb = num_sets + 2;
-  L.tmax = (nblocks + 31) / 32 + L.nb;
+  L.group = group;
+  L.tmax = (nblocks + group - 1) / group + L.nb;
   size_t off = 0;
   L.counts = off; off = align16(off + 4 * (size_t)L.nb);
   L.starts = off; off = align16(off + 4 * (size_t)(L.nb + 1));
   L.cursor = off; off = align16(off + 4 * (size_t)L.nb);
   L.meta = off;   off = align16(off + 16);
-  L.order = off;  off = align16(off + 4 * 32 * (size_t)L.tmax);
+  L.order = off;  off = align16(off + 4 * (size_t)group * (size_t)L.tmax);
   L.total = off;
   return L;
 }
+
+// ---------------------------------------------------------------- tables
+// Per-set multiplier table of the batch kernels (int32 words), for block
+// size 2^LOG2N and LOG2E = batch_log2e(LOG2N):
+//   for each round r, for each pass p:
+//     p <  LOG2E: N/2 entries (c, s - c, -(c + s))       (3 words)
+//     p >= LOG2E: N/2 entries (c, s) for the m side of each pair, then
+//                 N/2 entries (c, -s) for the n side     (2 + 2 words)
+//   then, if the plan permutes, for each round r: N byte offsets of the
+//   gather source of element i in a block's permutation region.
+struct SetTableShape {
+  int log2n, log2e, rounds, perms;
+  __host__ __device__ constexpr int half() const { return 1 << (log2n - 1); }
+  __host__ __device__ constexpr int pass_offset(int p) const {
+    return half() * (3 * (p < log2e ? p : log2e) + 4 * (p < log2e ? 0 : p - log2e));
+  }
+  __host__ __device__ constexpr int round_words() const { return pass_offset(log2n); }
+  __host__ __device__ constexpr int perm_offset(int r) const {
+    return rounds * round_words() + r * (1 << log2n);
+  }
+  __host__ __device__ constexpr int set_words() const {
+    return rounds * round_words() + (perms ? rounds * (1 << log2n) : 0);
+  }
+};
+
+// Words per block in the permutation buffer and the word of element e:
+// one padding word after every 32 elements (or after the block when it is
+// shorter), which keeps the L lanes of a block and the G blocks of a warp
+// on distinct banks when they write their registers.
+__host__ __device__ constexpr int perm_region_words(int log2n) {
+  return log2n >= 5 ? (1 << log2n) + (1 << (log2n - 5)) : (1 << log2n) + 1;
+}
+__host__ __device__ constexpr int perm_word(int e) { return e + (e >> 5); }
 
 // ---------------------------------------------------------------- transform
 struct BatchParams {
   const void* in;
   void* out;
-  const int* order;      // [32 * ntasks]
-  const int* starts;     // [nb + 1] padded bucket starts
-  const int* meta;       // meta[0] = ntasks, meta[1] = nblocks, meta[2] = num_sets
+  const int* order;      // [G * ntasks]
+  const int* starts;     // [nb + 1] padded bucket starts (slots)
+  const int* meta;       // tasks, nblocks, num_sets, G
   long long nblocks;
-  const int4* gtab;      // (c, d1, d2, s) per pair, [S][R][k][N/2]
-  const int* poff;       // permutation gather indices as int32, [S][R][N], or nullptr
+  long long tmax;        // capacity of order[] in warp tasks (bounds the task count)
+  const int* ktab;       // per-set tables, [S][set_words]
+  int set_words;
   unsigned perm_mask;
+  int perms;
   int rounds;
   int num_sets;
   int frac_bits;
+  int max_cached_sets;   // sets that fit in shared memory next to the permutation buffer
   int* status;
 };
 
-// Gauss butterfly, forward (INV = false) or inverse.
-template <bool INV>
-__device__ __forceinline__ void gbfly(int32_t& a, int32_t& b, const int4 w, uint32_t half, int f) {
-  const uint32_t ua = (uint32_t)a, ub = (uint32_t)b;
-  const uint32_t k = (uint32_t)w.x * (ua + ub) + half;
-  const uint32_t d1 = (uint32_t)(INV ? w.z : w.y);
-  const uint32_t d2 = (uint32_t)(INV ? w.y : w.z);
-  a = (int32_t)(k + d1 * ub) >> f;
-  b = (int32_t)(k + d2 * ua) >> f;
+template <int LOG2N, bool INV>
+struct BatchMath {
+  static constexpr int N = 1 << LOG2N;
+  static constexpr int LOG2E = batch_log2e(LOG2N);
+  static constexpr int E = 1 << LOG2E;
+  static constexpr int L = N / E;
+
+  template <int P>
+  __device__ __forceinline__ static void bfly(int32_t (&v)[E], int jl, int c, int d1, int d2,
+                                              uint32_t half, int f) {
+    const int im = ((jl >> P) << (P + 1)) | (jl & ((1 << P) - 1));
+    const int in = im | (1 << P);
+    const uint32_t ua = (uint32_t)v[im], ub = (uint32_t)v[in];
+    const uint32_t k = (uint32_t)c * (ua + ub) + half;
+    const uint32_t e1 = (uint32_t)(INV ? d2 : d1);
+    const uint32_t e2 = (uint32_t)(INV ? d1 : d2);
+    v[im] = (int32_t)(k + e1 * ub) >> f;
+    v[in] = (int32_t)(k + e2 * ua) >> f;
+  }
+
+  // Register pass p: the lane's pairs are lane * E/2 + jl; `row` holds N/2
+  // entries of 3 words.
+  template <int P>
+  __device__ __forceinline__ static void reg_pass(int32_t (&v)[E], const int* row, int lane,
+                                                  uint32_t half, int f) {
+    constexpr int NP = E / 2;
+    const int* base = row + 3 * lane * NP;
+    if constexpr (NP % 4 == 0) {
+#pragma unroll
+      for (int q = 0; q < NP / 4; ++q) {
+        const int4 a = reinterpret_cast<const int4*>(base)[3 * q];
+        const int4 b = reinterpret_cast<const int4*>(base)[3 * q + 1];
+        const int4 c = reinterpret_cast<const int4*>(base)[3 * q + 2];
+        bfly<P>(v, 4 * q + 0, a.x, a.y, a.z, half, f);
+        bfly<P>(v, 4 * q + 1, a.w, b.x, b.y, half, f);
+        bfly<P>(v, 4 * q + 2, b.z, b.w, c.x, half, f);
+        bfly<P>(v, 4 * q + 3, c.y, c.z, c.w, half, f);
+      }
+    } else {
+#pragma unroll
+      for (int jl = 0; jl < NP; ++jl)
+        bfly<P>(v, jl, base[3 * jl], base[3 * jl + 1], base[3 * jl + 2], half, f);
+    }
+  }
+
+  // Lane pass p: partner lane = lane ^ 2^(p - LOG2E).  `row` holds the N/2
+  // (c, s) entries of the m sides, then the N/2 (c, -s) entries of the n
+  // sides; this lane's E elements use pairs jbase + i of its side.
+  template <int P>
+  __device__ __forceinline__ static void lane_pass(int32_t (&v)[E], const int* row, int lane,
+                                                   uint32_t half, int f) {
+    constexpr int Q = P - LOG2E;
+    constexpr int D = 1 << Q;
+    const int upper = (lane >> Q) & 1;  // this lane holds the n side
+    const int jbase = ((lane >> (Q + 1)) << P) + ((lane & (D - 1)) << LOG2E);
+    // forward: m side (c, s), n side (c, -s); inverse: the opposite
+    const int side = upper ^ (INV ? 1 : 0);
+    const int4* base = reinterpret_cast<const int4*>(row + side * N + 2 * jbase);
+#pragma unroll
+    for (int i = 0; i < E; i += 2) {
+      const int4 cs = base[i / 2];
+      const int32_t p0 = __shfl_xor_sync(kFullMask, v[i], D);
+      const int32_t p1 = __shfl_xor_sync(kFullMask, v[i + 1], D);
+      const uint32_t u0 = (uint32_t)cs.x * (uint32_t)v[i] + (uint32_t)cs.y * (uint32_t)p0 + half;
+      const uint32_t u1 =
+          (uint32_t)cs.z * (uint32_t)v[i + 1] + (uint32_t)cs.w * (uint32_t)p1 + half;
+      v[i] = (int32_t)u0 >> f;
+      v[i + 1] = (int32_t)u1 >> f;
+    }
+  }
+
+  template <int P>
+  __device__ __forceinline__ static void pass(int32_t (&v)[E], const int* rtab, int lane,
+                                              uint32_t half, int f) {
+    constexpr SetTableShape sh{LOG2N, LOG2E, 1, 0};
+    const int* row = rtab + sh.pass_offset(P);
+    if constexpr (P < LOG2E)
+      reg_pass<P>(v, row, lane, half, f);
+    else
+      lane_pass<P>(v, row, lane, half, f);
+  }
+
+  // All passes of one round: increasing p forward, decreasing p inverse.
+  template <int K>
+  __device__ __forceinline__ static void round(int32_t (&v)[E], const int* rtab, int lane,
+                                               uint32_t half, int f) {
+    if constexpr (K < LOG2N) {
+      pass<INV ? (LOG2N - 1 - K) : K>(v, rtab, lane, half, f);
+      round<K + 1>(v, rtab, lane, half, f);
+    }
+  }
+};
+
+template <int LOG2N, int KIND>
+__device__ __forceinline__ void batch_load(const BatchParams& p, long long b, int lane,
+                                           int32_t (&v)[BatchMath<LOG2N, false>::E]) {
+  constexpr int N = 1 << LOG2N;
+  constexpr int E = BatchMath<LOG2N, false>::E;
+  if constexpr (KIND == 0)
+    load_i16<E>(static_cast<const int16_t*>(p.in) + b * N + lane * E, v);
+  else
+    load_i32<E>(static_cast<const int32_t*>(p.in) + b * N + lane * E, v);
 }
 
-// One thread per block (E = N <= 64): every pass is a register pass.
-template <int LOG2N, bool INV>
-__device__ __forceinline__ void batch_round(int32_t (&v)[1 << LOG2N], const int4* row,
-                                            uint32_t half, int f) {
+template <int LOG2N, int KIND>
+__device__ __forceinline__ void batch_store(const BatchParams& p, long long b, int lane,
+                                            const int32_t (&v)[BatchMath<LOG2N, false>::E]) {
   constexpr int N = 1 << LOG2N;
-#pragma unroll
-  for (int pp = 0; pp < LOG2N; ++pp) {
-    const int p = INV ? (LOG2N - 1 - pp) : pp;
-    const int4* prow = row + p * (N / 2);
-#pragma unroll
-    for (int j = 0; j < N / 2; ++j) {
-      const int m = ((j >> p) << (p + 1)) | (j & ((1 << p) - 1));
-      const int n = m | (1 << p);
-      const int4 w = __ldg(prow + j);
-      gbfly<INV>(v[m], v[n], w, half, f);
+  constexpr int E = BatchMath<LOG2N, false>::E;
+  if constexpr (KIND == 0)
+    store_i32<E>(static_cast<int32_t*>(p.out) + b * N + lane * E, v);
+  else
+    store_i16_sat<E>(static_cast<int16_t*>(p.out) + b * N + lane * E, v);
+}
+
+// Gather offset i of a lane's permutation row (vector loads when aligned).
+template <int E>
+__device__ __forceinline__ int perm_at(const int* prow, int i) {
+  if constexpr (E % 4 == 0) {
+    const int4 q = reinterpret_cast<const int4*>(prow)[i / 4];
+    return (i & 3) == 0 ? q.x : (i & 3) == 1 ? q.y : (i & 3) == 2 ? q.z : q.w;
+  } else {
+    return prow[i];
+  }
+}
+
+// Bucket of a slot: the largest k with starts[k] <= slot (empty buckets share
+// their start with the next one, so the largest is non-empty).
+__device__ __forceinline__ int bucket_of_slot(const int* starts, int num_sets, int slot) {
+  int lo = 0, hi = num_sets + 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(starts + mid) <= slot) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// The tasks [t0, t1) of one warp.  `cache` holds the tables of sets
+// [set_lo, set_lo + cached count) when CACHED, else tables are read from
+// global memory.
+template <int LOG2N, int KIND, bool CACHED>
+__device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, long long t1,
+                                            const int* cache, int set_lo, int32_t* region) {
+  using M = BatchMath<LOG2N, KIND == 1>;
+  constexpr int E = M::E;
+  constexpr int L = M::L;
+  constexpr int G = 32 / L;
+  constexpr bool INV = (KIND == 1);
+  const int lane32 = threadIdx.x & 31;
+  const int lane = lane32 % L;
+  const int sub = lane32 / L;
+  const uint32_t half = 1u << (p.frac_bits - 1);
+  const int f = p.frac_bits;
+  const int R = p.rounds;
+  const int S = p.num_sets;
+  const SetTableShape sh{LOG2N, M::LOG2E, R, p.perms};
+  const int rw = sh.round_words();
+  char* rb = reinterpret_cast<char*>(region);  // this block's permutation region
+
+  int bucket = 0, bucket_end = 0;
+  for (long long t = t0; t < t1; ++t) {
+    const int slot = (int)(t * G);
+    if (slot >= bucket_end) {  // warp-uniform
+      bucket = bucket_of_slot(p.starts, S, slot);
+      bucket_end = __ldg(p.starts + bucket + 1);
     }
+    const int b = __ldg(p.order + slot + sub);
+    const bool active = b >= 0 && b < p.nblocks;
+    int32_t v[E];
+    if (active) {
+      batch_load<LOG2N, KIND>(p, b, lane, v);
+    } else {
+#pragma unroll
+      for (int i = 0; i < E; ++i) v[i] = 0;
+    }
+    if (bucket < S) {
+      const int* stab = CACHED ? cache + (size_t)(bucket - set_lo) * p.set_words
+                               : p.ktab + (size_t)bucket * p.set_words;
+      for (int rr = 0; rr < R; ++rr) {
+        const int r = INV ? (R - 1 - rr) : rr;
+        const bool has_perm = p.perms && ((p.perm_mask >> r) & 1u);
+        const int* prow = stab + sh.perm_offset(r) + lane * E;
+        if (INV && has_perm) {  // undo the gather of slot r: v_prev[perm[e]] = v[e]
+#pragma unroll
+          for (int i = 0; i < E; ++i) *reinterpret_cast<int32_t*>(rb + perm_at<E>(prow, i)) = v[i];
+          __syncwarp();
+#pragma unroll
+          for (int i = 0; i < E; ++i) v[i] = region[perm_word(lane * E + i)];
+          __syncwarp();
+        }
+        M::template round<0>(v, stab + r * rw, lane, half, f);
+        if (!INV && has_perm) {  // gather: v'[e] = v[perm[e]]
+#pragma unroll
+          for (int i = 0; i < E; ++i) region[perm_word(lane * E + i)] = v[i];
+          __syncwarp();
+#pragma unroll
+          for (int i = 0; i < E; ++i) v[i] = *reinterpret_cast<const int32_t*>(rb + perm_at<E>(prow, i));
+          __syncwarp();
+        }
+      }
+    } else if (bucket == S + 1) {  // bad set index: zeros, status
+#pragma unroll
+      for (int i = 0; i < E; ++i) v[i] = 0;
+      if (active && lane == 0 && p.status) atomicCAS(p.status, 0, 4);
+    }
+    if (active) batch_store<LOG2N, KIND>(p, b, lane, v);
   }
 }
 
 // KIND 0: int16 -> int32 forward; KIND 1: int32 -> int16 inverse.
 template <int LOG2N, int KIND>
-__global__ void __launch_bounds__(kBatchThreads) hygt_batch_kernel(BatchParams p) {
-  constexpr int N = 1 << LOG2N;
-  constexpr bool INV = (KIND == 1);
-  static_assert(LOG2N <= 6, "one thread per block up to N = 64");
-  extern __shared__ __align__(16) int32_t pscr[];  // [N][blockDim.x] permutation scratch
+__global__ void __launch_bounds__(kBatchThreads, 1) hygt_batch_kernel(BatchParams p) {
+  constexpr int G = batch_group(LOG2N);
+  constexpr int L = 32 / G;
+  constexpr int RW = perm_region_words(LOG2N);
+  extern __shared__ __align__(16) int32_t bsmem[];
 
-  // The schedule must have been built for this block count and set count.
-  if (p.meta[1] != (int)p.nblocks || p.meta[2] != p.num_sets) {
+  // The schedule must have been built for this block count, set count and G.
+  if (p.meta[1] != (int)p.nblocks || p.meta[2] != p.num_sets || p.meta[3] != G) {
     if (threadIdx.x == 0 && blockIdx.x == 0 && p.status) atomicCAS(p.status, 0, 1);
     return;
   }
-  const int ntasks = p.meta[0];
-  const int lane = threadIdx.x & 31;
-  const long long warps_total = (long long)gridDim.x * (blockDim.x >> 5);
-  const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const long long ntasks = max(0LL, min((long long)p.meta[0], p.tmax));
+  const int wpc = blockDim.x >> 5;
+  const long long warps_total = (long long)gridDim.x * wpc;
   const long long chunk = (ntasks + warps_total - 1) / warps_total;
-  const long long t0 = gw * chunk;
-  const long long t1 = min((long long)ntasks, t0 + chunk);
-  const uint32_t half = 1u << (p.frac_bits - 1);
-  const int f = p.frac_bits;
-  const int R = p.rounds;
-  const int S = p.num_sets;
-  int32_t* col = pscr + threadIdx.x;
-  const int T = blockDim.x;
+  const int warp = threadIdx.x >> 5;
+  const long long gw = (long long)blockIdx.x * wpc + warp;
+  const long long t0 = min(ntasks, gw * chunk);
+  const long long t1 = min(ntasks, t0 + chunk);
 
-  // Bucket of the first task: the largest k with starts[k] <= slot (empty
-  // buckets share their start with the next one, so the largest is non-empty).
-  int bucket = 0, bucket_end = 0;
-  for (long long t = t0; t < t1; ++t) {
-    const int slot = (int)(t * 32);
-    if (slot >= bucket_end) {  // warp-uniform
-      int lo = 0, hi = S + 1;  // search over buckets 0..S+1
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(p.starts + mid) <= slot) lo = mid; else hi = mid - 1;
-      }
-      bucket = lo;
-      bucket_end = __ldg(p.starts + bucket + 1);
-    }
-    const int b = __ldg(p.order + t * 32 + lane);
-    const bool active = b >= 0 && b < p.nblocks;
-    int32_t v[N];
-    if (active) {
-      if constexpr (KIND == 0)
-        load_i16<N>(static_cast<const int16_t*>(p.in) + (long long)b * N, v);
-      else
-        load_i32<N>(static_cast<const int32_t*>(p.in) + (long long)b * N, v);
-    } else {
-#pragma unroll
-      for (int i = 0; i < N; ++i) v[i] = 0;
-    }
-    if (bucket < S) {
-      const int4* tab = p.gtab + (size_t)bucket * R * LOG2N * (N / 2);
-      const int* poff = p.poff ? p.poff + (size_t)bucket * R * N : nullptr;
-      for (int rr = 0; rr < R; ++rr) {
-        const int r = INV ? (R - 1 - rr) : rr;
-        const bool has_perm = poff && ((p.perm_mask >> r) & 1u);
-        if (INV && has_perm) {  // undo the gather of slot r: v_prev[perm[i]] = v[i]
-#pragma unroll
-          for (int i = 0; i < N; ++i) col[__ldg(poff + r * N + i) * T] = v[i];
-#pragma unroll
-          for (int i = 0; i < N; ++i) v[i] = col[i * T];
-        }
-        batch_round<LOG2N, INV>(v, tab + (size_t)r * LOG2N * (N / 2), half, f);
-        if (!INV && has_perm) {  // gather: v'[i] = v[perm[i]]
-#pragma unroll
-          for (int i = 0; i < N; ++i) col[i * T] = v[i];
-#pragma unroll
-          for (int i = 0; i < N; ++i) v[i] = col[__ldg(poff + r * N + i) * T];
-        }
-      }
-    } else if (bucket == S + 1) {  // bad set index: zeros, status
-#pragma unroll
-      for (int i = 0; i < N; ++i) v[i] = 0;
-      if (active && p.status) atomicCAS(p.status, 0, 4);
-    }
-    if (active) {
-      if constexpr (KIND == 0)
-        store_i32<N>(static_cast<int32_t*>(p.out) + (long long)b * N, v);
-      else
-        store_i16_sat<N>(static_cast<int16_t*>(p.out) + (long long)b * N, v);
-    }
+  // Sets spanned by this CTA's tasks (consecutive in the sorted order).
+  const long long c0 = min(ntasks, (long long)blockIdx.x * wpc * chunk);
+  const long long c1 = min(ntasks, c0 + (long long)wpc * chunk);
+  int set_lo = 0, ncache = 0;
+  if (c1 > c0) {
+    const int bk_lo = bucket_of_slot(p.starts, p.num_sets, (int)(c0 * G));
+    const int bk_hi = bucket_of_slot(p.starts, p.num_sets, (int)(c1 * G - 1));
+    set_lo = min(bk_lo, p.num_sets);
+    const int set_hi = min(bk_hi, p.num_sets - 1);
+    ncache = set_hi >= set_lo ? set_hi - set_lo + 1 : 0;
   }
+  const bool cached = ncache <= p.max_cached_sets;
+  int32_t* cache = bsmem;
+  int32_t* pbuf = bsmem + (size_t)p.max_cached_sets * p.set_words;
+  if (cached && ncache > 0) {
+    const int4* src = reinterpret_cast<const int4*>(p.ktab + (size_t)set_lo * p.set_words);
+    int4* dst = reinterpret_cast<int4*>(cache);
+    const int n4 = ncache * p.set_words / 4;
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) dst[i] = __ldg(src + i);
+  }
+  __syncthreads();
+
+  int32_t* region = pbuf + (size_t)(warp * G + (threadIdx.x & 31) / L) * RW;
+  if (cached)
+    batch_tasks<LOG2N, KIND, true>(p, t0, t1, cache, set_lo, region);
+  else
+    batch_tasks<LOG2N, KIND, false>(p, t0, t1, cache, set_lo, region);
 }
 
-}  // namespace hygt
-
-namespace hygt {
 // Host launchers (batch_int.cu).
-cudaError_t batch_build(const uint16_t* d_set, long long nblocks, int num_sets, void* d_work,
-                        cudaStream_t stream);
-cudaError_t launch_batch_fwd(int log2n, const BatchParams& p, bool perms, long long nblocks,
-                             cudaStream_t stream);
-cudaError_t launch_batch_inv(int log2n, const BatchParams& p, bool perms, long long nblocks,
-                             cudaStream_t stream);
+cudaError_t batch_build(const uint16_t* d_set, long long nblocks, int num_sets, int group,
+                        void* d_work, cudaStream_t stream);
+cudaError_t launch_batch_fwd(int log2n, const BatchParams& p, cudaStream_t stream);
+cudaError_t launch_batch_inv(int log2n, const BatchParams& p, cudaStream_t stream);
+
 }  // namespace hygt

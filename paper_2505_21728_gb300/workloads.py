@@ -79,6 +79,13 @@ _REGISTRY = {
 }
 
 
+def truncated(w: Workload, nblocks: int) -> Workload:
+    """The first nblocks blocks of a workload (same parameters and seeds)."""
+    import dataclasses
+    n = min(int(nblocks), w.nblocks)
+    return dataclasses.replace(w, name="%s[:%d]" % (w.name, n), nblocks=n)
+
+
 def get(name: str) -> Workload:
     return _REGISTRY[name]
 

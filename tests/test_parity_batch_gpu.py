@@ -26,7 +26,7 @@ def run_batch(gpu, log2n, rounds, q, perms, x, sets):
     return y.cpu().numpy(), xr.cpu().numpy(), int(st.item())
 
 
-@pytest.mark.parametrize("log2n", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("log2n", [1, 2, 3, 4, 5, 6, 7, 8])
 @pytest.mark.parametrize("rounds,perm_kind", [(1, "none"), (2, "between"), (3, "all")])
 def test_batch_parity(gpu, orc, log2n, rounds, perm_kind):
     N = 1 << log2n
@@ -70,6 +70,34 @@ def test_batch_no_sets_one_set(gpu, orc):
     ye, _ = orc.fwd_int(x, q, log2n, rounds, perms)
     xe, _ = orc.inv_int(ye, q, log2n, rounds, perms)
     assert st == 0 and np.array_equal(y, ye) and np.array_equal(xr, xe)
+
+
+def test_batch_many_sets_uncached(gpu, orc):
+    """Few blocks per set: a CTA's tasks span more sets than fit in shared
+    memory, so the kernel reads the multipliers from global memory."""
+    log2n, rounds, S = 8, 3, 600
+    q = inputs.angle_indices(S, rounds, log2n, seed=9)
+    perms = inputs.permutations(S, rounds, 256, seed=9)
+    B = 3000
+    x = inputs.laplacian_blocks(B, 256, 30.0, -2048, 2047, seed=9)
+    sets = inputs.set_indices(B, S, seed=9)
+    y, xr, st = run_batch(gpu, log2n, rounds, q, perms, x, sets)
+    ye, _ = orc.fwd_int(x, q, log2n, rounds, perms, sets)
+    xe, _ = orc.inv_int(ye, q, log2n, rounds, perms, sets)
+    assert st == 0 and np.array_equal(y, ye) and np.array_equal(xr, xe)
+
+
+def test_batch_max_rounds_extremes(gpu, orc):
+    log2n, rounds, S = 8, 8, 3
+    q = inputs.angle_indices(S, rounds, log2n, seed=5)
+    perms = inputs.permutations(S, rounds, 256, seed=5, between_rounds_only=False)
+    rng = np.random.default_rng(1)
+    x = rng.choice(np.array([-32768, 32767], np.int16), size=(100, 256))
+    sets = (np.arange(100) % S).astype(np.uint16)
+    y, xr, st = run_batch(gpu, log2n, rounds, q, perms, x, sets)
+    ye, ste = orc.fwd_int(x, q, log2n, rounds, perms, sets)
+    xe, _ = orc.inv_int(ye, q, log2n, rounds, perms, sets)
+    assert st == 0 and ste == 0 and np.array_equal(y, ye) and np.array_equal(xr, xe)
 
 
 def test_batch_schedule_size_mismatch_reports(gpu):
