@@ -164,6 +164,54 @@ hygt_status hygt_inverse_batch(hygt_plan plan, const void *d_work, const int32_t
                                int16_t *d_x, int64_t nblocks, hygt_stream stream,
                                int *d_status);
 
+/*
+ * Mixed block sizes in one persistent launch.  The paper's codec applies
+ * 4x4 (N = 16) and 8x8 (N = 64) secondary transforms (Sec. VI); a frame
+ * tiled into 4x4, 8x8 and 16x16 blocks gives one batch per block size, each
+ * with its own plan, set indices and schedule.  One launch transforms all of
+ * them: the CTAs of the launch are split among the classes (`ctas` per
+ * class, all > 0 and summing to at most 4 * hygt_mixed_ctas(); otherwise a
+ * split proportional to an estimate of each class's cost is used).
+ *
+ * Each class: plan = integer plan with N = 16, 64 or 256 (others return
+ * HYGT_ERR_UNSUPPORTED); d_set, nblocks, d_work / work_bytes as for
+ * hygt_batch_build; d_x int16 [nblocks][N] forward input, d_y int32
+ * [nblocks][N] coefficients (forward output, inverse input), d_xr int16
+ * [nblocks][N] inverse output.  Data pointers 16-byte aligned.
+ *
+ *   hygt_forward_mixed / hygt_inverse_mixed  one launch over all classes,
+ *        async on stream, with schedules already built (hygt_batch_build).
+ *   hygt_mixed_graph_create  captures one whole step -- the schedules of
+ *        all classes, the mixed forward, the mixed inverse -- into a CUDA
+ *        graph (on a private stream; pointers and sizes are fixed at
+ *        capture).  hygt_graph_launch replays it on `stream`;
+ *        hygt_graph_destroy frees it.
+ *   hygt_mixed_ctas  CTAs of one mixed launch on the current device.
+ */
+typedef struct hygt_mixed_class {
+  hygt_plan plan;
+  const uint16_t *d_set;
+  int64_t nblocks;
+  void *d_work;
+  size_t work_bytes;
+  const int16_t *d_x;
+  int32_t *d_y;
+  int16_t *d_xr;
+  int ctas;
+} hygt_mixed_class;
+
+typedef struct hygt_graph_s *hygt_graph;
+
+int hygt_mixed_ctas(void);
+hygt_status hygt_forward_mixed(const hygt_mixed_class *classes, int nclasses,
+                               hygt_stream stream, int *d_status);
+hygt_status hygt_inverse_mixed(const hygt_mixed_class *classes, int nclasses,
+                               hygt_stream stream, int *d_status);
+hygt_status hygt_mixed_graph_create(hygt_graph *out, const hygt_mixed_class *classes,
+                                    int nclasses, int *d_status);
+hygt_status hygt_graph_launch(hygt_graph graph, hygt_stream stream);
+void hygt_graph_destroy(hygt_graph graph);
+
 /* Plan shape: any out-pointer may be NULL. */
 hygt_status hygt_plan_info(hygt_plan plan, int *log2n, int *rounds, int *num_sets,
                            int *is_float);

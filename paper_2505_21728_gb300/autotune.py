@@ -1,0 +1,139 @@
+"""Autotuner of the mixed-size launch.
+
+The mixed kernel runs every block-size class on its own share of the CTAs
+(one CTA per SM), so the launch ends when the slowest class ends.  The tuner
+picks the split of the CTAs among the classes:
+
+1. time each class alone on all CTAs (t_c);
+2. start from the split proportional to t_c (equal finishing times if each
+   class scales linearly with its CTAs);
+3. local search: move k CTAs between any two classes (k halving down to 1)
+   while the measured forward + inverse time improves.
+
+Results are cached in a JSON file keyed by the GPU name and the classes'
+shapes (block size, rounds, sets, block count).
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+import statistics
+
+from . import hygt
+
+
+def _cache_path():
+    return os.environ.get("HYGT_AUTOTUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "hygt_autotune.json"))
+
+
+def _key(mb):
+    import torch
+    dev = torch.cuda.get_device_name()
+    shapes = []
+    for e in mb.entries:
+        p = e["plan"]
+        shapes.append("N%d_R%d_S%d_B%d" % (p.N, p.rounds, p.num_sets, int(e["x"].shape[0])))
+    return dev + "|" + ",".join(shapes)
+
+
+def _time_pair(classes, n, reps):
+    """Median time (ms) of one mixed forward + one mixed inverse launch."""
+    import torch
+    stream = torch.cuda.current_stream()
+    h = stream.cuda_stream
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    hygt._check(hygt.hygt_forward_mixed(classes, n, h, None), "hygt_forward_mixed")
+    hygt._check(hygt.hygt_inverse_mixed(classes, n, h, None), "hygt_inverse_mixed")
+    times = []
+    for _ in range(reps):
+        a.record(stream)
+        hygt._check(hygt.hygt_forward_mixed(classes, n, h, None), "hygt_forward_mixed")
+        hygt._check(hygt.hygt_inverse_mixed(classes, n, h, None), "hygt_inverse_mixed")
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    return statistics.median(times)
+
+
+def _with_split(mb, split):
+    arr = (hygt.MixedClass * mb.n)()
+    for i in range(mb.n):
+        arr[i] = mb.classes[i]
+        arr[i].ctas = int(split[i])
+    return arr
+
+
+def tune_split(mb, reps=5, use_cache=True, verbose=False):
+    """Returns the tuned CTA split (list, one entry per class) and applies it
+    to ``mb``.  ``mb`` must have its schedules built."""
+    key = _key(mb)
+    path = _cache_path()
+    cache = {}
+    if use_cache and os.path.exists(path):
+        try:
+            with open(path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+    if use_cache and key in cache:
+        split = cache[key]["split"]
+        mb.set_split(split)
+        return split
+
+    G = hygt.hygt_mixed_ctas()
+    active = [i for i in range(mb.n) if mb.classes[i].nblocks > 0]
+    if len(active) <= 1 or G < len(active):
+        split = [G if i in active else 0 for i in range(mb.n)]
+        mb.set_split(split)
+        return split
+
+    # 1. each class alone on all CTAs
+    alone = {}
+    for i in active:
+        one = (hygt.MixedClass * 1)()
+        one[0] = mb.classes[i]
+        one[0].ctas = G
+        alone[i] = _time_pair(one, 1, reps)
+    # 2. proportional split
+    tot = sum(alone.values())
+    split = [0] * mb.n
+    for i in active:
+        split[i] = max(1, int(round(G * alone[i] / tot)))
+    big = max(active, key=lambda i: alone[i])
+    split[big] += G - sum(split)
+    best = _time_pair(_with_split(mb, split), mb.n, reps)
+    trials = [(list(split), best)]
+    # 3. local search
+    step = max(1, G // 16)
+    while step >= 1:
+        improved = True
+        while improved:
+            improved = False
+            for a in active:
+                for b in active:
+                    if a == b or split[a] - step < 1:
+                        continue
+                    cand = list(split)
+                    cand[a] -= step
+                    cand[b] += step
+                    t = _time_pair(_with_split(mb, cand), mb.n, reps)
+                    trials.append((cand, t))
+                    if t < best * 0.995:
+                        best, split, improved = t, cand, True
+        step //= 2
+    if verbose:
+        print("autotune: alone", alone, "best", split, "%.4f ms" % best)
+    mb.set_split(split)
+    if use_cache:
+        cache[key] = {"split": split, "ms": best, "alone_ms": {str(k): v for k, v in alone.items()},
+                      "trials": len(trials)}
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            with open(path, "w") as f:
+                json.dump(cache, f, indent=1)
+        except OSError:
+            pass
+    return split

@@ -163,7 +163,7 @@ static cudaError_t launch_batch_sized(BatchParams p, cudaStream_t stream) {
   if (err != cudaSuccess) return err;
   const DeviceInfo info = device_info(dev);
   constexpr int G = batch_group(LOG2N);
-  const size_t pbuf = (size_t)(kBatchThreads / 32) * G * perm_region_words(LOG2N) * 4;
+  const size_t pbuf = batch_pbuf_bytes<LOG2N>(kBatchThreads);
   const size_t set_bytes = (size_t)p.set_words * 4;
   long long fit = ((long long)info.max_smem_optin - (long long)pbuf) / (long long)set_bytes;
   if (fit > 64) fit = 64;

@@ -11,6 +11,7 @@
 
 #include "../../include/hygt.h"
 #include "hygt_batch.cuh"
+#include "hygt_mixed.cuh"
 #include "hygt_launch.cuh"
 
 struct hygt_plan_s {
@@ -119,9 +120,10 @@ hygt_status upload_perms(hygt_plan p, const std::vector<uint8_t>& perm, unsigned
 }
 
 // Per-set tables of the batch kernels (layout: hygt::SetTableShape).  Register
-// passes store (c, s - c, -(c + s)); lane passes store (c, s) for the m sides
-// then (c, -s) for the n sides; then the permutation gather sources as byte
-// offsets in a block's permutation region.
+// passes store (c, s - c, -(c + s)); lane passes store (c, s) for the m side
+// and (c, -s) for the n side of each pair, in alternating 16-byte chunks of
+// two pairs; then the permutation gather sources as byte offsets in a
+// block's permutation region.
 void build_ktab(int log2n, int rounds, int num_sets, const uint8_t* q, const std::vector<int>& ct,
                 const std::vector<int>& st, const std::vector<uint8_t>& perm, unsigned mask,
                 std::vector<int>* out, int* words) {
@@ -142,11 +144,12 @@ void build_ktab(int log2n, int rounds, int num_sets, const uint8_t* q, const std
             row[3 * j] = c;
             row[3 * j + 1] = sn - c;
             row[3 * j + 2] = -(c + sn);
-          } else {
-            row[2 * j] = c;  // m side
-            row[2 * j + 1] = sn;
-            row[N + 2 * j] = c;  // n side
-            row[N + 2 * j + 1] = -sn;
+          } else {  // chunk 2 (j/2) + side holds pairs j & ~1, j | 1 of that side
+            const int w0 = 8 * (j >> 1) + 2 * (j & 1);
+            row[w0] = c;  // m side
+            row[w0 + 1] = sn;
+            row[w0 + 4] = c;  // n side
+            row[w0 + 5] = -sn;
           }
         }
       }
@@ -361,12 +364,8 @@ hygt_status hygt_batch_build(hygt_plan plan, const uint16_t* d_set, int64_t nblo
       hygt::batch_build(d_set, nblocks, plan->num_sets, group, d_work, (cudaStream_t)stream));
 }
 
-static hygt_status batch_call(hygt_plan plan, const void* d_work, const void* in, void* out,
-                              int64_t nblocks, hygt_stream stream, int* d_status, bool inverse) {
-  hygt_status s = check_io(plan, in, out, nblocks);
-  if (s != HYGT_OK || nblocks == 0) return s;
-  if (plan->is_float) return HYGT_ERR_UNSUPPORTED;
-  if (!d_work || !aligned16(d_work) || nblocks > kBatchMaxBlocks) return HYGT_ERR_ARG;
+static hygt::BatchParams make_batch_params(hygt_plan plan, const void* d_work, const void* in,
+                                           void* out, int64_t nblocks, int* d_status) {
   const hygt::BatchLayout L =
       hygt::batch_layout(plan->num_sets, nblocks, hygt::batch_group(plan->log2n));
   const char* w = static_cast<const char*>(d_work);
@@ -386,6 +385,16 @@ static hygt_status batch_call(hygt_plan plan, const void* d_work, const void* in
   p.num_sets = plan->num_sets;
   p.frac_bits = plan->frac_bits;
   p.status = d_status;
+  return p;
+}
+
+static hygt_status batch_call(hygt_plan plan, const void* d_work, const void* in, void* out,
+                              int64_t nblocks, hygt_stream stream, int* d_status, bool inverse) {
+  hygt_status s = check_io(plan, in, out, nblocks);
+  if (s != HYGT_OK || nblocks == 0) return s;
+  if (plan->is_float) return HYGT_ERR_UNSUPPORTED;
+  if (!d_work || !aligned16(d_work) || nblocks > kBatchMaxBlocks) return HYGT_ERR_ARG;
+  const hygt::BatchParams p = make_batch_params(plan, d_work, in, out, nblocks, d_status);
   cudaError_t e = inverse ? hygt::launch_batch_inv(plan->log2n, p, (cudaStream_t)stream)
                           : hygt::launch_batch_fwd(plan->log2n, p, (cudaStream_t)stream);
   return to_status(e);
@@ -399,6 +408,142 @@ hygt_status hygt_forward_batch(hygt_plan plan, const void* d_work, const int16_t
 hygt_status hygt_inverse_batch(hygt_plan plan, const void* d_work, const int32_t* d_y, int16_t* d_x,
                                int64_t nblocks, hygt_stream stream, int* d_status) {
   return batch_call(plan, d_work, d_y, d_x, nblocks, stream, d_status, true);
+}
+
+int hygt_mixed_ctas(void) { return hygt::mixed_grid_ctas(); }
+
+// Validates the classes of a mixed launch and fills the kernel parameters.
+static hygt_status mixed_params(const hygt_mixed_class* cls, int nclasses, bool inverse,
+                                int* d_status, hygt::MixedParams* mp) {
+  if (!cls || nclasses < 1 || nclasses > hygt::kMaxMixedClasses) return HYGT_ERR_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HYGT_ERR_CUDA;
+  *mp = hygt::MixedParams{};
+  mp->nclasses = nclasses;
+  double cost[hygt::kMaxMixedClasses] = {0, 0, 0};
+  double total_cost = 0;
+  bool explicit_split = true;
+  int explicit_sum = 0;
+  for (int c = 0; c < nclasses; ++c) {
+    const hygt_mixed_class& k = cls[c];
+    hygt_plan plan = k.plan;
+    if (!plan || plan->is_float) return plan ? HYGT_ERR_UNSUPPORTED : HYGT_ERR_ARG;
+    if (plan->log2n != 4 && plan->log2n != 6 && plan->log2n != 8) return HYGT_ERR_UNSUPPORTED;
+    if (plan->device != dev || k.nblocks < 0 || k.nblocks > kBatchMaxBlocks) return HYGT_ERR_ARG;
+    const void* in = inverse ? (const void*)k.d_y : (const void*)k.d_x;
+    void* out = inverse ? (void*)k.d_xr : (void*)k.d_y;
+    if (k.nblocks > 0) {
+      if (!in || !out || !aligned16(in) || !aligned16(out) || !k.d_work || !aligned16(k.d_work))
+        return HYGT_ERR_ARG;
+      const int group = hygt::batch_group(plan->log2n);
+      if (k.work_bytes < hygt::batch_layout(plan->num_sets, k.nblocks, group).total)
+        return HYGT_ERR_ARG;
+    }
+    mp->cls[c] = make_batch_params(plan, k.d_work, in, out, k.nblocks, d_status);
+    mp->log2n[c] = plan->log2n;
+    const double N = (double)(1 << plan->log2n);
+    // relative cost: memory traffic plus butterfly work
+    cost[c] = (double)k.nblocks * N * (6.0 + 0.5 * plan->rounds * plan->log2n);
+    total_cost += cost[c];
+    if (k.ctas <= 0) explicit_split = false;
+    explicit_sum += k.ctas > 0 ? k.ctas : 0;
+  }
+  const int grid = hygt::mixed_grid_ctas();
+  if (grid < 1) return HYGT_ERR_CUDA;
+  int n[hygt::kMaxMixedClasses] = {0, 0, 0};
+  if (explicit_split && explicit_sum <= 4 * grid) {
+    for (int c = 0; c < nclasses; ++c) n[c] = cls[c].ctas;
+  } else if (total_cost > 0) {
+    int given = 0;
+    for (int c = 0; c < nclasses; ++c) {
+      n[c] = cls[c].nblocks > 0 ? (int)(grid * cost[c] / total_cost) : 0;
+      if (cls[c].nblocks > 0 && n[c] < 1) n[c] = 1;
+      given += n[c];
+    }
+    // hand the rounding remainder to the most expensive class
+    int big = 0;
+    for (int c = 1; c < nclasses; ++c)
+      if (cost[c] > cost[big]) big = c;
+    n[big] += grid - given;
+    if (n[big] < 1) n[big] = 1;
+  }
+  mp->cta_begin[0] = 0;
+  for (int c = 0; c < nclasses; ++c) mp->cta_begin[c + 1] = mp->cta_begin[c] + n[c];
+  return HYGT_OK;
+}
+
+static hygt_status mixed_call(const hygt_mixed_class* cls, int nclasses, hygt_stream stream,
+                              int* d_status, bool inverse) {
+  hygt::MixedParams mp;
+  hygt_status s = mixed_params(cls, nclasses, inverse, d_status, &mp);
+  if (s != HYGT_OK) return s;
+  return to_status(hygt::launch_mixed(inverse ? 1 : 0, mp, (cudaStream_t)stream));
+}
+
+hygt_status hygt_forward_mixed(const hygt_mixed_class* classes, int nclasses, hygt_stream stream,
+                               int* d_status) {
+  return mixed_call(classes, nclasses, stream, d_status, false);
+}
+
+hygt_status hygt_inverse_mixed(const hygt_mixed_class* classes, int nclasses, hygt_stream stream,
+                               int* d_status) {
+  return mixed_call(classes, nclasses, stream, d_status, true);
+}
+
+struct hygt_graph_s {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+hygt_status hygt_mixed_graph_create(hygt_graph* out, const hygt_mixed_class* classes, int nclasses,
+                                    int* d_status) {
+  if (!out) return HYGT_ERR_ARG;
+  *out = nullptr;
+  hygt::MixedParams fwd, inv;
+  hygt_status s = mixed_params(classes, nclasses, false, d_status, &fwd);
+  if (s == HYGT_OK) s = mixed_params(classes, nclasses, true, d_status, &inv);
+  if (s != HYGT_OK) return s;
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return HYGT_ERR_CUDA;
+  hygt_graph g = new (std::nothrow) hygt_graph_s();
+  if (!g) {
+    cudaStreamDestroy(cs);
+    return HYGT_ERR_OOM;
+  }
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  for (int c = 0; c < nclasses && e == cudaSuccess; ++c) {
+    const hygt_mixed_class& k = classes[c];
+    if (k.nblocks > 0)
+      e = hygt::batch_build(k.d_set, k.nblocks, k.plan->num_sets, hygt::batch_group(k.plan->log2n),
+                            k.d_work, cs);
+  }
+  if (e == cudaSuccess) e = hygt::launch_mixed(0, fwd, cs);
+  if (e == cudaSuccess) e = hygt::launch_mixed(1, inv, cs);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, graph, 0);
+  g->graph = graph;
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    hygt_graph_destroy(g);
+    cudaGetLastError();
+    return HYGT_ERR_CUDA;
+  }
+  *out = g;
+  return HYGT_OK;
+}
+
+hygt_status hygt_graph_launch(hygt_graph graph, hygt_stream stream) {
+  if (!graph || !graph->exec) return HYGT_ERR_ARG;
+  return to_status(cudaGraphLaunch(graph->exec, (cudaStream_t)stream));
+}
+
+void hygt_graph_destroy(hygt_graph graph) {
+  if (!graph) return;
+  if (graph->exec) cudaGraphExecDestroy(graph->exec);
+  if (graph->graph) cudaGraphDestroy(graph->graph);
+  delete graph;
 }
 
 hygt_status hygt_plan_info(hygt_plan plan, int* log2n, int* rounds, int* num_sets, int* is_float) {

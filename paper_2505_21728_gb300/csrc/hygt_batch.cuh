@@ -79,8 +79,9 @@ __host__ __device__ inline BatchLayout batch_layout(int num_sets, long long nblo
 // size 2^LOG2N and LOG2E = batch_log2e(LOG2N):
 //   for each round r, for each pass p:
 //     p <  LOG2E: N/2 entries (c, s - c, -(c + s))       (3 words)
-//     p >= LOG2E: N/2 entries (c, s) for the m side of each pair, then
-//                 N/2 entries (c, -s) for the n side     (2 + 2 words)
+//     p >= LOG2E: for each pair j, (c, s) for its m side and (c, -s) for
+//                 its n side, laid out so that 16-byte chunk 2 (j/2) + side
+//                 holds pairs j & ~1 and j | 1 of that side (2 + 2 words)
 //   then, if the plan permutes, for each round r: N byte offsets of the
 //   gather source of element i in a block's permutation region.
 struct SetTableShape {
@@ -172,9 +173,11 @@ struct BatchMath {
     }
   }
 
-  // Lane pass p: partner lane = lane ^ 2^(p - LOG2E).  `row` holds the N/2
-  // (c, s) entries of the m sides, then the N/2 (c, -s) entries of the n
-  // sides; this lane's E elements use pairs jbase + i of its side.
+  // Lane pass p: partner lane = lane ^ 2^(p - LOG2E).  `row` holds (c, s)
+  // for the m side and (c, -s) for the n side of each pair, two pairs of one
+  // side per 16-byte chunk, the sides alternating chunk by chunk (so the two
+  // lanes of a pair read different banks); this lane's E elements use pairs
+  // jbase + i of its side.
   template <int P>
   __device__ __forceinline__ static void lane_pass(int32_t (&v)[E], const int* row, int lane,
                                                    uint32_t half, int f) {
@@ -184,10 +187,10 @@ struct BatchMath {
     const int jbase = ((lane >> (Q + 1)) << P) + ((lane & (D - 1)) << LOG2E);
     // forward: m side (c, s), n side (c, -s); inverse: the opposite
     const int side = upper ^ (INV ? 1 : 0);
-    const int4* base = reinterpret_cast<const int4*>(row + side * N + 2 * jbase);
+    const int4* base = reinterpret_cast<const int4*>(row + 4 * jbase + 4 * side);
 #pragma unroll
     for (int i = 0; i < E; i += 2) {
-      const int4 cs = base[i / 2];
+      const int4 cs = base[i];  // chunk 2 ((jbase + i) / 2) + side
       const int32_t p0 = __shfl_xor_sync(kFullMask, v[i], D);
       const int32_t p1 = __shfl_xor_sync(kFullMask, v[i + 1], D);
       const uint32_t u0 = (uint32_t)cs.x * (uint32_t)v[i] + (uint32_t)cs.y * (uint32_t)p0 + half;
@@ -336,30 +339,33 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
   }
 }
 
+// One CTA's share of a bucketed batch: CTA `cta` of `ncta` walks a contiguous
+// range of warp tasks.  `smem` is the dynamic shared memory: the cached set
+// tables (max_cached_sets x set_words) followed by the permutation buffer.
 // KIND 0: int16 -> int32 forward; KIND 1: int32 -> int16 inverse.
 template <int LOG2N, int KIND>
-__global__ void __launch_bounds__(kBatchThreads, 1) hygt_batch_kernel(BatchParams p) {
+__device__ __forceinline__ void batch_cta(const BatchParams& p, long long cta, long long ncta,
+                                          int32_t* smem) {
   constexpr int G = batch_group(LOG2N);
   constexpr int L = 32 / G;
   constexpr int RW = perm_region_words(LOG2N);
-  extern __shared__ __align__(16) int32_t bsmem[];
 
   // The schedule must have been built for this block count, set count and G.
   if (p.meta[1] != (int)p.nblocks || p.meta[2] != p.num_sets || p.meta[3] != G) {
-    if (threadIdx.x == 0 && blockIdx.x == 0 && p.status) atomicCAS(p.status, 0, 1);
+    if (threadIdx.x == 0 && cta == 0 && p.status) atomicCAS(p.status, 0, 1);
     return;
   }
   const long long ntasks = max(0LL, min((long long)p.meta[0], p.tmax));
   const int wpc = blockDim.x >> 5;
-  const long long warps_total = (long long)gridDim.x * wpc;
+  const long long warps_total = ncta * wpc;
   const long long chunk = (ntasks + warps_total - 1) / warps_total;
   const int warp = threadIdx.x >> 5;
-  const long long gw = (long long)blockIdx.x * wpc + warp;
+  const long long gw = cta * wpc + warp;
   const long long t0 = min(ntasks, gw * chunk);
   const long long t1 = min(ntasks, t0 + chunk);
 
   // Sets spanned by this CTA's tasks (consecutive in the sorted order).
-  const long long c0 = min(ntasks, (long long)blockIdx.x * wpc * chunk);
+  const long long c0 = min(ntasks, cta * wpc * chunk);
   const long long c1 = min(ntasks, c0 + (long long)wpc * chunk);
   int set_lo = 0, ncache = 0;
   if (c1 > c0) {
@@ -370,8 +376,8 @@ __global__ void __launch_bounds__(kBatchThreads, 1) hygt_batch_kernel(BatchParam
     ncache = set_hi >= set_lo ? set_hi - set_lo + 1 : 0;
   }
   const bool cached = ncache <= p.max_cached_sets;
-  int32_t* cache = bsmem;
-  int32_t* pbuf = bsmem + (size_t)p.max_cached_sets * p.set_words;
+  int32_t* cache = smem;
+  int32_t* pbuf = smem + (size_t)p.max_cached_sets * p.set_words;
   if (cached && ncache > 0) {
     const int4* src = reinterpret_cast<const int4*>(p.ktab + (size_t)set_lo * p.set_words);
     int4* dst = reinterpret_cast<int4*>(cache);
@@ -385,6 +391,19 @@ __global__ void __launch_bounds__(kBatchThreads, 1) hygt_batch_kernel(BatchParam
     batch_tasks<LOG2N, KIND, true>(p, t0, t1, cache, set_lo, region);
   else
     batch_tasks<LOG2N, KIND, false>(p, t0, t1, cache, set_lo, region);
+}
+
+// Dynamic shared memory of batch_cta for block size 2^LOG2N: permutation
+// buffer plus `cached_sets` set tables of `set_words` words.
+template <int LOG2N>
+__host__ __device__ inline size_t batch_pbuf_bytes(int threads) {
+  return (size_t)(threads / 32) * batch_group(LOG2N) * perm_region_words(LOG2N) * 4;
+}
+
+template <int LOG2N, int KIND>
+__global__ void __launch_bounds__(kBatchThreads, 1) hygt_batch_kernel(BatchParams p) {
+  extern __shared__ __align__(16) int32_t bsmem[];
+  batch_cta<LOG2N, KIND>(p, blockIdx.x, gridDim.x, bsmem);
 }
 
 // Host launchers (batch_int.cu).

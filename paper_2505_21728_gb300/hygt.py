@@ -32,6 +32,14 @@ class HygtError(RuntimeError):
         super().__init__("%s: %s (status %d)" % (where, hygt_status_string(code), code))
 
 
+class MixedClass(ctypes.Structure):
+    """hygt_mixed_class of include/hygt.h."""
+    _fields_ = [("plan", ctypes.c_void_p), ("d_set", ctypes.c_void_p),
+                ("nblocks", ctypes.c_int64), ("d_work", ctypes.c_void_p),
+                ("work_bytes", ctypes.c_size_t), ("d_x", ctypes.c_void_p),
+                ("d_y", ctypes.c_void_p), ("d_xr", ctypes.c_void_p), ("ctas", ctypes.c_int)]
+
+
 def _load() -> ctypes.CDLL:
     if not os.path.exists(SO):
         raise ImportError("libhygt.so is not built (%s); run "
@@ -56,6 +64,18 @@ def _load() -> ctypes.CDLL:
         f = getattr(L, name)
         f.argtypes = [P, P, P, P, i64, P, P]
         f.restype = i32
+    L.hygt_mixed_ctas.argtypes = []
+    L.hygt_mixed_ctas.restype = i32
+    for name in ("hygt_forward_mixed", "hygt_inverse_mixed"):
+        f = getattr(L, name)
+        f.argtypes = [ctypes.POINTER(MixedClass), i32, P, P]
+        f.restype = i32
+    L.hygt_mixed_graph_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(MixedClass), i32, P]
+    L.hygt_mixed_graph_create.restype = i32
+    L.hygt_graph_launch.argtypes = [P, P]
+    L.hygt_graph_launch.restype = i32
+    L.hygt_graph_destroy.argtypes = [P]
+    L.hygt_graph_destroy.restype = None
     L.hygt_plan_info.argtypes = [P] + [ctypes.POINTER(i32)] * 4
     L.hygt_plan_info.restype = i32
     L.hygt_param_bytes.argtypes = [i32, i32, i32]
@@ -138,6 +158,32 @@ def hygt_forward_batch(plan, d_work, d_x, d_y, nblocks, stream, d_status):
 
 def hygt_inverse_batch(plan, d_work, d_y, d_x, nblocks, stream, d_status):
     return int(_lib.hygt_inverse_batch(plan, d_work, d_y, d_x, nblocks, stream, d_status))
+
+
+def hygt_mixed_ctas():
+    return int(_lib.hygt_mixed_ctas())
+
+
+def hygt_forward_mixed(classes, nclasses, stream, d_status):
+    return int(_lib.hygt_forward_mixed(classes, nclasses, stream, d_status))
+
+
+def hygt_inverse_mixed(classes, nclasses, stream, d_status):
+    return int(_lib.hygt_inverse_mixed(classes, nclasses, stream, d_status))
+
+
+def hygt_mixed_graph_create(classes, nclasses, d_status):
+    h = ctypes.c_void_p()
+    st = _lib.hygt_mixed_graph_create(ctypes.byref(h), classes, nclasses, d_status)
+    return int(st), h.value
+
+
+def hygt_graph_launch(graph, stream):
+    return int(_lib.hygt_graph_launch(graph, stream))
+
+
+def hygt_graph_destroy(graph):
+    _lib.hygt_graph_destroy(graph)
 
 
 def hygt_plan_info(plan):
@@ -310,3 +356,87 @@ class Batch:
             out = torch.empty(y.shape, dtype=torch.int16, device=y.device)
         return self._run(hygt_inverse_batch, "hygt_inverse_batch", y, out, torch.int32,
                          torch.int16, status, stream)
+
+
+class MixedBatch:
+    """Blocks of several sizes (N = 16, 64, 256) transformed in one launch.
+
+    ``classes`` is a list of (plan, x, sets) with x an int16 CUDA tensor
+    [nblocks, N] and sets an int16/uint16 CUDA tensor [nblocks] (or None).
+    The object owns the coefficient and reconstruction tensors and one
+    schedule workspace per class.
+    """
+
+    def __init__(self, classes, device=None):
+        import torch
+        self.entries = []
+        arr = (MixedClass * len(classes))()
+        for i, (plan, x, sets) in enumerate(classes):
+            nb = int(x.shape[0])
+            dev = device or x.device
+            work = torch.empty(max(1, hygt_batch_workspace_bytes(plan.handle, nb)),
+                               dtype=torch.uint8, device=dev)
+            y = torch.empty((nb, plan.N), dtype=torch.int32, device=dev)
+            xr = torch.empty((nb, plan.N), dtype=torch.int16, device=dev)
+            _dptr(x, torch.int16, plan.N, "x")
+            ps = None
+            if sets is not None:
+                ps = _dptr(sets, torch.int16 if sets.dtype == torch.int16 else torch.uint16,
+                           None, "sets")
+            arr[i] = MixedClass(plan.handle, ps, nb, work.data_ptr(), work.numel(),
+                                x.data_ptr(), y.data_ptr(), xr.data_ptr(), 0)
+            self.entries.append({"plan": plan, "x": x, "sets": sets, "y": y, "xr": xr,
+                                 "work": work})
+        self.classes = arr
+        self.n = len(classes)
+
+    def set_split(self, ctas):
+        """CTAs of the mixed launch per class (None or zeros: automatic)."""
+        for i in range(self.n):
+            self.classes[i].ctas = 0 if ctas is None else int(ctas[i])
+
+    def build(self, stream=None):
+        for i, e in enumerate(self.entries):
+            c = self.classes[i]
+            _check(hygt_batch_build(c.plan, c.d_set, c.nblocks, c.d_work, c.work_bytes,
+                                    _stream_handle(stream)), "hygt_batch_build")
+        return self
+
+    def forward(self, status=None, stream=None):
+        import torch
+        pst = None if status is None else _dptr(status, torch.int32, None, "status")
+        _check(hygt_forward_mixed(self.classes, self.n, _stream_handle(stream), pst),
+               "hygt_forward_mixed")
+
+    def inverse(self, status=None, stream=None):
+        import torch
+        pst = None if status is None else _dptr(status, torch.int32, None, "status")
+        _check(hygt_inverse_mixed(self.classes, self.n, _stream_handle(stream), pst),
+               "hygt_inverse_mixed")
+
+    def graph(self, status=None):
+        """A CUDA graph of one step: schedules, mixed forward, mixed inverse."""
+        import torch
+        pst = None if status is None else _dptr(status, torch.int32, None, "status")
+        st, h = hygt_mixed_graph_create(self.classes, self.n, pst)
+        _check(st, "hygt_mixed_graph_create")
+        return Graph(h)
+
+
+class Graph:
+    def __init__(self, handle):
+        self.handle = handle
+
+    def launch(self, stream=None):
+        _check(hygt_graph_launch(self.handle, _stream_handle(stream)), "hygt_graph_launch")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            hygt_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

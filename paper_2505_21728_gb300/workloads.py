@@ -79,6 +79,64 @@ _REGISTRY = {
 }
 
 
+@dataclass
+class MixedWorkload:
+    """A frame sequence tiled into 4x4, 8x8 and 16x16 blocks (one class per
+    block size, each with its own transform sets)."""
+    name: str
+    frames: int
+    width: int
+    height: int
+    num_sets: int
+    scale: float
+    clip: tuple
+    skip_frac: float
+    rounds: tuple = (2, 2, 3)       # rounds for N = 16, 64, 256
+    area_mix: tuple = (0.50, 0.35, 0.15)
+    seed: int = 0
+    description: str = ""
+    scale_down: int = 1             # divide the block counts (small test cases)
+
+    def counts(self):
+        t = inputs.mixed_frame_tiling(self.frames, self.width, self.height, self.seed,
+                                      self.area_mix)["blocks"]
+        return tuple(max(1, c // self.scale_down) for c in t)
+
+    def classes(self):
+        """One Workload per block size (N = 16, 64, 256)."""
+        out = []
+        for k, (log2n, nb) in enumerate(zip((4, 6, 8), self.counts())):
+            out.append(Workload("%s/N%d" % (self.name, 1 << log2n), log2n=log2n,
+                                rounds=self.rounds[k], num_sets=self.num_sets, nblocks=nb,
+                                scale=self.scale, clip=self.clip, seed=self.seed + 17 * (k + 1),
+                                skip_frac=self.skip_frac))
+        return out
+
+    @property
+    def nblocks(self):
+        return sum(self.counts())
+
+    def bytes_fwd_inv(self):
+        return sum(c.bytes_fwd_inv() for c in self.classes())
+
+
+_MIXED = {
+    "mixed_frame_2160p16": MixedWorkload(
+        "mixed_frame_2160p16", frames=16, width=3840, height=2160, num_sets=105, scale=6.0,
+        clip=(-512, 511), skip_frac=0.10,
+        description="16 frames of 3840x2160 residual tiled into 4x4 / 8x8 / 16x16 blocks "
+                    "(50/35/15% of the area, seeded), set index uniform over 0..104, 10% of "
+                    "blocks without a transform, Laplace(6) int16 clipped to [-512, 511]; "
+                    "N=16 and N=64 with 2 rounds, N=256 with 3 rounds"),
+}
+
+
+def get_mixed(name: str, scale_down: int = 1) -> MixedWorkload:
+    import dataclasses
+    w = _MIXED[name]
+    return dataclasses.replace(w, scale_down=scale_down) if scale_down != 1 else w
+
+
 def truncated(w: Workload, nblocks: int) -> Workload:
     """The first nblocks blocks of a workload (same parameters and seeds)."""
     import dataclasses
