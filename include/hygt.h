@@ -165,6 +165,36 @@ hygt_status hygt_inverse_batch(hygt_plan plan, const void *d_work, const int32_t
                                int *d_status);
 
 /*
+ * Differentiable FP32 path (the angles are the parameters optimised in
+ * Sec. V; the paper leaves the optimiser out of scope).
+ *
+ *   hygt_update_theta  recompute the (cos, sin) table of an FP32 plan from
+ *        device angles d_theta (float [num_sets][rounds][log2n][N/2], radians),
+ *        async on stream; order it with other calls that use the plan.
+ *        Integer plans return HYGT_ERR_UNSUPPORTED.
+ *   hygt_backward_workspace_bytes  device bytes hygt_backward_f32 needs for
+ *        nblocks blocks (0 if the plan has too many angles: the shared-memory
+ *        accumulators of one warp must fit in one CTA).
+ *   hygt_backward_f32  given the forward output d_y and dL/dy d_gy (float
+ *        [nblocks][N]), writes dL/dx to d_gx (float [nblocks][N]; must not
+ *        alias d_y or d_gy) and dL/dtheta to d_gtheta (double, layout of the
+ *        angles; overwritten).  For each rotation, dL/dtheta gets
+ *        g_m y_n - g_n y_m (y = the rotation's outputs, g = their
+ *        gradients); each pass's input is recomputed from its output by the
+ *        inverse rotation, so nothing is stored between forward and
+ *        backward.  The sum over blocks is deterministic (fixed order; FP32
+ *        within a block slot, FP64 across slots and CTAs).  Skip blocks pass
+ *        dL/dy through and add nothing; bad set indices give zero dL/dx and
+ *        HYGT_ERR_SET_INDEX in d_status.
+ */
+hygt_status hygt_update_theta(hygt_plan plan, const float *d_theta, hygt_stream stream);
+size_t hygt_backward_workspace_bytes(hygt_plan plan, int64_t nblocks);
+hygt_status hygt_backward_f32(hygt_plan plan, const float *d_y, const float *d_gy, float *d_gx,
+                              double *d_gtheta, const uint16_t *d_set, int64_t nblocks,
+                              void *d_work, size_t work_bytes, hygt_stream stream,
+                              int *d_status);
+
+/*
  * Mixed block sizes in one persistent launch.  The paper's codec applies
  * 4x4 (N = 16) and 8x8 (N = 64) secondary transforms (Sec. VI); a frame
  * tiled into 4x4, 8x8 and 16x16 blocks gives one batch per block size, each

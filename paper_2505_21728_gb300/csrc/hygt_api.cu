@@ -11,6 +11,7 @@
 
 #include "../../include/hygt.h"
 #include "hygt_batch.cuh"
+#include "hygt_grad.cuh"
 #include "hygt_mixed.cuh"
 #include "hygt_launch.cuh"
 
@@ -544,6 +545,67 @@ void hygt_graph_destroy(hygt_graph graph) {
   if (graph->exec) cudaGraphExecDestroy(graph->exec);
   if (graph->graph) cudaGraphDestroy(graph->graph);
   delete graph;
+}
+
+hygt_status hygt_update_theta(hygt_plan plan, const float* d_theta, hygt_stream stream) {
+  if (!plan || !d_theta) return HYGT_ERR_ARG;
+  if (!plan->is_float) return HYGT_ERR_UNSUPPORTED;
+  const long long n = (long long)plan->num_sets * plan->rounds * plan->log2n * (1 << (plan->log2n - 1));
+  hygt::hygt_theta_to_table<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+      d_theta, static_cast<float2*>(plan->d_tab_f32), n);
+  return to_status(cudaGetLastError());
+}
+
+static int plan_angles(hygt_plan plan) {
+  return plan->num_sets * plan->rounds * plan->log2n * (1 << (plan->log2n - 1));
+}
+
+size_t hygt_backward_workspace_bytes(hygt_plan plan, int64_t nblocks) {
+  if (!plan || nblocks < 0) return 0;
+  int threads = 0, grid = 0;
+  size_t smem = 0;
+  hygt::grad_config(plan->log2n, plan_angles(plan), nblocks, &threads, &grid, &smem);
+  if (threads == 0) return 0;
+  return (size_t)(grid > 0 ? grid : 1) * plan_angles(plan) * sizeof(double);
+}
+
+hygt_status hygt_backward_f32(hygt_plan plan, const float* d_y, const float* d_gy, float* d_gx,
+                              double* d_gtheta, const uint16_t* d_set, int64_t nblocks,
+                              void* d_work, size_t work_bytes, hygt_stream stream, int* d_status) {
+  if (!plan || nblocks < 0 || !d_gtheta) return HYGT_ERR_ARG;
+  hygt_status s = check_io(plan, d_y, d_gx, nblocks);
+  if (s != HYGT_OK) return s;
+  if (nblocks > 0 && (!d_gy || !aligned16(d_gy))) return HYGT_ERR_ARG;
+  const int angles = plan_angles(plan);
+  int threads = 0, grid = 0;
+  size_t smem = 0;
+  hygt::grad_config(plan->log2n, angles, nblocks, &threads, &grid, &smem);
+  if (threads == 0) return HYGT_ERR_UNSUPPORTED;
+  if (!d_work || work_bytes < (size_t)(grid > 0 ? grid : 1) * angles * sizeof(double))
+    return HYGT_ERR_ARG;
+  if (nblocks == 0) {
+    return to_status(cudaMemsetAsync(d_gtheta, 0, (size_t)angles * sizeof(double),
+                                     (cudaStream_t)stream));
+  }
+  hygt::GradLaunch gl{};
+  gl.log2n = plan->log2n;
+  gl.threads = threads;
+  gl.grid = grid;
+  gl.smem = smem;
+  gl.p.y = d_y;
+  gl.p.gy = d_gy;
+  gl.p.gx = d_gx;
+  gl.p.set = d_set;
+  gl.p.nblocks = nblocks;
+  gl.p.tab = static_cast<const float2*>(plan->d_tab_f32);
+  gl.p.perm = plan->d_perm;
+  gl.p.perm_mask = plan->perm_mask;
+  gl.p.rounds = plan->rounds;
+  gl.p.num_sets = plan->num_sets;
+  gl.p.angles = angles;
+  gl.p.partials = static_cast<double*>(d_work);
+  gl.p.status = d_status;
+  return to_status(hygt::launch_grad(gl, d_gtheta, (cudaStream_t)stream));
 }
 
 hygt_status hygt_plan_info(hygt_plan plan, int* log2n, int* rounds, int* num_sets, int* is_float) {

@@ -64,6 +64,12 @@ def _load() -> ctypes.CDLL:
         f = getattr(L, name)
         f.argtypes = [P, P, P, P, i64, P, P]
         f.restype = i32
+    L.hygt_update_theta.argtypes = [P, P, P]
+    L.hygt_update_theta.restype = i32
+    L.hygt_backward_workspace_bytes.argtypes = [P, i64]
+    L.hygt_backward_workspace_bytes.restype = ctypes.c_size_t
+    L.hygt_backward_f32.argtypes = [P, P, P, P, P, P, i64, P, ctypes.c_size_t, P, P]
+    L.hygt_backward_f32.restype = i32
     L.hygt_mixed_ctas.argtypes = []
     L.hygt_mixed_ctas.restype = i32
     for name in ("hygt_forward_mixed", "hygt_inverse_mixed"):
@@ -158,6 +164,20 @@ def hygt_forward_batch(plan, d_work, d_x, d_y, nblocks, stream, d_status):
 
 def hygt_inverse_batch(plan, d_work, d_y, d_x, nblocks, stream, d_status):
     return int(_lib.hygt_inverse_batch(plan, d_work, d_y, d_x, nblocks, stream, d_status))
+
+
+def hygt_update_theta(plan, d_theta, stream):
+    return int(_lib.hygt_update_theta(plan, d_theta, stream))
+
+
+def hygt_backward_workspace_bytes(plan, nblocks):
+    return int(_lib.hygt_backward_workspace_bytes(plan, nblocks))
+
+
+def hygt_backward_f32(plan, d_y, d_gy, d_gx, d_gtheta, d_set, nblocks, d_work, work_bytes,
+                      stream, d_status):
+    return int(_lib.hygt_backward_f32(plan, d_y, d_gy, d_gx, d_gtheta, d_set, nblocks, d_work,
+                                      work_bytes, stream, d_status))
 
 
 def hygt_mixed_ctas():
@@ -288,6 +308,35 @@ class Plan:
             out = torch.empty(y.shape, dtype=torch.int16, device=y.device)
         return self._call(hygt_inverse, "hygt_inverse", y, out, sets, torch.int32, torch.int16,
                           status, stream)
+
+    def update_theta(self, theta, stream=None):
+        """Recompute the FP32 table from device angles (float32, layout of
+        the angles); FP32 plans only."""
+        import torch
+        pt = _dptr(theta.contiguous() if theta.is_cuda else theta, torch.float32, None, "theta")
+        _check(hygt_update_theta(self.handle, pt, _stream_handle(stream)), "hygt_update_theta")
+
+    def backward_f32(self, y, gy, sets=None, status=None, stream=None):
+        """dL/dx (float32 [B, N]) and dL/dtheta (float64, flat) from the
+        forward output y and dL/dy."""
+        import torch
+        nb = y.shape[0]
+        gx = torch.empty_like(y)
+        angles = self.num_sets * self.rounds * self.log2n * (self.N // 2)
+        gth = torch.empty(angles, dtype=torch.float64, device=y.device)
+        wb = hygt_backward_workspace_bytes(self.handle, nb)
+        if wb == 0:
+            raise HygtError(HYGT_ERR_UNSUPPORTED, "hygt_backward_workspace_bytes")
+        work = torch.empty(wb, dtype=torch.uint8, device=y.device)
+        ps = None
+        if sets is not None:
+            ps = _dptr(sets, torch.int16 if sets.dtype == torch.int16 else torch.uint16, None, "sets")
+        pst = None if status is None else _dptr(status, torch.int32, None, "status")
+        _check(hygt_backward_f32(self.handle, _dptr(y, torch.float32, self.N, "y"),
+                                 _dptr(gy, torch.float32, self.N, "gy"), gx.data_ptr(),
+                                 gth.data_ptr(), ps, nb, work.data_ptr(), wb,
+                                 _stream_handle(stream), pst), "hygt_backward_f32")
+        return gx, gth
 
     def forward_f32(self, x, sets=None, out=None, status=None, stream=None):
         import torch
@@ -440,3 +489,64 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+def _autograd_function():
+    import torch
+
+    class HyGTFunction(torch.autograd.Function):
+        """y = HyGT(theta) x on FP32 blocks; backward recomputes the passes
+        from y (nothing is stored between forward and backward)."""
+
+        @staticmethod
+        def forward(ctx, x, theta, plan, sets):
+            plan.update_theta(theta.detach())
+            y = plan.forward_f32(x.contiguous(), sets)
+            ctx.save_for_backward(y)
+            ctx.plan = plan
+            ctx.sets = sets
+            ctx.theta_shape = theta.shape
+            return y
+
+        @staticmethod
+        def backward(ctx, gy):
+            (y,) = ctx.saved_tensors
+            gx, gth = ctx.plan.backward_f32(y, gy.contiguous(), ctx.sets)
+            return gx, gth.to(torch.float32).view(ctx.theta_shape), None, None
+
+    return HyGTFunction
+
+
+_HYGT_FN = None
+
+
+def hygt_function(x, theta, plan, sets=None):
+    """Differentiable HyGT: x float32 [B, N] (CUDA), theta float32 CUDA tensor
+    of the angles [S, R, log2 N, N/2]; ``plan`` an FP32 plan of that shape."""
+    global _HYGT_FN
+    if _HYGT_FN is None:
+        _HYGT_FN = _autograd_function()
+    return _HYGT_FN.apply(x, theta, plan, sets)
+
+
+def HyGTLayer(log2n, rounds, num_sets=1, perms=None, theta=None, seed=0):
+    """A torch.nn.Module holding the angles as a parameter."""
+    import torch
+
+    class _Layer(torch.nn.Module):
+        def __init__(self):
+            super().__init__()
+            N = 1 << log2n
+            shape = (num_sets, rounds, log2n, N // 2)
+            if theta is None:
+                g = torch.Generator().manual_seed(seed)
+                t0 = (torch.rand(shape, generator=g, dtype=torch.float64) * 2 - 1) * np.pi
+            else:
+                t0 = torch.as_tensor(np.asarray(theta, np.float64)).reshape(shape)
+            self.theta = torch.nn.Parameter(t0.to(torch.float32).cuda())
+            self.plan = Plan.from_theta(log2n, rounds, t0.numpy().astype(np.float32), perms)
+
+        def forward(self, x, sets=None):
+            return hygt_function(x, self.theta, self.plan, sets)
+
+    return _Layer()

@@ -131,6 +131,42 @@ _MIXED = {
 }
 
 
+@dataclass
+class FitWorkload:
+    """Differentiable FP32 HyGT on correlated patches (angle fitting)."""
+    name: str
+    log2n: int
+    rounds: int
+    nvec: int
+    keep: int                       # K: coefficients whose energy is kept
+    seed: int = 0
+    description: str = ""
+
+    @property
+    def N(self) -> int:
+        return 1 << self.log2n
+
+    def patches(self, count=None) -> np.ndarray:
+        side = int(round(self.N ** 0.5))
+        return inputs.ar1_patches(self.nvec if count is None else count, side, seed=self.seed)
+
+    def theta0(self) -> np.ndarray:
+        return inputs.theta_uniform((1, self.rounds, self.log2n, self.N // 2), seed=self.seed)
+
+
+_FIT = {
+    "hygt8x8_r4_fit": FitWorkload(
+        "hygt8x8_r4_fit", log2n=6, rounds=4, nvec=1048576, keep=8, seed=0,
+        description="differentiable FP32 HyGT, N=64, 4 rounds (768 angles), 1,048,576 8x8 "
+                    "patches: half separable AR(1) (0.95, 0.9), half 45-degree rotated AR(1) "
+                    "(0.97 / 0.6); loss = energy outside the first 8 coefficients"),
+}
+
+
+def get_fit(name: str) -> FitWorkload:
+    return _FIT[name]
+
+
 def get_mixed(name: str, scale_down: int = 1) -> MixedWorkload:
     import dataclasses
     w = _MIXED[name]
