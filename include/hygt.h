@@ -242,6 +242,36 @@ hygt_status hygt_mixed_graph_create(hygt_graph *out, const hygt_mixed_class *cla
 hygt_status hygt_graph_launch(hygt_graph graph, hygt_stream stream);
 void hygt_graph_destroy(hygt_graph graph);
 
+/*
+ * Dense matrix transform, the baseline of the comparison: y_b = K_{set(b)} x_b
+ * with one N x N matrix per set (the matrix transform of Eq. 3; a KLT of
+ * Eq. 2 is such a matrix).  Blocks are bucketed by set in tiles of 128.
+ *
+ *   dense_klt_create  h_K host float [num_sets][N][N], row-major (y = K x);
+ *        N = 16, 64 or 256; builds BF16 operand images (N = 64, 256) and
+ *        the integer matrices round(2^frac_bits K) (|entries| <= 32767,
+ *        else HYGT_ERR_ARG).  Synchronous.
+ *   dense_klt_workspace_bytes / dense_klt_build  schedule of nblocks blocks
+ *        (as hygt_batch_build), async on stream.
+ *   dense_klt_apply  kind DENSE_KLT_BF16: BF16 x BF16 products with FP32
+ *        accumulation on the tensor cores (tcgen05), d_y float [nblocks][N],
+ *        N = 64 or 256; kind DENSE_KLT_INT: d_y int32 [nblocks][N] =
+ *        floor((round(2^f K) x + 2^(f-1)) / 2^f) on the CUDA cores, N = 16
+ *        or 64.  Skip blocks are copied, bad set indices give zeros and
+ *        HYGT_ERR_SET_INDEX in d_status.
+ */
+typedef struct dense_klt_s *dense_klt;
+#define DENSE_KLT_BF16 0
+#define DENSE_KLT_INT 1
+hygt_status dense_klt_create(dense_klt *out, int log2n, int num_sets, const float *h_K,
+                             int frac_bits);
+void dense_klt_destroy(dense_klt d);
+size_t dense_klt_workspace_bytes(dense_klt d, int64_t nblocks);
+hygt_status dense_klt_build(dense_klt d, const uint16_t *d_set, int64_t nblocks, void *d_work,
+                            size_t work_bytes, hygt_stream stream);
+hygt_status dense_klt_apply(dense_klt d, const void *d_work, const int16_t *d_x, void *d_y,
+                            int64_t nblocks, int kind, hygt_stream stream, int *d_status);
+
 /* Plan shape: any out-pointer may be NULL. */
 hygt_status hygt_plan_info(hygt_plan plan, int *log2n, int *rounds, int *num_sets,
                            int *is_float);

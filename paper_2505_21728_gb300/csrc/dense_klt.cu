@@ -1,0 +1,374 @@
+// dense_klt.cu -- dense matrix transform y = K_set x per block (the matrix
+// form of Eq. 3), the baseline the HyGT is compared with.
+//
+// Blocks are bucketed by set (the batch schedule, in tiles of 128 blocks),
+// so every tile multiplies one 128 x N slice of blocks by one N x N matrix.
+//
+// BF16 tensor-core kernel (sm_103a tcgen05): a CTA of 128 threads walks its
+// tiles; thread t converts block (tile row) t from int16 to BF16 and writes
+// it into shared memory in the 128-byte-swizzled K-major layout; the CTA's
+// copy of the set's matrix is a pre-swizzled image (built on the host); one
+// thread issues N/16 tcgen05.mma (M = 128, N, K = 16, FP32 accumulate in
+// tensor memory) and commits them to an mbarrier; every warp then reads its
+// 32 rows of the accumulator with tcgen05.ld and stores FP32 outputs.
+//
+// Integer CUDA-core kernel: y = floor((K_int x + 2^(f-1)) / 2^f) with
+// K_int = round(2^f K), int32 arithmetic; a warp computes 32 blocks of one
+// set, each lane one output row at a time.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "hygt_batch.cuh"
+#include "hygt_dense.cuh"
+#include "hygt_launch.cuh"
+
+namespace hygt {
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor of a K-major operand in the 128-byte
+// swizzled layout: rows of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);           // start address
+  d |= (uint64_t)(16 >> 4) << 16;                   // leading byte offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                           // descriptor version
+  d |= (uint64_t)2 << 61;                           // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major.
+__host__ __device__ constexpr uint32_t bf16_idesc(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+}
+
+// Bounded wait on an mbarrier phase; returns false if the limit was reached.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, uint32_t limit) {
+  const uint32_t a = smem_addr(bar);
+  for (uint32_t it = 0; it < limit; ++it) {
+    uint32_t done = 0;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(a), "r"(phase)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_addr(dst_smem)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_addr(bar))
+      : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's accumulator row.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&r)[16]) {
+  uint32_t u[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]),
+        "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]),
+        "=r"(u[14]), "=r"(u[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) r[i] = __uint_as_float(u[i]);
+}
+
+// ---------------------------------------------------------------- BF16 kernel
+// Shared memory: A tile (128 x N bf16, swizzled), B image (N x N bf16,
+// swizzled), then the mbarrier and the TMEM address.  Both images are split
+// into K blocks of 64 elements (128 bytes per row); K block kb of the A tile
+// is at kb * 128 * 128 bytes, of B at kb * N * 128 bytes.
+template <int N>
+struct DenseBf16Shape {
+  static constexpr int KB = N / 64;                 // K blocks
+  static constexpr size_t A_BYTES = (size_t)128 * N * 2;
+  static constexpr size_t B_BYTES = (size_t)N * N * 2;
+  static constexpr size_t SMEM = A_BYTES + B_BYTES + 64;
+  static constexpr uint32_t TMEM_COLS = N < 32 ? 32 : N;
+};
+
+template <int N>
+__global__ void __launch_bounds__(128, 1) dense_bf16_kernel(DenseParams p) {
+  using SH = DenseBf16Shape<N>;
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  unsigned char* a_img = dsm;
+  unsigned char* b_img = dsm + SH::A_BYTES;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(dsm + SH::A_BYTES + SH::B_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(dsm + SH::A_BYTES + SH::B_BYTES + 16);
+  const int t = threadIdx.x;
+  const int warp = t >> 5;
+
+  if (p.meta[1] != (int)p.nblocks || p.meta[2] != p.num_sets || p.meta[3] != 128) {
+    if (t == 0 && blockIdx.x == 0 && p.status) atomicCAS(p.status, 0, 1);
+    return;
+  }
+  // the 128-byte swizzle needs 1024-byte aligned operand images
+  if ((smem_addr(a_img) & 1023u) != 0) {
+    if (t == 0 && p.status) atomicCAS(p.status, 0, 2);
+    return;
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, SH::TMEM_COLS);
+  if (t == 0) mbar_init(bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  const long long ntasks = max(0LL, min((long long)p.meta[0], p.tmax));
+  const long long chunk = (ntasks + gridDim.x - 1) / gridDim.x;
+  const long long t0 = min(ntasks, (long long)blockIdx.x * chunk);
+  const long long t1 = min(ntasks, t0 + chunk);
+  int cached = -1;
+  uint32_t phase = 0;
+  bool ok = true;
+  constexpr uint32_t kIdesc = bf16_idesc(128, N);
+
+  for (long long task = t0; task < t1 && ok; ++task) {
+    const int slot = (int)(task * 128);
+    const int bucket = bucket_of_slot(p.starts, p.num_sets, slot);
+    const int b = __ldg(p.order + slot + t);
+    const bool active = b >= 0 && b < p.nblocks;
+    if (bucket >= p.num_sets) {  // skip (identity) or bad set (zeros)
+      if (active) {
+        float* y = p.y + (long long)b * N;
+        const int16_t* x = p.x + (long long)b * N;
+        for (int i = 0; i < N; ++i) y[i] = bucket == p.num_sets ? (float)x[i] : 0.f;
+        if (bucket != p.num_sets && p.status) atomicCAS(p.status, 0, 4);
+      }
+      continue;
+    }
+    // B image of the set (uniform across the CTA, reloaded on change)
+    if (bucket != cached) {
+      const int4* src = reinterpret_cast<const int4*>(p.kimg + (size_t)bucket * SH::B_BYTES);
+      int4* dst = reinterpret_cast<int4*>(b_img);
+      for (int i = t; i < (int)(SH::B_BYTES / 16); i += blockDim.x) dst[i] = __ldg(src + i);
+      cached = bucket;
+    }
+    // A row t: int16 -> bf16, 16-byte chunks at swizzled positions
+    {
+      const int4* xs = reinterpret_cast<const int4*>(p.x + (long long)(active ? b : 0) * N);
+      unsigned char* row = a_img + (t >> 3) * 1024 + (t & 7) * 128;
+#pragma unroll 4
+      for (int c = 0; c < N / 8; ++c) {
+        int4 raw = active ? __ldg(xs + c) : make_int4(0, 0, 0, 0);
+        const int16_t* h = reinterpret_cast<const int16_t*>(&raw);
+        __nv_bfloat162 q[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          q[k] = __floats2bfloat162_rn((float)h[2 * k], (float)h[2 * k + 1]);
+        const int kb = c >> 3, cc = c & 7;
+        unsigned char* dst = row + kb * (128 * 128) + ((cc ^ (t & 7)) << 4);
+        *reinterpret_cast<int4*>(dst) = *reinterpret_cast<int4*>(q);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (t == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_addr(a_img), b0 = smem_addr(b_img);
+#pragma unroll
+      for (int s = 0; s < N / 16; ++s) {
+        const uint32_t ka = (uint32_t)((s >> 2) * (128 * 128) + (s & 3) * 32);
+        const uint32_t kb = (uint32_t)((s >> 2) * (N * 128) + (s & 3) * 32);
+        mma_bf16(tmem, sw128_desc(a0 + ka), sw128_desc(b0 + kb), kIdesc, s > 0 ? 1u : 0u);
+      }
+      mma_commit(bar);
+    }
+    ok = __syncthreads_and(mbar_wait(bar, phase, 1u << 26) ? 1 : 0) != 0;
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+      float* y = p.y + (long long)(active ? b : 0) * N;
+      const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+      for (int c0 = 0; c0 < N; c0 += 16) {
+        float r[16];
+        tmem_ld16(lane_addr + (uint32_t)c0, r);
+        if (active) {
+#pragma unroll
+          for (int k = 0; k < 16; k += 4)
+            *reinterpret_cast<float4*>(y + c0 + k) = make_float4(r[k], r[k + 1], r[k + 2], r[k + 3]);
+        }
+      }
+    } else if (t == 0 && p.status) {
+      atomicCAS(p.status, 0, 2);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, SH::TMEM_COLS);
+}
+
+// ---------------------------------------------------------------- int32 kernel
+// One lane per block: the lane holds its block's N values in registers; the
+// warp's 32 blocks share the set, so every multiplier K_int[i][k] is read by
+// all lanes at once (a broadcast from the CTA's shared copy of the matrix).
+// Four outputs are formed at a time and stored as one 16-byte vector.
+template <int N>
+__global__ void __launch_bounds__(256) dense_int_kernel(DenseParams p) {
+  __shared__ __align__(16) int32_t km[N * N];
+  if (p.meta[1] != (int)p.nblocks || p.meta[2] != p.num_sets || p.meta[3] != 128) {
+    if (threadIdx.x == 0 && blockIdx.x == 0 && p.status) atomicCAS(p.status, 0, 1);
+    return;
+  }
+  // CTA tasks are 128-block tiles (one bucket each); warp w takes rows 32w..
+  const long long ntasks = max(0LL, min((long long)p.meta[0], p.tmax));
+  const long long chunk = (ntasks + gridDim.x - 1) / gridDim.x;
+  const long long t0 = min(ntasks, (long long)blockIdx.x * chunk);
+  const long long t1 = min(ntasks, t0 + chunk);
+  const int half = 1 << (p.frac_bits - 1);
+  int cached = -1;  // the bucket is CTA-uniform, so every thread tracks the same value
+  for (long long task = t0; task < t1; ++task) {
+    const int slot = (int)(task * 128);
+    const int bucket = bucket_of_slot(p.starts, p.num_sets, slot);
+    if (bucket < p.num_sets && bucket != cached) {
+      __syncthreads();
+      const int16_t* K = p.kint + (size_t)bucket * N * N;
+      for (int i = threadIdx.x; i < N * N; i += blockDim.x) km[i] = (int32_t)__ldg(K + i);
+      __syncthreads();
+      cached = bucket;
+    }
+    for (int row = threadIdx.x; row < 128; row += blockDim.x) {
+      const int b = __ldg(p.order + slot + row);
+      const bool active = b >= 0 && b < p.nblocks;
+      int32_t x[N];
+      {
+        uint32_t w[N / 2];
+        if (active) load_words<N / 2>(p.x + (long long)b * N, w);
+        else
+          for (int k = 0; k < N / 2; ++k) w[k] = 0;
+#pragma unroll
+        for (int k = 0; k < N / 2; ++k) {
+          x[2 * k] = (int32_t)(int16_t)(w[k] & 0xffffu);
+          x[2 * k + 1] = (int32_t)w[k] >> 16;
+        }
+      }
+      int32_t* y = p.yint + (long long)(active ? b : 0) * N;
+      if (bucket < p.num_sets) {
+#pragma unroll 1
+        for (int i = 0; i < N; i += 4) {
+          int32_t acc[4] = {half, half, half, half};
+#pragma unroll
+          for (int k = 0; k < N; k += 4) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int4 kv = *reinterpret_cast<const int4*>(&km[(i + q) * N + k]);
+              acc[q] += kv.x * x[k] + kv.y * x[k + 1] + kv.z * x[k + 2] + kv.w * x[k + 3];
+            }
+          }
+          if (active)
+            *reinterpret_cast<int4*>(y + i) =
+                make_int4(acc[0] >> p.frac_bits, acc[1] >> p.frac_bits, acc[2] >> p.frac_bits,
+                          acc[3] >> p.frac_bits);
+        }
+      } else if (active) {
+        for (int k = 0; k < N; ++k) y[k] = bucket == p.num_sets ? x[k] : 0;
+        if (bucket != p.num_sets && p.status) atomicCAS(p.status, 0, 4);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+template <int N>
+static cudaError_t launch_bf16(const DenseParams& p, cudaStream_t stream) {
+  using SH = DenseBf16Shape<N>;
+  auto kern = dense_bf16_kernel<N>;
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  const DeviceInfo info = device_info(dev);
+  // Shared memory per CTA is padded so that the CTAs resident on an SM never
+  // ask for more than the 512 tensor-memory columns of the SM: allocation
+  // then never has to wait.
+  const int max_ctas = 512 / (int)SH::TMEM_COLS;
+  size_t smem = SH::SMEM;
+  const size_t sm_total = 228 * 1024;
+  if (smem * (size_t)(max_ctas + 1) <= sm_total) smem = sm_total / (size_t)(max_ctas + 1) + 1024;
+  if (smem > (size_t)info.max_smem_optin) return cudaErrorInvalidConfiguration;
+  err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  int occ = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 128, smem);
+  if (err != cudaSuccess) return err;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  if (occ > max_ctas) return cudaErrorInvalidConfiguration;
+  long long grid = (long long)occ * info.sms;
+  const long long tiles = (p.nblocks + 127) / 128 + p.num_sets + 2;
+  if (grid > tiles) grid = tiles;
+  kern<<<(unsigned)grid, 128, smem, stream>>>(p);
+  return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t launch_int(const DenseParams& p, cudaStream_t stream) {
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  const DeviceInfo info = device_info(dev);
+  int occ = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dense_int_kernel<N>, 128, 0);
+  if (err != cudaSuccess) return err;
+  if (occ < 1) occ = 1;
+  long long grid = (long long)occ * info.sms;
+  const long long tiles = (p.nblocks + 127) / 128 + p.num_sets + 2;
+  if (grid > tiles) grid = tiles;
+  dense_int_kernel<N><<<(unsigned)grid, 128, 0, stream>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dense(int log2n, int kind, const DenseParams& p, cudaStream_t stream) {
+  if (kind == 0) {
+    switch (log2n) {
+      case 6: return launch_bf16<64>(p, stream);
+      case 8: return launch_bf16<256>(p, stream);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch (log2n) {
+    case 4: return launch_int<16>(p, stream);
+    case 6: return launch_int<64>(p, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace hygt

@@ -11,6 +11,7 @@
 
 #include "../../include/hygt.h"
 #include "hygt_batch.cuh"
+#include "hygt_dense.cuh"
 #include "hygt_grad.cuh"
 #include "hygt_mixed.cuh"
 #include "hygt_launch.cuh"
@@ -606,6 +607,126 @@ hygt_status hygt_backward_f32(hygt_plan plan, const float* d_y, const float* d_g
   gl.p.partials = static_cast<double*>(d_work);
   gl.p.status = d_status;
   return to_status(hygt::launch_grad(gl, d_gtheta, (cudaStream_t)stream));
+}
+
+struct dense_klt_s {
+  int log2n = 0, num_sets = 0, frac_bits = 0, device = 0;
+  unsigned char* d_kimg = nullptr;  // BF16 images (N = 64, 256)
+  int16_t* d_kint = nullptr;        // round(2^f K)
+};
+
+// Round-to-nearest-even FP32 -> BF16 (finite inputs).
+static uint16_t to_bf16(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+hygt_status dense_klt_create(dense_klt* out, int log2n, int num_sets, const float* h_K,
+                             int frac_bits) {
+  if (!out) return HYGT_ERR_ARG;
+  *out = nullptr;
+  if (!h_K || num_sets < 1 || num_sets > 65535 || frac_bits < 1 || frac_bits > 14)
+    return HYGT_ERR_ARG;
+  if (log2n != 4 && log2n != 6 && log2n != 8) return HYGT_ERR_UNSUPPORTED;
+  const int N = 1 << log2n;
+  const size_t per = (size_t)N * N;
+  std::vector<int16_t> kint(per * num_sets);
+  for (size_t i = 0; i < per * num_sets; ++i) {
+    const double v = std::ldexp((double)h_K[i], frac_bits);
+    if (!std::isfinite(v) || std::fabs(v) > 32767.0) return HYGT_ERR_ARG;
+    kint[i] = (int16_t)std::lround(v);
+  }
+  // BF16 image: per 64-column K block, N rows of 128 bytes, 8-row groups of
+  // 1024 bytes, 16-byte chunk c of row i stored at chunk c ^ (i % 8).
+  std::vector<uint16_t> img;
+  if (N >= 64) {
+    img.assign(per * num_sets, 0);
+    for (int s = 0; s < num_sets; ++s) {
+      uint16_t* base = img.data() + (size_t)s * per;
+      for (int kb = 0; kb < N / 64; ++kb)
+        for (int i = 0; i < N; ++i)
+          for (int c = 0; c < 8; ++c)
+            for (int e = 0; e < 8; ++e) {
+              const int k = kb * 64 + c * 8 + e;
+              const size_t byte = (size_t)kb * N * 128 + (size_t)(i / 8) * 1024 +
+                                  (size_t)(i % 8) * 128 + (size_t)((c ^ (i % 8)) * 16) + 2 * e;
+              base[byte / 2] = to_bf16(h_K[(size_t)s * per + (size_t)i * N + k]);
+            }
+    }
+  }
+  dense_klt d = new (std::nothrow) dense_klt_s();
+  if (!d) return HYGT_ERR_OOM;
+  d->log2n = log2n;
+  d->num_sets = num_sets;
+  d->frac_bits = frac_bits;
+  if (cudaGetDevice(&d->device) != cudaSuccess) {
+    delete d;
+    return HYGT_ERR_CUDA;
+  }
+  hygt_status st = upload(reinterpret_cast<void**>(&d->d_kint), kint.data(), kint.size() * 2,
+                          pad16(kint.size() * 2));
+  if (st == HYGT_OK && !img.empty())
+    st = upload(reinterpret_cast<void**>(&d->d_kimg), img.data(), img.size() * 2,
+                pad16(img.size() * 2));
+  if (st != HYGT_OK) {
+    dense_klt_destroy(d);
+    return st;
+  }
+  *out = d;
+  return HYGT_OK;
+}
+
+void dense_klt_destroy(dense_klt d) {
+  if (!d) return;
+  if (d->d_kimg) cudaFree(d->d_kimg);
+  if (d->d_kint) cudaFree(d->d_kint);
+  delete d;
+}
+
+size_t dense_klt_workspace_bytes(dense_klt d, int64_t nblocks) {
+  if (!d || nblocks < 0 || nblocks > kBatchMaxBlocks) return 0;
+  return hygt::batch_layout(d->num_sets, nblocks, 128).total;
+}
+
+hygt_status dense_klt_build(dense_klt d, const uint16_t* d_set, int64_t nblocks, void* d_work,
+                            size_t work_bytes, hygt_stream stream) {
+  if (!d || nblocks < 0 || nblocks > kBatchMaxBlocks || !d_work || !aligned16(d_work))
+    return HYGT_ERR_ARG;
+  if (work_bytes < hygt::batch_layout(d->num_sets, nblocks, 128).total) return HYGT_ERR_ARG;
+  return to_status(hygt::batch_build(d_set, nblocks, d->num_sets, 128, d_work, (cudaStream_t)stream));
+}
+
+hygt_status dense_klt_apply(dense_klt d, const void* d_work, const int16_t* d_x, void* d_y,
+                            int64_t nblocks, int kind, hygt_stream stream, int* d_status) {
+  if (!d || nblocks < 0 || nblocks > kBatchMaxBlocks) return HYGT_ERR_ARG;
+  if (nblocks == 0) return HYGT_OK;
+  if (!d_work || !aligned16(d_work) || !d_x || !d_y || !aligned16(d_x) || !aligned16(d_y))
+    return HYGT_ERR_ARG;
+  if (kind != DENSE_KLT_BF16 && kind != DENSE_KLT_INT) return HYGT_ERR_ARG;
+  if (kind == DENSE_KLT_BF16 && d->log2n < 6) return HYGT_ERR_UNSUPPORTED;
+  if (kind == DENSE_KLT_INT && d->log2n > 6) return HYGT_ERR_UNSUPPORTED;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HYGT_ERR_CUDA;
+  if (dev != d->device) return HYGT_ERR_ARG;
+  const hygt::BatchLayout L = hygt::batch_layout(d->num_sets, nblocks, 128);
+  const char* w = static_cast<const char*>(d_work);
+  hygt::DenseParams p{};
+  p.x = d_x;
+  p.y = static_cast<float*>(d_y);
+  p.yint = static_cast<int32_t*>(d_y);
+  p.order = reinterpret_cast<const int*>(w + L.order);
+  p.starts = reinterpret_cast<const int*>(w + L.starts);
+  p.meta = reinterpret_cast<const int*>(w + L.meta);
+  p.nblocks = nblocks;
+  p.tmax = L.tmax;
+  p.kimg = d->d_kimg;
+  p.kint = d->d_kint;
+  p.num_sets = d->num_sets;
+  p.frac_bits = d->frac_bits;
+  p.status = d_status;
+  return to_status(hygt::launch_dense(d->log2n, kind, p, (cudaStream_t)stream));
 }
 
 hygt_status hygt_plan_info(hygt_plan plan, int* log2n, int* rounds, int* num_sets, int* is_float) {

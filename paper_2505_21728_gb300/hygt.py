@@ -24,6 +24,8 @@ HYGT_ERR_OOM = 3
 HYGT_ERR_SET_INDEX = 4
 HYGT_ERR_UNSUPPORTED = 6
 HYGT_SKIP_SET = 0xFFFF
+DENSE_KLT_BF16 = 0
+DENSE_KLT_INT = 1
 
 
 class HygtError(RuntimeError):
@@ -70,6 +72,16 @@ def _load() -> ctypes.CDLL:
     L.hygt_backward_workspace_bytes.restype = ctypes.c_size_t
     L.hygt_backward_f32.argtypes = [P, P, P, P, P, P, i64, P, ctypes.c_size_t, P, P]
     L.hygt_backward_f32.restype = i32
+    L.dense_klt_create.argtypes = [ctypes.POINTER(P), i32, i32, P, i32]
+    L.dense_klt_create.restype = i32
+    L.dense_klt_destroy.argtypes = [P]
+    L.dense_klt_destroy.restype = None
+    L.dense_klt_workspace_bytes.argtypes = [P, i64]
+    L.dense_klt_workspace_bytes.restype = ctypes.c_size_t
+    L.dense_klt_build.argtypes = [P, P, i64, P, ctypes.c_size_t, P]
+    L.dense_klt_build.restype = i32
+    L.dense_klt_apply.argtypes = [P, P, P, P, i64, i32, P, P]
+    L.dense_klt_apply.restype = i32
     L.hygt_mixed_ctas.argtypes = []
     L.hygt_mixed_ctas.restype = i32
     for name in ("hygt_forward_mixed", "hygt_inverse_mixed"):
@@ -178,6 +190,29 @@ def hygt_backward_f32(plan, d_y, d_gy, d_gx, d_gtheta, d_set, nblocks, d_work, w
                       stream, d_status):
     return int(_lib.hygt_backward_f32(plan, d_y, d_gy, d_gx, d_gtheta, d_set, nblocks, d_work,
                                       work_bytes, stream, d_status))
+
+
+def dense_klt_create(log2n, num_sets, K, frac_bits=8):
+    k = np.ascontiguousarray(K, dtype=np.float32)
+    h = ctypes.c_void_p()
+    st = _lib.dense_klt_create(ctypes.byref(h), log2n, num_sets, _np_ptr(k), frac_bits)
+    return int(st), h.value
+
+
+def dense_klt_destroy(d):
+    _lib.dense_klt_destroy(d)
+
+
+def dense_klt_workspace_bytes(d, nblocks):
+    return int(_lib.dense_klt_workspace_bytes(d, nblocks))
+
+
+def dense_klt_build(d, d_set, nblocks, d_work, work_bytes, stream):
+    return int(_lib.dense_klt_build(d, d_set, nblocks, d_work, work_bytes, stream))
+
+
+def dense_klt_apply(d, d_work, d_x, d_y, nblocks, kind, stream, d_status):
+    return int(_lib.dense_klt_apply(d, d_work, d_x, d_y, nblocks, kind, stream, d_status))
 
 
 def hygt_mixed_ctas():
@@ -550,3 +585,53 @@ def HyGTLayer(log2n, rounds, num_sets=1, perms=None, theta=None, seed=0):
             return hygt_function(x, self.theta, self.plan, sets)
 
     return _Layer()
+
+
+class DenseKLT:
+    """Dense per-set matrix transform (the matrix baseline), y = K[set] x."""
+
+    def __init__(self, log2n, K, frac_bits=8):
+        K = np.ascontiguousarray(K, dtype=np.float32)
+        self.log2n = int(log2n)
+        self.N = 1 << self.log2n
+        self.num_sets = K.shape[0]
+        st, h = dense_klt_create(self.log2n, self.num_sets, K, frac_bits)
+        _check(st, "dense_klt_create")
+        self.handle = h
+        self.work = None
+        self.nblocks = None
+
+    def build(self, sets, nblocks, stream=None):
+        import torch
+        self.nblocks = int(nblocks)
+        nbytes = dense_klt_workspace_bytes(self.handle, self.nblocks)
+        if self.work is None or self.work.numel() < nbytes:
+            self.work = torch.empty(max(1, nbytes), dtype=torch.uint8, device="cuda")
+        ps = None
+        if sets is not None:
+            ps = _dptr(sets, torch.int16 if sets.dtype == torch.int16 else torch.uint16, None, "sets")
+        _check(dense_klt_build(self.handle, ps, self.nblocks, self.work.data_ptr(),
+                               self.work.numel(), _stream_handle(stream)), "dense_klt_build")
+        return self
+
+    def apply(self, x, kind=DENSE_KLT_BF16, out=None, status=None, stream=None):
+        import torch
+        if out is None:
+            dt = torch.float32 if kind == DENSE_KLT_BF16 else torch.int32
+            out = torch.empty((x.shape[0], self.N), dtype=dt, device=x.device)
+        pst = None if status is None else _dptr(status, torch.int32, None, "status")
+        _check(dense_klt_apply(self.handle, self.work.data_ptr(), _dptr(x, torch.int16, self.N, "x"),
+                               out.data_ptr(), self.nblocks, kind, _stream_handle(stream), pst),
+               "dense_klt_apply")
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            dense_klt_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

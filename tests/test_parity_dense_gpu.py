@@ -1,0 +1,88 @@
+"""Parity of the dense matrix-transform baseline with the CPU oracle.
+
+Integer kernel: bit-exact against the oracle's int64 matrix product.
+BF16 tensor-core kernel: against the FP64 product of the BF16-rounded
+matrices and inputs (the kernel's FP32 accumulation error is <= N 2^-24 of
+the sum of |terms|), and within BF16 accuracy of the exact FP64 product."""
+import numpy as np
+import pytest
+
+from paper_2505_21728_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _t(a):
+    import torch
+    if a.dtype == np.uint16:
+        a = a.view(np.int16)
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def bf16_round(a):
+    """Round-to-nearest-even to BF16, returned as float64."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return (u.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def hygt_matrices(orc, log2n, rounds, S, seed):
+    N = 1 << log2n
+    theta = inputs.theta_uniform((S, rounds, log2n, N // 2), seed=seed)
+    perms = inputs.permutations(S, rounds, N, seed=seed)
+    return np.stack([orc.dense_f64(theta[s], log2n, rounds, perms[s]) for s in range(S)])
+
+
+@pytest.mark.parametrize("log2n,S,B", [(4, 3, 1000), (6, 7, 3001), (6, 105, 20000)])
+def test_dense_int_bit_exact(gpu, orc, log2n, S, B):
+    import torch
+    N = 1 << log2n
+    K = hygt_matrices(orc, log2n, 2, S, seed=log2n)
+    K_int = np.sign(256 * K) * np.floor(np.abs(256 * K) + 0.5)  # round half away from zero
+    x = inputs.laplacian_blocks(B, N, 30.0, -1024, 1023, seed=1)
+    sets = inputs.set_indices(B, S, seed=1, skip_frac=0.05)
+    d = gpu.DenseKLT(log2n, K.astype(np.float32)).build(_t(sets), B)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    y = d.apply(_t(x), kind=gpu.DENSE_KLT_INT, status=st).cpu().numpy()
+    K_int_f32 = np.sign(256 * K.astype(np.float32).astype(np.float64)) * \
+        np.floor(np.abs(256 * K.astype(np.float32).astype(np.float64)) + 0.5)
+    ye, ste = orc.dense_apply_int(x, K_int_f32.astype(np.int32), 8, sets)
+    assert ste == 0 and int(st.item()) == 0
+    assert np.array_equal(y, ye)
+
+
+@pytest.mark.parametrize("log2n,S,B", [(6, 5, 2000), (6, 105, 30000), (8, 4, 1500)])
+def test_dense_bf16_tensor_cores(gpu, orc, log2n, S, B):
+    import torch
+    N = 1 << log2n
+    K = hygt_matrices(orc, log2n, 2, S, seed=2 * log2n)
+    x = inputs.laplacian_blocks(B, N, 60.0, -2048, 2047, seed=3)
+    sets = inputs.set_indices(B, S, seed=3, skip_frac=0.05)
+    d = gpu.DenseKLT(log2n, K.astype(np.float32)).build(_t(sets), B)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    y = d.apply(_t(x), kind=gpu.DENSE_KLT_BF16, status=st).cpu().numpy().astype(np.float64)
+    assert int(st.item()) == 0
+    Kb = bf16_round(K.astype(np.float32))
+    xb = bf16_round(x.astype(np.float32))
+    yb, _ = orc.dense_apply_f64(xb, Kb, sets)
+    skip = sets == 0xFFFF
+    yb[skip] = x[skip]
+    scale = np.einsum("bij,bj->bi", np.abs(Kb[np.where(skip, 0, sets)]), np.abs(xb))
+    assert np.all(np.abs(y - yb) <= N * 2.0 ** -23 * scale + 1e-9)
+    ye, _ = orc.dense_apply_f64(x.astype(np.float64), K, sets)
+    ye[skip] = x[skip]
+    rel = np.max(np.abs(y - ye)) / np.max(np.abs(ye))
+    assert rel < 2 ** -7  # BF16 has 8 significant bits
+
+
+def test_dense_bad_set_and_empty(gpu, orc):
+    import torch
+    K = hygt_matrices(orc, 6, 2, 3, seed=9)
+    x = inputs.laplacian_blocks(300, 64, 20.0, -512, 511, seed=9)
+    sets = inputs.set_indices(300, 3, seed=9)
+    sets[10] = 77
+    d = gpu.DenseKLT(6, K.astype(np.float32)).build(_t(sets), 300)
+    for kind in (gpu.DENSE_KLT_BF16, gpu.DENSE_KLT_INT):
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        y = d.apply(_t(x), kind=kind, status=st).cpu().numpy()
+        assert int(st.item()) == 4 and np.all(y[10] == 0)
