@@ -45,6 +45,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the timed oracle sample (for profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the secondary workloads (mixed block sizes)")
     ap.add_argument("--nblocks", type=int, default=0,
                     help="use only the first N blocks of the workload (profiling cases)")
     return ap.parse_args()
@@ -351,6 +353,7 @@ def run_ours(args, rank, world, local):
 
     # context: the direct (unbucketed) kernels on the same data
     direct = direct_path_ms(plan, d_x, d_s, d_y, d_xr, stream)
+    del d_y, d_xr
 
     line = {
         "metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": world,
@@ -373,6 +376,12 @@ def run_ours(args, rank, world, local):
     if not args.no_e2e:
         line["e2e"] = e2e_leg(plan, x_np, s_np, N, dev, stream, world)
 
+    if not args.no_extras and rank == 0:
+        line["dense_klt"] = dense_leg(w, data, d_x, d_s, dev, stream, steps=max(5, K // 4),
+                                      hygt_step_ms=total_ms / K)
+        line["mixed"] = mixed_leg(dev, stream, steps=max(10, K // 2))
+        line["backward"] = backward_leg(dev, stream, steps=max(5, K // 4))
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, data)
 
@@ -381,6 +390,165 @@ def run_ours(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def mixed_leg(dev, stream, steps=20, name="mixed_frame_2160p16"):
+    """The mixed-size frame batch (4x4 / 8x8 / 16x16 blocks, one persistent
+    launch per direction) as a CUDA graph of one step: schedules of the three
+    classes, mixed forward, mixed inverse.  The CTA split is autotuned."""
+    import numpy as np
+    import torch
+    from paper_2505_21728_gb300 import autotune, hygt, workloads
+    w = workloads.get_mixed(name)
+    classes = []
+    for cw in w.classes():
+        d = cw.generate()
+        plan = hygt.Plan(cw.log2n, cw.rounds, d["angle_idx"], d["perms"])
+        classes.append((plan, torch.from_numpy(d["x"]).to(dev),
+                        torch.from_numpy(d["sets"].view(np.int16)).to(dev)))
+    mb = hygt.MixedBatch(classes, device=dev)
+    mb.build()
+    split = autotune.tune_split(mb, reps=3, use_cache=False)
+    graph = mb.graph()
+    for _ in range(3):
+        graph.launch()
+    torch.cuda.synchronize(dev)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        graph.launch()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    step_ms = a.elapsed_time(b) / steps
+    # the two mixed kernels alone (schedules already built)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    f_ms, i_ms = [], []
+    for _ in range(steps):
+        ev[0].record(stream)
+        mb.forward()
+        ev[1].record(stream)
+        mb.inverse()
+        ev[2].record(stream)
+        torch.cuda.synchronize(dev)
+        f_ms.append(ev[0].elapsed_time(ev[1]))
+        i_ms.append(ev[1].elapsed_time(ev[2]))
+    nblocks = w.nblocks
+    bytes_per_launch = w.bytes_fwd_inv() // 2
+    f_avg, i_avg = statistics.mean(f_ms), statistics.mean(i_ms)
+    dom_name, dom_ms = (("hygt_mixed_forward", f_avg) if f_avg >= i_avg
+                        else ("hygt_mixed_inverse", i_avg))
+    peak, kind = measured_peaks()
+    achieved = bytes_per_launch / (dom_ms / 1000.0) / 1e9
+    graph.close()
+    return {"workload": w.name, "description": w.description, "nblocks": nblocks,
+            "blocks_per_class": list(w.counts()), "value": nblocks / (step_ms / 1000.0),
+            "unit": "blocks/s", "ms_per_step": step_ms,
+            "step": "CUDA graph: schedules of 3 classes, mixed forward, mixed inverse",
+            "cta_split": split, "gpu_launches_per_step": 3 * 3 + 2,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "kernel": dom_name, "peak_source": kind,
+                         "bytes_per_launch": bytes_per_launch, "fwd_ms": f_avg, "inv_ms": i_avg,
+                         "traffic": ncu_traffic(dom_name, w.name),
+                         "step_frac": (2 * bytes_per_launch / (step_ms / 1000.0) / 1e9) / peak}}
+
+
+def dense_leg(w, data, d_x, d_s, dev, stream, steps, hygt_step_ms):
+    """The dense matrix transform of the same blocks and sets (one N x N
+    matrix per set, the HyGT's own matrices): tcgen05 BF16 and int32 CUDA-core
+    kernels, one direction; the HyGT step is forward + inverse."""
+    import torch
+    from paper_2505_21728_gb300 import hygt
+    K = hygt.Plan(w.log2n, w.rounds, data["angle_idx"], data["perms"]).dense_matrices()
+    d = hygt.DenseKLT(w.log2n, K)
+    nb = d_x.shape[0]
+    N = w.N
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize(dev)
+        ev[0].record(stream)
+        for _ in range(steps):
+            fn()
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        return ev[0].elapsed_time(ev[1]) / steps
+
+    build_ms = timed(lambda: d.build(d_s, nb))
+    y = torch.empty((nb, N), dtype=torch.float32, device=dev)
+    yi = torch.empty((nb, N), dtype=torch.int32, device=dev)
+    out = {"matrices": "the HyGT's own %dx%d matrices, %d sets" % (N, N, w.num_sets),
+           "schedule_ms": build_ms}
+    peak, kind = measured_peaks()
+    bytes_per_block = 2 * N + 4 * N + 4  # int16 in, 32-bit out, slot id
+    for name, kd, buf in (("bf16_tcgen05", hygt.DENSE_KLT_BF16, y),
+                          ("int32_cuda_core", hygt.DENSE_KLT_INT, yi)):
+        if (kd == hygt.DENSE_KLT_BF16 and N < 64) or (kd == hygt.DENSE_KLT_INT and N > 64):
+            continue
+        ms = timed(lambda: d.apply(d_x, kind=kd, out=buf))
+        gbs = nb * bytes_per_block / (ms / 1000.0) / 1e9
+        out[name] = {"ms_per_apply": ms, "blocks_per_s_one_direction": nb / (ms / 1000.0),
+                     "blocks_per_s_fwd_inv": nb / ((2 * (ms + build_ms / 2)) / 1000.0),
+                     "tflops": 2.0 * N * N * nb / (ms / 1000.0) / 1e12,
+                     "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                                  "frac": gbs / peak, "peak_source": kind}}
+    out["hygt_fwd_inv_step_ms"] = hygt_step_ms
+    d.close()
+    return out
+
+
+def backward_leg(dev, stream, steps, name="hygt8x8_r4_fit"):
+    """The differentiable FP32 path on the fitting workload: forward, the
+    energy-compaction loss gradient, and the recomputing backward."""
+    import torch
+    from paper_2505_21728_gb300 import hygt, workloads
+    w = workloads.get_fit(name)
+    x = torch.from_numpy(w.patches()).to(dev)
+    theta = w.theta0().astype("float32")
+    plan = hygt.Plan.from_theta(w.log2n, w.rounds, theta)
+    mask = torch.zeros(w.N, device=dev)
+    mask[w.keep:] = 2.0 / w.nvec
+    y = plan.forward_f32(x)
+    gy = y * mask
+    plan.backward_f32(y, gy)
+    torch.cuda.synchronize(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    f_ms, b_ms = [], []
+    for _ in range(steps):
+        ev[0].record(stream)
+        y = plan.forward_f32(x, out=y)
+        ev[1].record(stream)
+        gy = y * mask
+        e2 = torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        plan.backward_f32(y, gy)
+        ev[2].record(stream)
+        torch.cuda.synchronize(dev)
+        f_ms.append(ev[0].elapsed_time(ev[1]))
+        b_ms.append(e2.elapsed_time(ev[2]))
+    fm, bm = statistics.mean(f_ms), statistics.mean(b_ms)
+    pairs = w.rounds * w.log2n * (w.N // 2)
+    flops = 15.0 * pairs * w.nvec  # inverse rotation 6, gradient rotation 6, angle term 3
+    sm_mhz = 2070.0
+    try:
+        sm_mhz = float(torch.cuda.get_device_properties(dev).clock_rate) / 1000.0 or sm_mhz
+    except Exception:
+        pass
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12  # FFMA lanes x 2 FLOP x clock
+    peak, kind = measured_peaks()
+    gbs = 3 * 4 * w.N * w.nvec / (bm / 1000.0) / 1e9
+    plan.close()
+    return {"workload": w.name, "description": w.description, "nvec": w.nvec,
+            "forward_ms": fm, "backward_ms": bm,
+            "vectors_per_s_fwd_bwd": w.nvec / ((fm + bm) / 1000.0),
+            "roofline": {"bound": "alu", "achieved": flops / (bm / 1000.0) / 1e12,
+                         "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": flops / (bm / 1000.0) / 1e12 / fp32_peak,
+                         "peak_source": "FP32 FMA lanes x clock (%d SMs x 128 x 2 x %.0f MHz)"
+                                        % (sms, sm_mhz),
+                         "kernel": "hygt_grad_kernel", "hbm_gbs": gbs, "hbm_frac": gbs / peak}}
 
 
 def direct_path_ms(plan, d_x, d_s, d_y, d_xr, stream, steps=5):

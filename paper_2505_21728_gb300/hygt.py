@@ -373,6 +373,16 @@ class Plan:
                                  _stream_handle(stream), pst), "hygt_backward_f32")
         return gx, gth
 
+    def dense_matrices(self):
+        """The N x N matrix of every set (float32 [S, N, N], y = T x), from
+        the FP32 transform of the unit vectors: column i = T e_i."""
+        import torch
+        N, S = self.N, self.num_sets
+        eye = torch.eye(N, dtype=torch.float32, device="cuda").repeat(S, 1).contiguous()
+        sets = torch.arange(S, device="cuda").repeat_interleave(N).to(torch.int16)
+        y = self.forward_f32(eye, sets)
+        return y.view(S, N, N).transpose(1, 2).contiguous().cpu().numpy()
+
     def forward_f32(self, x, sets=None, out=None, status=None, stream=None):
         import torch
         if out is None:
