@@ -159,7 +159,7 @@ void build_ktab(int log2n, int rounds, int num_sets, const uint8_t* q, const std
         int* prow = t + sh.perm_offset(r);
         for (int i = 0; i < N; ++i) {
           const int src = perm.empty() ? i : perm[((size_t)s * rounds + r) * N + i];
-          prow[i] = 4 * hygt::perm_word(src);
+          prow[i] = 4 * hygt::perm_word(src, sh.log2e);
         }
       }
     }

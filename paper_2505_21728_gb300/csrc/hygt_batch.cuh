@@ -8,9 +8,13 @@
 // sets' multipliers into shared memory once, and every lane reads them by
 // broadcast.
 //
-// Mapping.  A block of N = 2^LOG2N values is held by L = N / E lanes with
-// E = min(N, 32) consecutive values per lane (element e = lane * E + i in
-// register i), so G = 32 / L blocks per warp.
+// Mapping.  A block of N = 2^LOG2N values is held by a group of L = N / E
+// lanes with E consecutive values per lane (element e = lane * E + i in
+// register i), and every lane group holds K blocks of the same set at once:
+// each multiplier loaded into a register serves K butterflies, and the K
+// blocks are independent work for the scheduler.  A warp task is
+// G = (32 / L) K blocks; block k of lane group g is the task's block
+// k (32 / L) + g.
 //   - Pass p < LOG2E pairs two registers of a lane (register butterfly).
 //   - Pass p >= LOG2E pairs lane l with lane l ^ 2^(p - LOG2E): each lane
 //     fetches its partner's value with __shfl_xor_sync and computes its own
@@ -34,14 +38,21 @@
 
 namespace hygt {
 
-constexpr int kBatchThreads = 768;   // threads per CTA of the batch transform
+constexpr int kBatchThreads = 512;   // threads per CTA of the batch transform
 constexpr int kBucketThreads = 512;  // threads per CTA of the bucketing kernels
 constexpr int kBucketTile = 8192;    // blocks per CTA tile in the scatter pass
 
-__host__ __device__ constexpr int batch_log2e(int log2n) { return log2n < 5 ? log2n : 5; }
-// Blocks per warp task for block size 2^log2n.
+// Layout for block size 2^log2n: E = 2^batch_log2e values of a block per
+// lane, L = N / E lanes per block (a lane group), K = batch_k blocks of the
+// same set per lane group, G = (32 / L) K blocks per warp task.
+__host__ __device__ constexpr int batch_log2e(int log2n) {
+  return log2n <= 4 ? log2n : (log2n <= 6 ? 4 : 5);
+}
+__host__ __device__ constexpr int batch_k(int log2n) {
+  return log2n <= 2 ? 1 : (log2n == 5 || log2n == 6 ? 4 : 2);
+}
 __host__ __device__ constexpr int batch_group(int log2n) {
-  return 32 >> (log2n - batch_log2e(log2n));
+  return (32 >> (log2n - batch_log2e(log2n))) * batch_k(log2n);
 }
 
 // Workspace layout (all offsets in bytes, 16-byte aligned sections):
@@ -99,14 +110,15 @@ struct SetTableShape {
   }
 };
 
-// Words per block in the permutation buffer and the word of element e:
-// one padding word after every 32 elements (or after the block when it is
-// shorter), which keeps the L lanes of a block and the G blocks of a warp
-// on distinct banks when they write their registers.
+// Words per block in the permutation buffer and the word of element e: one
+// padding word after each lane's E elements, so lane l's element i is at
+// l (E + 1) + i.  With the block slots of a warp task numbered block-major
+// (k (32 / L) + g), the 32 lanes of a warp writing register i of their
+// k-th block land on 32 distinct banks (E + 1 is odd).
 __host__ __device__ constexpr int perm_region_words(int log2n) {
-  return log2n >= 5 ? (1 << log2n) + (1 << (log2n - 5)) : (1 << log2n) + 1;
+  return (1 << log2n) + (1 << (log2n - batch_log2e(log2n)));
 }
-__host__ __device__ constexpr int perm_word(int e) { return e + (e >> 5); }
+__host__ __device__ constexpr int perm_word(int e, int log2e) { return e + (e >> log2e); }
 
 // ---------------------------------------------------------------- transform
 struct BatchParams {
@@ -134,33 +146,47 @@ struct BatchMath {
   static constexpr int LOG2E = batch_log2e(LOG2N);
   static constexpr int E = 1 << LOG2E;
   static constexpr int L = N / E;
+  static constexpr int K = batch_k(LOG2N);
+  using Blocks = int32_t[K][E];
 
   template <int P>
-  __device__ __forceinline__ static void bfly(int32_t (&v)[E], int jl, int c, int d1, int d2,
+  __device__ __forceinline__ static void bfly(Blocks& v, int jl, int c, int d1, int d2,
                                               uint32_t half, int f) {
     const int im = ((jl >> P) << (P + 1)) | (jl & ((1 << P) - 1));
     const int in = im | (1 << P);
-    const uint32_t ua = (uint32_t)v[im], ub = (uint32_t)v[in];
-    const uint32_t k = (uint32_t)c * (ua + ub) + half;
     const uint32_t e1 = (uint32_t)(INV ? d2 : d1);
     const uint32_t e2 = (uint32_t)(INV ? d1 : d2);
-    v[im] = (int32_t)(k + e1 * ub) >> f;
-    v[in] = (int32_t)(k + e2 * ua) >> f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const uint32_t ua = (uint32_t)v[k][im], ub = (uint32_t)v[k][in];
+      const uint32_t kk = (uint32_t)c * (ua + ub) + half;
+      v[k][im] = (int32_t)(kk + e1 * ub) >> f;
+      v[k][in] = (int32_t)(kk + e2 * ua) >> f;
+    }
   }
 
   // Register pass p: the lane's pairs are lane * E/2 + jl; `row` holds N/2
-  // entries of 3 words.
+  // entries of 3 words.  The multipliers of 4 pairs (three 16-byte loads) are
+  // fetched one group ahead of their use; the empty asm statements with a
+  // memory clobber keep the compiler from hoisting loads further (which
+  // would cost registers the K blocks need).
   template <int P>
-  __device__ __forceinline__ static void reg_pass(int32_t (&v)[E], const int* row, int lane,
+  __device__ __forceinline__ static void reg_pass(Blocks& v, const int* row, int lane,
                                                   uint32_t half, int f) {
     constexpr int NP = E / 2;
     const int* base = row + 3 * lane * NP;
     if constexpr (NP % 4 == 0) {
+      const int4* b4 = reinterpret_cast<const int4*>(base);
+      int4 na = b4[0], nb = b4[1], nc = b4[2];
 #pragma unroll
       for (int q = 0; q < NP / 4; ++q) {
-        const int4 a = reinterpret_cast<const int4*>(base)[3 * q];
-        const int4 b = reinterpret_cast<const int4*>(base)[3 * q + 1];
-        const int4 c = reinterpret_cast<const int4*>(base)[3 * q + 2];
+        const int4 a = na, b = nb, c = nc;
+        if (q + 1 < NP / 4) {
+          na = b4[3 * (q + 1)];
+          nb = b4[3 * (q + 1) + 1];
+          nc = b4[3 * (q + 1) + 2];
+        }
+        asm volatile("" ::: "memory");
         bfly<P>(v, 4 * q + 0, a.x, a.y, a.z, half, f);
         bfly<P>(v, 4 * q + 1, a.w, b.x, b.y, half, f);
         bfly<P>(v, 4 * q + 2, b.z, b.w, c.x, half, f);
@@ -179,7 +205,7 @@ struct BatchMath {
   // lanes of a pair read different banks); this lane's E elements use pairs
   // jbase + i of its side.
   template <int P>
-  __device__ __forceinline__ static void lane_pass(int32_t (&v)[E], const int* row, int lane,
+  __device__ __forceinline__ static void lane_pass(Blocks& v, const int* row, int lane,
                                                    uint32_t half, int f) {
     constexpr int Q = P - LOG2E;
     constexpr int D = 1 << Q;
@@ -191,18 +217,22 @@ struct BatchMath {
 #pragma unroll
     for (int i = 0; i < E; i += 2) {
       const int4 cs = base[i];  // chunk 2 ((jbase + i) / 2) + side
-      const int32_t p0 = __shfl_xor_sync(kFullMask, v[i], D);
-      const int32_t p1 = __shfl_xor_sync(kFullMask, v[i + 1], D);
-      const uint32_t u0 = (uint32_t)cs.x * (uint32_t)v[i] + (uint32_t)cs.y * (uint32_t)p0 + half;
-      const uint32_t u1 =
-          (uint32_t)cs.z * (uint32_t)v[i + 1] + (uint32_t)cs.w * (uint32_t)p1 + half;
-      v[i] = (int32_t)u0 >> f;
-      v[i + 1] = (int32_t)u1 >> f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int32_t p0 = __shfl_xor_sync(kFullMask, v[k][i], D);
+        const int32_t p1 = __shfl_xor_sync(kFullMask, v[k][i + 1], D);
+        const uint32_t u0 =
+            (uint32_t)cs.x * (uint32_t)v[k][i] + (uint32_t)cs.y * (uint32_t)p0 + half;
+        const uint32_t u1 =
+            (uint32_t)cs.z * (uint32_t)v[k][i + 1] + (uint32_t)cs.w * (uint32_t)p1 + half;
+        v[k][i] = (int32_t)u0 >> f;
+        v[k][i + 1] = (int32_t)u1 >> f;
+      }
     }
   }
 
   template <int P>
-  __device__ __forceinline__ static void pass(int32_t (&v)[E], const int* rtab, int lane,
+  __device__ __forceinline__ static void pass(Blocks& v, const int* rtab, int lane,
                                               uint32_t half, int f) {
     constexpr SetTableShape sh{LOG2N, LOG2E, 1, 0};
     const int* row = rtab + sh.pass_offset(P);
@@ -213,12 +243,12 @@ struct BatchMath {
   }
 
   // All passes of one round: increasing p forward, decreasing p inverse.
-  template <int K>
-  __device__ __forceinline__ static void round(int32_t (&v)[E], const int* rtab, int lane,
+  template <int J>
+  __device__ __forceinline__ static void round(Blocks& v, const int* rtab, int lane,
                                                uint32_t half, int f) {
-    if constexpr (K < LOG2N) {
-      pass<INV ? (LOG2N - 1 - K) : K>(v, rtab, lane, half, f);
-      round<K + 1>(v, rtab, lane, half, f);
+    if constexpr (J < LOG2N) {
+      pass<INV ? (LOG2N - 1 - J) : J>(v, rtab, lane, half, f);
+      round<J + 1>(v, rtab, lane, half, f);
     }
   }
 };
@@ -269,25 +299,28 @@ __device__ __forceinline__ int bucket_of_slot(const int* starts, int num_sets, i
 
 // The tasks [t0, t1) of one warp.  `cache` holds the tables of sets
 // [set_lo, set_lo + cached count) when CACHED, else tables are read from
-// global memory.
+// global memory.  `pbuf` is the warp's part of the permutation buffer: G
+// block regions of perm_region_words(LOG2N) words.
 template <int LOG2N, int KIND, bool CACHED>
 __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, long long t1,
-                                            const int* cache, int set_lo, int32_t* region) {
+                                            const int* cache, int set_lo, int32_t* pbuf) {
   using M = BatchMath<LOG2N, KIND == 1>;
   constexpr int E = M::E;
   constexpr int L = M::L;
-  constexpr int G = 32 / L;
+  constexpr int K = M::K;
+  constexpr int GROUPS = 32 / L;
+  constexpr int G = GROUPS * K;
+  constexpr int RW = perm_region_words(LOG2N);
   constexpr bool INV = (KIND == 1);
   const int lane32 = threadIdx.x & 31;
   const int lane = lane32 % L;
-  const int sub = lane32 / L;
+  const int grp = lane32 / L;
   const uint32_t half = 1u << (p.frac_bits - 1);
   const int f = p.frac_bits;
   const int R = p.rounds;
   const int S = p.num_sets;
   const SetTableShape sh{LOG2N, M::LOG2E, R, p.perms};
   const int rw = sh.round_words();
-  char* rb = reinterpret_cast<char*>(region);  // this block's permutation region
 
   int bucket = 0, bucket_end = 0;
   for (long long t = t0; t < t1; ++t) {
@@ -296,14 +329,19 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
       bucket = bucket_of_slot(p.starts, S, slot);
       bucket_end = __ldg(p.starts + bucket + 1);
     }
-    const int b = __ldg(p.order + slot + sub);
-    const bool active = b >= 0 && b < p.nblocks;
-    int32_t v[E];
-    if (active) {
-      batch_load<LOG2N, KIND>(p, b, lane, v);
-    } else {
+    int b[K];
+    bool active[K];
+    int32_t v[K][E];
 #pragma unroll
-      for (int i = 0; i < E; ++i) v[i] = 0;
+    for (int k = 0; k < K; ++k) {
+      b[k] = __ldg(p.order + slot + k * GROUPS + grp);
+      active[k] = b[k] >= 0 && b[k] < p.nblocks;
+      if (active[k]) {
+        batch_load<LOG2N, KIND>(p, b[k], lane, v[k]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < E; ++i) v[k][i] = 0;
+      }
     }
     if (bucket < S) {
       const int* stab = CACHED ? cache + (size_t)(bucket - set_lo) * p.set_words
@@ -314,28 +352,56 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
         const int* prow = stab + sh.perm_offset(r) + lane * E;
         if (INV && has_perm) {  // undo the gather of slot r: v_prev[perm[e]] = v[e]
 #pragma unroll
-          for (int i = 0; i < E; ++i) *reinterpret_cast<int32_t*>(rb + perm_at<E>(prow, i)) = v[i];
+          for (int k = 0; k < K; ++k) {
+            int32_t* region = pbuf + (k * GROUPS + grp) * RW;
+            char* rb = reinterpret_cast<char*>(region);
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+              *reinterpret_cast<int32_t*>(rb + perm_at<E>(prow, i)) = v[k][i];
+              if ((i & 3) == 3) asm volatile("" ::: "memory");
+            }
+          }
           __syncwarp();
 #pragma unroll
-          for (int i = 0; i < E; ++i) v[i] = region[perm_word(lane * E + i)];
+          for (int k = 0; k < K; ++k) {
+            const int32_t* region = pbuf + (k * GROUPS + grp) * RW;
+#pragma unroll
+            for (int i = 0; i < E; ++i) v[k][i] = region[perm_word(lane * E + i, M::LOG2E)];
+          }
           __syncwarp();
         }
         M::template round<0>(v, stab + r * rw, lane, half, f);
         if (!INV && has_perm) {  // gather: v'[e] = v[perm[e]]
 #pragma unroll
-          for (int i = 0; i < E; ++i) region[perm_word(lane * E + i)] = v[i];
+          for (int k = 0; k < K; ++k) {
+            int32_t* region = pbuf + (k * GROUPS + grp) * RW;
+#pragma unroll
+            for (int i = 0; i < E; ++i) region[perm_word(lane * E + i, M::LOG2E)] = v[k][i];
+          }
           __syncwarp();
 #pragma unroll
-          for (int i = 0; i < E; ++i) v[i] = *reinterpret_cast<const int32_t*>(rb + perm_at<E>(prow, i));
+          for (int k = 0; k < K; ++k) {
+            const char* rb = reinterpret_cast<const char*>(pbuf + (k * GROUPS + grp) * RW);
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+              v[k][i] = *reinterpret_cast<const int32_t*>(rb + perm_at<E>(prow, i));
+              if ((i & 3) == 3) asm volatile("" ::: "memory");
+            }
+          }
           __syncwarp();
         }
       }
     } else if (bucket == S + 1) {  // bad set index: zeros, status
 #pragma unroll
-      for (int i = 0; i < E; ++i) v[i] = 0;
-      if (active && lane == 0 && p.status) atomicCAS(p.status, 0, 4);
+      for (int k = 0; k < K; ++k) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) v[k][i] = 0;
+        if (active[k] && lane == 0 && p.status) atomicCAS(p.status, 0, 4);
+      }
     }
-    if (active) batch_store<LOG2N, KIND>(p, b, lane, v);
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (active[k]) batch_store<LOG2N, KIND>(p, b[k], lane, v[k]);
   }
 }
 
@@ -347,7 +413,6 @@ template <int LOG2N, int KIND>
 __device__ __forceinline__ void batch_cta(const BatchParams& p, long long cta, long long ncta,
                                           int32_t* smem) {
   constexpr int G = batch_group(LOG2N);
-  constexpr int L = 32 / G;
   constexpr int RW = perm_region_words(LOG2N);
 
   // The schedule must have been built for this block count, set count and G.
@@ -386,11 +451,11 @@ __device__ __forceinline__ void batch_cta(const BatchParams& p, long long cta, l
   }
   __syncthreads();
 
-  int32_t* region = pbuf + (size_t)(warp * G + (threadIdx.x & 31) / L) * RW;
+  int32_t* wbuf = pbuf + (size_t)warp * G * RW;
   if (cached)
-    batch_tasks<LOG2N, KIND, true>(p, t0, t1, cache, set_lo, region);
+    batch_tasks<LOG2N, KIND, true>(p, t0, t1, cache, set_lo, wbuf);
   else
-    batch_tasks<LOG2N, KIND, false>(p, t0, t1, cache, set_lo, region);
+    batch_tasks<LOG2N, KIND, false>(p, t0, t1, cache, set_lo, wbuf);
 }
 
 // Dynamic shared memory of batch_cta for block size 2^LOG2N: permutation

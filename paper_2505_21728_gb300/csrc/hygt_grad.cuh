@@ -55,11 +55,16 @@ struct GradMap {
   static constexpr int G = 32 / L;
 };
 
-// Shared memory: accumulators [warps][G][angles] floats, then the
-// permutation scratch [warps][32 * E] (y) and [warps][32 * E] (g).
+// Shared memory: accumulators [warps][G][angles + pad] floats, then the
+// permutation scratch [warps][32 * E] (y) and [warps][32 * E] (g).  The
+// accumulator stride is padded to an odd multiple of the 4-word lane step,
+// so the G block slots of a warp, updating the same angle index, use
+// different banks.
+__host__ __device__ inline int grad_acc_stride(int angles) { return ((angles + 3) & ~3) + 4 + 1; }
+
 template <int LOG2N>
 __host__ __device__ inline size_t grad_smem_bytes(int warps, int angles) {
-  return (size_t)warps * GradMap<LOG2N>::G * angles * 4 +
+  return (size_t)warps * GradMap<LOG2N>::G * grad_acc_stride(angles) * 4 +
          (size_t)warps * 2 * 32 * GradMap<LOG2N>::E * 4;
 }
 
@@ -128,11 +133,12 @@ __global__ void __launch_bounds__(kGradThreadsMax) hygt_grad_kernel(GradParams p
   const int lane32 = threadIdx.x & 31;
   const int sub = lane32 / L;
   const int lane = lane32 % L;
+  const int stride = grad_acc_stride(p.angles);
   float* acc_all = gsm;
-  float* acc = acc_all + (size_t)(warp * G + sub) * p.angles;
-  float* ybuf = gsm + (size_t)warps * G * p.angles + (size_t)warp * 2 * 32 * E + sub * N;
+  float* acc = acc_all + (size_t)(warp * G + sub) * stride;
+  float* ybuf = gsm + (size_t)warps * G * stride + (size_t)warp * 2 * 32 * E + sub * N;
   float* gbuf = ybuf + 32 * E;
-  for (int i = threadIdx.x; i < warps * G * p.angles; i += blockDim.x) acc_all[i] = 0.f;
+  for (int i = threadIdx.x; i < warps * G * stride; i += blockDim.x) acc_all[i] = 0.f;
   __syncthreads();
 
   const long long warps_total = (long long)gridDim.x * warps;
@@ -196,7 +202,7 @@ __global__ void __launch_bounds__(kGradThreadsMax) hygt_grad_kernel(GradParams p
   // CTA partial: sum of all (warp, block slot) accumulators, in FP64, fixed order
   for (int a = threadIdx.x; a < p.angles; a += blockDim.x) {
     double s = 0.0;
-    for (int k = 0; k < warps * G; ++k) s += (double)acc_all[(size_t)k * p.angles + a];
+    for (int k = 0; k < warps * G; ++k) s += (double)acc_all[(size_t)k * stride + a];
     p.partials[(size_t)blockIdx.x * p.angles + a] = s;
   }
 }
