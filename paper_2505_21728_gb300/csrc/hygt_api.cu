@@ -122,15 +122,16 @@ hygt_status upload_perms(hygt_plan p, const std::vector<uint8_t>& perm, unsigned
 }
 
 // Per-set tables of the batch kernels (layout: hygt::SetTableShape).  Register
-// passes store (c, s - c, -(c + s)); lane passes store (c, s) for the m side
-// and (c, -s) for the n side of each pair, in alternating 16-byte chunks of
-// two pairs; then the permutation gather sources as byte offsets in a
-// block's permutation region.
+// passes store (c, s - c, -(c + s)) per pair in per-lane segments; lane passes
+// store (c, s) for the m side and (c, -s) for the n side of each pair; then
+// the permutation gather sources as byte offsets in a block's permutation
+// region, per lane.
 void build_ktab(int log2n, int rounds, int num_sets, const uint8_t* q, const std::vector<int>& ct,
                 const std::vector<int>& st, const std::vector<uint8_t>& perm, unsigned mask,
                 std::vector<int>* out, int* words) {
   const int N = 1 << log2n;
   const hygt::SetTableShape sh{log2n, hygt::batch_log2e(log2n), rounds, mask ? 1 : 0};
+  const int E = sh.e();
   const int w = (sh.set_words() + 3) & ~3;
   *words = w;
   out->assign((size_t)num_sets * w, 0);
@@ -142,16 +143,18 @@ void build_ktab(int log2n, int rounds, int num_sets, const uint8_t* q, const std
         const uint8_t* qa = q + (((size_t)s * rounds + r) * log2n + p) * (N / 2);
         for (int j = 0; j < N / 2; ++j) {
           const int c = ct[qa[j]], sn = st[qa[j]];
-          if (p < sh.log2e) {
-            row[3 * j] = c;
-            row[3 * j + 1] = sn - c;
-            row[3 * j + 2] = -(c + sn);
-          } else {  // chunk 2 (j/2) + side holds pairs j & ~1, j | 1 of that side
-            const int w0 = 8 * (j >> 1) + 2 * (j & 1);
-            row[w0] = c;  // m side
-            row[w0 + 1] = sn;
-            row[w0 + 4] = c;  // n side
-            row[w0 + 5] = -sn;
+          if (p < sh.log2e) {  // lane j / (E/2), pair j mod (E/2) of its segment
+            int* e3 = row + (j / (E / 2)) * sh.seg() + 3 * (j % (E / 2));
+            e3[0] = c;
+            e3[1] = sn - c;
+            e3[2] = -(c + sn);
+          } else {
+            int* m = row + sh.lane_word(j, 0);
+            int* n = row + sh.lane_word(j, 1);
+            m[0] = c;
+            m[1] = sn;
+            n[0] = c;
+            n[1] = -sn;
           }
         }
       }
@@ -159,7 +162,7 @@ void build_ktab(int log2n, int rounds, int num_sets, const uint8_t* q, const std
         int* prow = t + sh.perm_offset(r);
         for (int i = 0; i < N; ++i) {
           const int src = perm.empty() ? i : perm[((size_t)s * rounds + r) * N + i];
-          prow[i] = 4 * hygt::perm_word(src, sh.log2e);
+          prow[(i / E) * sh.perm_seg() + (i % E)] = 4 * hygt::perm_word(src, sh.log2e);
         }
       }
     }

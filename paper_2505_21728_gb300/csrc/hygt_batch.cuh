@@ -87,26 +87,42 @@ __host__ __device__ inline BatchLayout batch_layout(int num_sets, long long nblo
 
 // ---------------------------------------------------------------- tables
 // Per-set multiplier table of the batch kernels (int32 words), for block
-// size 2^LOG2N and LOG2E = batch_log2e(LOG2N):
+// size 2^LOG2N, E = 2^log2e values per lane and L = N / E lanes per block:
 //   for each round r, for each pass p:
-//     p <  LOG2E: N/2 entries (c, s - c, -(c + s))       (3 words)
-//     p >= LOG2E: for each pair j, (c, s) for its m side and (c, -s) for
-//                 its n side, laid out so that 16-byte chunk 2 (j/2) + side
-//                 holds pairs j & ~1 and j | 1 of that side (2 + 2 words)
-//   then, if the plan permutes, for each round r: N byte offsets of the
-//   gather source of element i in a block's permutation region.
+//     p <  log2e: lane l's E/2 pairs (c, s - c, -(c + s)) (3 words each) in a
+//                 segment of seg() words starting at l * seg();
+//     p >= log2e: for each pair j, (c, s) for its m side and (c, -s) for its
+//                 n side; 16-byte chunk c = 2 (j / 2) + side holds pairs
+//                 j & ~1 and j | 1 of that side and is stored at chunk
+//                 c + 2 ((c / E) mod 4);
+//   then, if the plan permutes, for each round r: lane l's E gather sources
+//   (byte offsets in a block's permutation region) at l * (E + 4).
+// The segment strides are odd numbers of 16-byte chunks and the chunk skew
+// spreads the (up to 8) lanes of a block over distinct bank groups.
 struct SetTableShape {
   int log2n, log2e, rounds, perms;
-  __host__ __device__ constexpr int half() const { return 1 << (log2n - 1); }
+  __host__ __device__ constexpr int n() const { return 1 << log2n; }
+  __host__ __device__ constexpr int e() const { return 1 << log2e; }
+  __host__ __device__ constexpr int lanes() const { return 1 << (log2n - log2e); }
+  __host__ __device__ constexpr int seg() const {
+    return e() >= 8 ? ((3 * e() / 2 + 3) / 4 | 1) * 4 : 3 * e() / 2;
+  }
+  __host__ __device__ constexpr int reg_row() const { return lanes() * seg(); }
+  __host__ __device__ constexpr int lane_row() const { return 2 * n() + 24; }
+  __host__ __device__ constexpr int perm_seg() const { return e() >= 4 ? e() + 4 : e(); }
   __host__ __device__ constexpr int pass_offset(int p) const {
-    return half() * (3 * (p < log2e ? p : log2e) + 4 * (p < log2e ? 0 : p - log2e));
+    return reg_row() * (p < log2e ? p : log2e) + lane_row() * (p < log2e ? 0 : p - log2e);
   }
   __host__ __device__ constexpr int round_words() const { return pass_offset(log2n); }
   __host__ __device__ constexpr int perm_offset(int r) const {
-    return rounds * round_words() + r * (1 << log2n);
+    return rounds * round_words() + r * lanes() * perm_seg();
   }
   __host__ __device__ constexpr int set_words() const {
-    return rounds * round_words() + (perms ? rounds * (1 << log2n) : 0);
+    return rounds * round_words() + (perms ? rounds * lanes() * perm_seg() : 0);
+  }
+  // word of entry (c, s') of pair j on `side` in a lane-pass row
+  __host__ __device__ constexpr int lane_word(int j, int side) const {
+    return 4 * ((2 * (j / 2) + side) + 2 * (((2 * (j / 2) + side) / e()) & 3)) + 2 * (j & 1);
   }
 };
 
@@ -174,7 +190,8 @@ struct BatchMath {
   __device__ __forceinline__ static void reg_pass(Blocks& v, const int* row, int lane,
                                                   uint32_t half, int f) {
     constexpr int NP = E / 2;
-    const int* base = row + 3 * lane * NP;
+    constexpr SetTableShape sh{LOG2N, LOG2E, 1, 0};
+    const int* base = row + lane * sh.seg();
     if constexpr (NP % 4 == 0) {
       const int4* b4 = reinterpret_cast<const int4*>(base);
       int4 na = b4[0], nb = b4[1], nc = b4[2];
@@ -200,10 +217,8 @@ struct BatchMath {
   }
 
   // Lane pass p: partner lane = lane ^ 2^(p - LOG2E).  `row` holds (c, s)
-  // for the m side and (c, -s) for the n side of each pair, two pairs of one
-  // side per 16-byte chunk, the sides alternating chunk by chunk (so the two
-  // lanes of a pair read different banks); this lane's E elements use pairs
-  // jbase + i of its side.
+  // for the m side and (c, -s) for the n side of each pair (layout in
+  // SetTableShape); this lane's E elements use pairs jbase + i of its side.
   template <int P>
   __device__ __forceinline__ static void lane_pass(Blocks& v, const int* row, int lane,
                                                    uint32_t half, int f) {
@@ -213,10 +228,13 @@ struct BatchMath {
     const int jbase = ((lane >> (Q + 1)) << P) + ((lane & (D - 1)) << LOG2E);
     // forward: m side (c, s), n side (c, -s); inverse: the opposite
     const int side = upper ^ (INV ? 1 : 0);
-    const int4* base = reinterpret_cast<const int4*>(row + 4 * jbase + 4 * side);
+    // chunk c = jbase + i + side (i even) is stored at c + 2 ((c / E) mod 4);
+    // c / E = jbase / E for every i of this lane
+    const int skew = 2 * ((jbase >> LOG2E) & 3);
+    const int4* base = reinterpret_cast<const int4*>(row) + jbase + side + skew;
 #pragma unroll
     for (int i = 0; i < E; i += 2) {
-      const int4 cs = base[i];  // chunk 2 ((jbase + i) / 2) + side
+      const int4 cs = base[i];
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const int32_t p0 = __shfl_xor_sync(kFullMask, v[k][i], D);
@@ -349,7 +367,7 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
       for (int rr = 0; rr < R; ++rr) {
         const int r = INV ? (R - 1 - rr) : rr;
         const bool has_perm = p.perms && ((p.perm_mask >> r) & 1u);
-        const int* prow = stab + sh.perm_offset(r) + lane * E;
+        const int* prow = stab + sh.perm_offset(r) + lane * sh.perm_seg();
         if (INV && has_perm) {  // undo the gather of slot r: v_prev[perm[e]] = v[e]
 #pragma unroll
           for (int k = 0; k < K; ++k) {
