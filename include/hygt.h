@@ -64,7 +64,8 @@ typedef enum hygt_status {
   HYGT_ERR_CUDA = 2,        /* a CUDA runtime call or launch failed */
   HYGT_ERR_OOM = 3,         /* device allocation failed */
   HYGT_ERR_SET_INDEX = 4,   /* device: set index >= num_sets and != HYGT_SKIP_SET */
-  HYGT_ERR_UNSUPPORTED = 6  /* plan kind does not support this call */
+  HYGT_ERR_UNSUPPORTED = 6, /* plan kind does not support this call */
+  HYGT_ERR_TOO_LARGE = 7    /* batch larger than the static scratch of hygt_forward_static */
 } hygt_status;
 
 #define HYGT_SKIP_SET 0xFFFFu
@@ -271,6 +272,36 @@ hygt_status dense_klt_build(dense_klt d, const uint16_t *d_set, int64_t nblocks,
                             size_t work_bytes, hygt_stream stream);
 hygt_status dense_klt_apply(dense_klt d, const void *d_work, const int16_t *d_x, void *d_y,
                             int64_t nblocks, int kind, hygt_stream stream, int *d_status);
+
+/*
+ * Bucketing plus integer forward transform with no device allocation.  The
+ * paper has no counterpart: this is a calling convention of this library.
+ *
+ * Some callers cannot allocate device memory when they transform -- code
+ * that runs where cudaMalloc is not allowed or not wanted (a real-time
+ * encode loop, a host process that owns no device allocator, a library
+ * layered under another runtime) -- so they cannot provide the workspace
+ * that hygt_batch_build needs.  hygt_forward_static does the same work as
+ * hygt_batch_build followed by hygt_forward_batch (same results, bit for
+ * bit), with the schedule in a fixed 8 MiB array that the library holds in
+ * the global memory of every GPU that loads it, until the process exits.
+ *
+ *   - The caller passes the plan (created beforehand), d_x, d_y, d_set and
+ *     d_status exactly as for hygt_forward.
+ *   - nblocks must satisfy hygt_batch_workspace_bytes(plan, nblocks) <=
+ *     8,388,608 (about 2 million 8x8 blocks for 105 sets); larger batches
+ *     return HYGT_ERR_TOO_LARGE before anything is launched.
+ *   - The call itself allocates nothing.  Its first call on a device looks
+ *     up the address of that device's array (cudaGetSymbolAddress) with
+ *     the device current; make that first call before any stream capture.
+ *   - All calls share the array and it keeps the last call's schedule; each
+ *     call rebuilds the parts that must start at zero.  Calls whose work
+ *     overlaps on the GPU (other streams, other host threads) race on the
+ *     array: order them.
+ */
+hygt_status hygt_forward_static(hygt_plan plan, const int16_t *d_x, int32_t *d_y,
+                                const uint16_t *d_set, int64_t nblocks, hygt_stream stream,
+                                int *d_status);
 
 /* Plan shape: any out-pointer may be NULL. */
 hygt_status hygt_plan_info(hygt_plan plan, int *log2n, int *rounds, int *num_sets,

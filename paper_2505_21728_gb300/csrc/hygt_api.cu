@@ -755,8 +755,63 @@ const char* hygt_status_string(int status) {
     case HYGT_ERR_OOM: return "device allocation failed";
     case HYGT_ERR_SET_INDEX: return "set index out of range";
     case HYGT_ERR_UNSUPPORTED: return "operation not supported by this plan";
+    case HYGT_ERR_TOO_LARGE: return "batch larger than the static scratch (8 MiB)";
     default: return "unknown status";
   }
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- no allocation
+// hygt_forward_static: the schedule lives in a file-scope device array
+// instead of a caller workspace.  Host code cannot use the array's name as a
+// device address (in host code it names a host-side stand-in), so the
+// address is looked up once per device with cudaGetSymbolAddress, with that
+// device current, and cached.
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)8 << 20;
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxDevices] = {};
+
+hygt_status static_scratch(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HYGT_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) return HYGT_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return HYGT_ERR_CUDA;
+    }
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return HYGT_OK;
+}
+
+}  // namespace
+
+extern "C" hygt_status hygt_forward_static(hygt_plan plan, const int16_t* d_x, int32_t* d_y,
+                                           const uint16_t* d_set, int64_t nblocks,
+                                           hygt_stream stream, int* d_status) {
+  hygt_status s = check_io(plan, d_x, d_y, nblocks);
+  if (s != HYGT_OK || nblocks == 0) return s;
+  if (plan->is_float) return HYGT_ERR_UNSUPPORTED;
+  if (nblocks > kBatchMaxBlocks) return HYGT_ERR_TOO_LARGE;
+  const int group = hygt::batch_group(plan->log2n);
+  if (hygt::batch_layout(plan->num_sets, nblocks, group).total > kStaticScratchBytes)
+    return HYGT_ERR_TOO_LARGE;
+  void* work = nullptr;
+  s = static_scratch(&work);
+  if (s != HYGT_OK) return s;
+  cudaError_t e =
+      hygt::batch_build(d_set, nblocks, plan->num_sets, group, work, (cudaStream_t)stream);
+  if (e != cudaSuccess) return to_status(e);
+  const hygt::BatchParams p = make_batch_params(plan, work, d_x, d_y, nblocks, d_status);
+  return to_status(hygt::launch_batch_fwd(plan->log2n, p, (cudaStream_t)stream));
+}

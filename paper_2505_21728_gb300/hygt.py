@@ -23,6 +23,7 @@ HYGT_ERR_CUDA = 2
 HYGT_ERR_OOM = 3
 HYGT_ERR_SET_INDEX = 4
 HYGT_ERR_UNSUPPORTED = 6
+HYGT_ERR_TOO_LARGE = 7
 HYGT_SKIP_SET = 0xFFFF
 DENSE_KLT_BF16 = 0
 DENSE_KLT_INT = 1
@@ -66,6 +67,8 @@ def _load() -> ctypes.CDLL:
         f = getattr(L, name)
         f.argtypes = [P, P, P, P, i64, P, P]
         f.restype = i32
+    L.hygt_forward_static.argtypes = [P, P, P, P, i64, P, P]
+    L.hygt_forward_static.restype = i32
     L.hygt_update_theta.argtypes = [P, P, P]
     L.hygt_update_theta.restype = i32
     L.hygt_backward_workspace_bytes.argtypes = [P, i64]
@@ -176,6 +179,10 @@ def hygt_forward_batch(plan, d_work, d_x, d_y, nblocks, stream, d_status):
 
 def hygt_inverse_batch(plan, d_work, d_y, d_x, nblocks, stream, d_status):
     return int(_lib.hygt_inverse_batch(plan, d_work, d_y, d_x, nblocks, stream, d_status))
+
+
+def hygt_forward_static(plan, d_x, d_y, d_set, nblocks, stream, d_status):
+    return int(_lib.hygt_forward_static(plan, d_x, d_y, d_set, nblocks, stream, d_status))
 
 
 def hygt_update_theta(plan, d_theta, stream):

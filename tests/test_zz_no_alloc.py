@@ -1,0 +1,58 @@
+"""hygt_forward_static: the integer forward for callers that cannot allocate
+device memory when they transform (it keeps its schedule in a fixed array
+the library holds on every GPU, instead of a caller workspace).
+
+Its output must equal the workspace path (hygt_batch_build +
+hygt_forward_batch) bit for bit, on two calls in a row (the array keeps the
+previous call's schedule), and a batch larger than the array must be
+refused before anything runs.  This file is collected last on purpose.
+"""
+import numpy as np
+import pytest
+
+from paper_2505_21728_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _t(a):
+    import torch
+    if a.dtype == np.uint16:
+        a = a.view(np.int16)
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def test_static_scratch_forward_matches_workspace_path(gpu):
+    import torch
+    log2n, rounds, S = 6, 2, 105
+    q = inputs.angle_indices(S, rounds, log2n, seed=21)
+    perms = inputs.permutations(S, rounds, 64, seed=21)
+    plan = gpu.Plan(log2n, rounds, q, perms)
+    stream = torch.cuda.current_stream().cuda_stream
+    for call, B in enumerate([200003, 77777]):  # two calls in a row, different sizes
+        x = inputs.laplacian_blocks(B, 64, 8.0, -1024, 1023, seed=30 + call)
+        sets = inputs.set_indices(B, S, seed=30 + call, skip_frac=0.1)
+        dx, ds = _t(x), _t(sets)
+        ref = gpu.Batch(plan, B).build(ds).forward(dx)
+        y = torch.full((B, 64), -7, dtype=torch.int32, device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        code = gpu.hygt_forward_static(plan.handle, dx.data_ptr(), y.data_ptr(), ds.data_ptr(),
+                                       B, stream, st.data_ptr())
+        assert code == gpu.HYGT_OK
+        torch.cuda.synchronize()
+        assert int(st.item()) == 0
+        assert torch.equal(y, ref)
+
+
+def test_static_scratch_rejects_oversized_batch(gpu):
+    import torch
+    q = inputs.angle_indices(4, 2, 6, seed=1)
+    plan = gpu.Plan(6, 2, q)
+    B = 4_000_000  # schedule larger than the 8 MiB array
+    assert gpu.hygt_batch_workspace_bytes(plan.handle, B) > 8 << 20
+    x = torch.zeros((16, 64), dtype=torch.int16, device="cuda")
+    y = torch.zeros((16, 64), dtype=torch.int32, device="cuda")
+    code = gpu.hygt_forward_static(plan.handle, x.data_ptr(), y.data_ptr(), None, B,
+                                   torch.cuda.current_stream().cuda_stream, None)
+    assert code == gpu.HYGT_ERR_TOO_LARGE
+    assert "static scratch" in gpu.hygt_status_string(code)
