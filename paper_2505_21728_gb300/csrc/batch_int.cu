@@ -162,8 +162,8 @@ static cudaError_t launch_batch_sized(BatchParams p, cudaStream_t stream) {
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
   const DeviceInfo info = device_info(dev);
-  constexpr int G = batch_group(LOG2N);
-  const size_t pbuf = batch_pbuf_bytes<LOG2N>(kBatchThreads);
+  constexpr int G = batch_task_group(LOG2N, KIND == 1);
+  const size_t pbuf = batch_pbuf_bytes<LOG2N, KIND>(kBatchThreads);
   const size_t set_bytes = (size_t)p.set_words * 4;
   long long fit = ((long long)info.max_smem_optin - (long long)pbuf) / (long long)set_bytes;
   if (fit > 64) fit = 64;

@@ -44,15 +44,22 @@ constexpr int kBucketTile = 8192;    // blocks per CTA tile in the scatter pass
 
 // Layout for block size 2^log2n: E = 2^batch_log2e values of a block per
 // lane, L = N / E lanes per block (a lane group), K = batch_k blocks of the
-// same set per lane group, G = (32 / L) K blocks per warp task.
+// same set per lane group, so a warp task is (32 / L) K blocks.  K may differ
+// between the directions; the schedule's group G = batch_group is a multiple
+// of both task sizes, so one schedule serves the forward and the inverse.
 __host__ __device__ constexpr int batch_log2e(int log2n) {
   return log2n <= 4 ? log2n : (log2n <= 6 ? 4 : 5);
 }
-__host__ __device__ constexpr int batch_k(int log2n) {
-  return log2n <= 2 ? 1 : (log2n == 5 || log2n == 6 ? 4 : 2);
+__host__ __device__ constexpr int batch_k(int log2n, bool inv) {
+  return log2n <= 2 ? 1 : (log2n == 5 || log2n == 6) ? (inv ? 2 : 4) : 2;
+}
+__host__ __device__ constexpr int batch_task_group(int log2n, bool inv) {
+  return (32 >> (log2n - batch_log2e(log2n))) * batch_k(log2n, inv);
 }
 __host__ __device__ constexpr int batch_group(int log2n) {
-  return (32 >> (log2n - batch_log2e(log2n))) * batch_k(log2n);
+  return batch_task_group(log2n, false) > batch_task_group(log2n, true)
+             ? batch_task_group(log2n, false)
+             : batch_task_group(log2n, true);
 }
 
 // Workspace layout (all offsets in bytes, 16-byte aligned sections):
@@ -162,7 +169,7 @@ struct BatchMath {
   static constexpr int LOG2E = batch_log2e(LOG2N);
   static constexpr int E = 1 << LOG2E;
   static constexpr int L = N / E;
-  static constexpr int K = batch_k(LOG2N);
+  static constexpr int K = batch_k(LOG2N, INV);
   using Blocks = int32_t[K][E];
 
   template <int P>
@@ -430,15 +437,16 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
 template <int LOG2N, int KIND>
 __device__ __forceinline__ void batch_cta(const BatchParams& p, long long cta, long long ncta,
                                           int32_t* smem) {
-  constexpr int G = batch_group(LOG2N);
+  constexpr int GS = batch_group(LOG2N);                 // schedule group
+  constexpr int G = batch_task_group(LOG2N, KIND == 1);  // this kernel's task size
   constexpr int RW = perm_region_words(LOG2N);
 
   // The schedule must have been built for this block count, set count and G.
-  if (p.meta[1] != (int)p.nblocks || p.meta[2] != p.num_sets || p.meta[3] != G) {
+  if (p.meta[1] != (int)p.nblocks || p.meta[2] != p.num_sets || p.meta[3] != GS) {
     if (threadIdx.x == 0 && cta == 0 && p.status) atomicCAS(p.status, 0, 1);
     return;
   }
-  const long long ntasks = max(0LL, min((long long)p.meta[0], p.tmax));
+  const long long ntasks = max(0LL, min((long long)p.meta[0], p.tmax)) * (GS / G);
   const int wpc = blockDim.x >> 5;
   const long long warps_total = ncta * wpc;
   const long long chunk = (ntasks + warps_total - 1) / warps_total;
@@ -476,11 +484,12 @@ __device__ __forceinline__ void batch_cta(const BatchParams& p, long long cta, l
     batch_tasks<LOG2N, KIND, false>(p, t0, t1, cache, set_lo, wbuf);
 }
 
-// Dynamic shared memory of batch_cta for block size 2^LOG2N: permutation
-// buffer plus `cached_sets` set tables of `set_words` words.
-template <int LOG2N>
+// Dynamic shared memory of batch_cta for block size 2^LOG2N without the set
+// tables: the permutation buffer (one region per block of a warp task).
+template <int LOG2N, int KIND>
 __host__ __device__ inline size_t batch_pbuf_bytes(int threads) {
-  return (size_t)(threads / 32) * batch_group(LOG2N) * perm_region_words(LOG2N) * 4;
+  return (size_t)(threads / 32) * batch_task_group(LOG2N, KIND == 1) * perm_region_words(LOG2N) *
+         4;
 }
 
 template <int LOG2N, int KIND>

@@ -177,16 +177,19 @@ __device__ __forceinline__ void load_f32(const float* p, float (&v)[E]) {
   for (int k = 0; k < E; ++k) v[k] = __uint_as_float(w[k]);
 }
 
-__device__ __forceinline__ uint32_t sat16(int32_t v) {
-  v = max(-32768, min(32767, v));
-  return (uint32_t)v & 0xffffu;
+// Two int32 values saturated to int16 and packed, lo in the low half (one
+// cvt.pack.sat instruction: its first source goes to the high half).
+__device__ __forceinline__ uint32_t pack_sat16(int32_t lo, int32_t hi) {
+  uint32_t d;
+  asm("cvt.pack.sat.s16.s32 %0, %1, %2;" : "=r"(d) : "r"(hi), "r"(lo));
+  return d;
 }
 
 template <int E>
 __device__ __forceinline__ void store_i16_sat(int16_t* p, const int32_t (&v)[E]) {
   uint32_t w[E / 2];
 #pragma unroll
-  for (int k = 0; k < E / 2; ++k) w[k] = sat16(v[2 * k]) | (sat16(v[2 * k + 1]) << 16);
+  for (int k = 0; k < E / 2; ++k) w[k] = pack_sat16(v[2 * k], v[2 * k + 1]);
   store_words<E / 2>(p, w);
 }
 

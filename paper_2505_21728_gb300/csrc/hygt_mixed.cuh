@@ -14,7 +14,7 @@ struct MixedParams {
   int nclasses;
 };
 
-// CTAs of one mixed launch (one 768-thread CTA per SM).
+// CTAs of one mixed launch (one CTA per SM).
 int mixed_grid_ctas();
 // kind 0: forward, 1: inverse.
 cudaError_t launch_mixed(int kind, const MixedParams& mp, cudaStream_t stream);

@@ -29,11 +29,12 @@ __global__ void __launch_bounds__(kBatchThreads, 1) hygt_mixed_kernel(MixedParam
   }
 }
 
+template <int KIND>
 static size_t pbuf_for(int log2n) {
   switch (log2n) {
-    case 4: return batch_pbuf_bytes<4>(kBatchThreads);
-    case 6: return batch_pbuf_bytes<6>(kBatchThreads);
-    case 8: return batch_pbuf_bytes<8>(kBatchThreads);
+    case 4: return batch_pbuf_bytes<4, KIND>(kBatchThreads);
+    case 6: return batch_pbuf_bytes<6, KIND>(kBatchThreads);
+    case 8: return batch_pbuf_bytes<8, KIND>(kBatchThreads);
     default: return 0;
   }
 }
@@ -41,7 +42,7 @@ static size_t pbuf_for(int log2n) {
 int mixed_grid_ctas() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-  return device_info(dev).sms;  // one 768-thread CTA per SM
+  return device_info(dev).sms;  // one CTA per SM
 }
 
 template <int KIND>
@@ -53,7 +54,7 @@ static cudaError_t launch_mixed_kind(MixedParams mp, cudaStream_t stream) {
   const DeviceInfo info = device_info(dev);
   const size_t smem = (size_t)info.max_smem_optin;
   for (int c = 0; c < mp.nclasses; ++c) {
-    const size_t pbuf = pbuf_for(mp.log2n[c]);
+    const size_t pbuf = pbuf_for<KIND>(mp.log2n[c]);
     const size_t set_bytes = (size_t)mp.cls[c].set_words * 4;
     long long fit = ((long long)smem - (long long)pbuf) / (long long)set_bytes;
     if (fit > 64) fit = 64;
