@@ -395,7 +395,9 @@ def run_ours(args, rank, world, local):
 def mixed_leg(dev, stream, steps=20, name="mixed_frame_2160p16"):
     """The mixed-size frame batch (4x4 / 8x8 / 16x16 blocks, one persistent
     launch per direction) as a CUDA graph of one step: schedules of the three
-    classes, mixed forward, mixed inverse.  The CTA split is autotuned."""
+    classes, mixed forward, mixed inverse.  The mode (one launch with every
+    CTA through the classes in turn, one launch with the classes concurrent
+    on a split of the CTAs, or one launch per class) is autotuned."""
     import numpy as np
     import torch
     from paper_2505_21728_gb300 import autotune, hygt, workloads
@@ -445,7 +447,10 @@ def mixed_leg(dev, stream, steps=20, name="mixed_frame_2160p16"):
             "blocks_per_class": list(w.counts()), "value": nblocks / (step_ms / 1000.0),
             "unit": "blocks/s", "ms_per_step": step_ms,
             "step": "CUDA graph: schedules of 3 classes, mixed forward, mixed inverse",
-            "cta_split": split, "gpu_launches_per_step": 3 * 3 + 2,
+            "mode": ("separate launches" if all(c == -1 for c in split) else
+                     "concurrent" if all(c > 0 for c in split) else "sequential"),
+            "cta_split": split,
+            "gpu_launches_per_step": 3 * 3 + (6 if all(c == -1 for c in split) else 2),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "kernel": dom_name, "peak_source": kind,
                          "bytes_per_launch": bytes_per_launch, "fwd_ms": f_avg, "inv_ms": i_avg,

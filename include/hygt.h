@@ -200,12 +200,21 @@ hygt_status hygt_backward_f32(hygt_plan plan, const float *d_y, const float *d_g
  * 4x4 (N = 16) and 8x8 (N = 64) secondary transforms (Sec. VI); a frame
  * tiled into 4x4, 8x8 and 16x16 blocks gives one batch per block size, each
  * with its own plan, set indices and schedule.  One launch transforms all of
- * them: the CTAs of the launch are split among the classes (`ctas` per
- * class, all > 0 and summing to at most 4 * hygt_mixed_ctas(); otherwise a
- * split proportional to an estimate of each class's cost is used).
+ * them, in one of three ways, chosen by the classes' `ctas`:
+ *   - `ctas` > 0 for every class, summing to at most 4 * hygt_mixed_ctas():
+ *     one launch; class c runs on its own `ctas` CTAs, concurrently with
+ *     the others;
+ *   - `ctas` = -1 for every class: one batch launch per class, one after
+ *     the other on the stream (hygt_forward_batch's kernels);
+ *   - otherwise (e.g. all 0): one launch; every CTA works through the
+ *     classes in turn, each class spread over all CTAs.
+ * A single launch sizes its shared memory for its largest class, which
+ * leaves less L1 cache to the smaller ones; the autotuner of the Python
+ * package times the three and keeps the fastest.
  *
  * Each class: plan = integer plan with N = 16, 64 or 256 (others return
- * HYGT_ERR_UNSUPPORTED); d_set, nblocks, d_work / work_bytes as for
+ * HYGT_ERR_UNSUPPORTED; at most one class per block size, else
+ * HYGT_ERR_ARG); d_set, nblocks, d_work / work_bytes as for
  * hygt_batch_build; d_x int16 [nblocks][N] forward input, d_y int32
  * [nblocks][N] coefficients (forward output, inverse input), d_xr int16
  * [nblocks][N] inverse output.  Data pointers 16-byte aligned.

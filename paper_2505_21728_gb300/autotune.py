@@ -1,14 +1,19 @@
 """Autotuner of the mixed-size launch.
 
-The mixed kernel runs every block-size class on its own share of the CTAs
-(one CTA per SM), so the launch ends when the slowest class ends.  The tuner
-picks the split of the CTAs among the classes:
+A mixed batch runs in one of three modes: one launch in which every CTA
+works through all classes in turn (split of all zeros); one launch in which
+each class runs concurrently on its own share of the CTAs (so the launch
+ends when the slowest class ends); or one batch launch per class (split of
+all -1).  The tuner times them:
 
-1. time each class alone on all CTAs (t_c);
-2. start from the split proportional to t_c (equal finishing times if each
+0. the sequential launch and the separate launches;
+1. each class alone on all CTAs (t_c);
+2. the concurrent split proportional to t_c (equal finishing times if each
    class scales linearly with its CTAs);
 3. local search: move k CTAs between any two classes (k halving down to 1)
-   while the measured forward + inverse time improves.
+   while the measured forward + inverse time improves;
+
+and keeps the fastest.
 
 Results are cached in a JSON file keyed by the GPU name and the classes'
 shapes (block size, rounds, sets, block count).
@@ -90,6 +95,11 @@ def tune_split(mb, reps=5, use_cache=True, verbose=False):
         mb.set_split(split)
         return split
 
+    # 0. sequential launch, separate launches
+    seq = [0] * mb.n
+    seq_ms = _time_pair(_with_split(mb, seq), mb.n, reps)
+    sep = [-1] * mb.n
+    sep_ms = _time_pair(_with_split(mb, sep), mb.n, reps)
     # 1. each class alone on all CTAs
     alone = {}
     for i in active:
@@ -124,11 +134,17 @@ def tune_split(mb, reps=5, use_cache=True, verbose=False):
                     if t < best * 0.995:
                         best, split, improved = t, cand, True
         step //= 2
+    if seq_ms <= best:
+        split, best = seq, seq_ms
+    if sep_ms <= best:
+        split, best = sep, sep_ms
     if verbose:
-        print("autotune: alone", alone, "best", split, "%.4f ms" % best)
+        print("autotune: sequential %.4f ms, separate %.4f ms, alone" % (seq_ms, sep_ms), alone,
+              "best", split, "%.4f ms" % best)
     mb.set_split(split)
     if use_cache:
-        cache[key] = {"split": split, "ms": best, "alone_ms": {str(k): v for k, v in alone.items()},
+        cache[key] = {"split": split, "ms": best, "sequential_ms": seq_ms, "separate_ms": sep_ms,
+                      "alone_ms": {str(k): v for k, v in alone.items()},
                       "trials": len(trials)}
         try:
             os.makedirs(os.path.dirname(path), exist_ok=True)

@@ -165,10 +165,9 @@ static cudaError_t launch_batch_sized(BatchParams p, cudaStream_t stream) {
   constexpr int G = batch_task_group(LOG2N, KIND == 1);
   const size_t pbuf = batch_pbuf_bytes<LOG2N, KIND>(kBatchThreads);
   const size_t set_bytes = (size_t)p.set_words * 4;
-  long long fit = ((long long)info.max_smem_optin - (long long)pbuf) / (long long)set_bytes;
-  if (fit > 64) fit = 64;
-  if (fit < 0) fit = 0;
-  p.max_cached_sets = (int)fit;
+  const int fit =
+      batch_cached_sets((size_t)info.max_smem_optin, pbuf, set_bytes, p.num_sets, info.sms);
+  p.max_cached_sets = fit;
   const size_t smem = pbuf + (size_t)fit * set_bytes;
   static std::atomic<int> attr_set{0};
   if ((int)smem > attr_set.load()) {

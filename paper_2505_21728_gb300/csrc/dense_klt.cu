@@ -4,13 +4,10 @@
 // Blocks are bucketed by set (the batch schedule, in tiles of 128 blocks),
 // so every tile multiplies one 128 x N slice of blocks by one N x N matrix.
 //
-// BF16 tensor-core kernel (sm_103a tcgen05): a CTA of 128 threads walks its
-// tiles; thread t converts block (tile row) t from int16 to BF16 and writes
-// it into shared memory in the 128-byte-swizzled K-major layout; the CTA's
-// copy of the set's matrix is a pre-swizzled image (built on the host); one
-// thread issues N/16 tcgen05.mma (M = 128, N, K = 16, FP32 accumulate in
-// tensor memory) and commits them to an mbarrier; every warp then reads its
-// 32 rows of the accumulator with tcgen05.ld and stores FP32 outputs.
+// BF16 tensor-core kernel (sm_103a tcgen05): a persistent, warp-specialised
+// pipeline (producer warps gather and convert tiles into swizzled shared
+// memory, one thread issues tcgen05.mma into tensor-memory accumulators,
+// epilogue warps drain them with tcgen05.ld), described at the kernel.
 //
 // Integer CUDA-core kernel: y = floor((K_int x + 2^(f-1)) / 2^f) with
 // K_int = round(2^f K), int32 arithmetic; a warp computes 32 blocks of one
@@ -50,21 +47,6 @@ __host__ __device__ constexpr uint32_t bf16_idesc(int m, int n) {
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
-}
-
-// Bounded wait on an mbarrier phase; returns false if the limit was reached.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, uint32_t limit) {
-  const uint32_t a = smem_addr(bar);
-  for (uint32_t it = 0; it < limit; ++it) {
-    uint32_t done = 0;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-        : "=r"(done)
-        : "r"(a), "r"(phase)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
@@ -112,27 +94,80 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&r)[16]) {
 }
 
 // ---------------------------------------------------------------- BF16 kernel
-// Shared memory: A tile (128 x N bf16, swizzled), B image (N x N bf16,
-// swizzled), then the mbarrier and the TMEM address.  Both images are split
-// into K blocks of 64 elements (128 bytes per row); K block kb of the A tile
-// is at kb * 128 * 128 bytes, of B at kb * N * 128 bytes.
+// Warp-specialised persistent kernel, one tile of 128 blocks per pipeline
+// step, three roles that hand tiles over through mbarriers:
+//   warps 0-3  producer: thread t gathers block t of the tile, converts it
+//              int16 -> BF16 into the 128-byte-swizzled K-major A stage
+//              (STAGES stages), and keeps the set's matrix image (B) current;
+//   warp 8     one thread issues N/16 tcgen05.mma (M = 128, K = 16) per tile
+//              into one of ACC tensor-memory accumulators and commits them;
+//   warps 4-7  epilogue: warp 4 + q reads accumulator lanes 32q.. with
+//              tcgen05.ld and stores the FP32 outputs.
+// So the gather of tile i + 1, the MMAs of tile i and the stores of tile
+// i - 1 run at the same time.  Skip and bad-set tiles are handled by the
+// producer alone (every role walks the same tile list and skips them).
+// Every wait is bounded by a time limit; a role that gives up raises the
+// CTA's abort flag, which the other roles' waits observe.
 template <int N>
 struct DenseBf16Shape {
-  static constexpr int KB = N / 64;                 // K blocks
+  static constexpr int KB = N / 64;                     // K blocks of 64 elements
   static constexpr size_t A_BYTES = (size_t)128 * N * 2;
   static constexpr size_t B_BYTES = (size_t)N * N * 2;
-  static constexpr size_t SMEM = A_BYTES + B_BYTES + 64;
-  static constexpr uint32_t TMEM_COLS = N < 32 ? 32 : N;
+  static constexpr int STAGES = N <= 64 ? 4 : 1;         // A stages
+  static constexpr int ACC = N <= 64 ? 4 : 2;            // accumulators in tensor memory
+  static constexpr uint32_t TMEM_COLS = (uint32_t)(N * ACC);  // 256 or 512 (a power of 2)
+  static constexpr size_t B_OFF = STAGES * A_BYTES;
+  static constexpr size_t BAR_OFF = B_OFF + B_BYTES;
+  static constexpr size_t SMEM = BAR_OFF + 256;
+  static constexpr int THREADS = 288;                   // 4 producer + 4 epilogue + 1 MMA warp
 };
 
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the completion of the mbarrier phase with parity `parity`, at
+// most about one second, and not past the CTA's abort flag (if given).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  volatile int* abort_flag) {
+  const uint32_t a = smem_addr(bar);
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0;; ++it) {
+    uint32_t done = 0;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 63) == 63 && ((abort_flag && *abort_flag) || global_ns() - t0 > 1000000000ull))
+      return false;
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void dense_abort(volatile int* abort_flag, int* status) {
+  *abort_flag = 1;
+  if (status) atomicCAS(status, 0, 2);
+}
+
 template <int N>
-__global__ void __launch_bounds__(128, 1) dense_bf16_kernel(DenseParams p) {
+__global__ void __launch_bounds__(288, 1) dense_bf16_kernel(DenseParams p) {
   using SH = DenseBf16Shape<N>;
   extern __shared__ __align__(1024) unsigned char dsm[];
-  unsigned char* a_img = dsm;
-  unsigned char* b_img = dsm + SH::A_BYTES;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(dsm + SH::A_BYTES + SH::B_BYTES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(dsm + SH::A_BYTES + SH::B_BYTES + 16);
+  unsigned char* b_img = dsm + SH::B_OFF;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(dsm + SH::BAR_OFF);
+  uint64_t* a_full = bars;                       // [STAGES], 128 producer arrivals
+  uint64_t* a_free = bars + SH::STAGES;          // [STAGES], MMA commit
+  uint64_t* acc_full = bars + 2 * SH::STAGES;    // [ACC], MMA commit
+  uint64_t* acc_empty = acc_full + SH::ACC;      // [ACC], 128 epilogue arrivals
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + SH::ACC);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int t = threadIdx.x;
   const int warp = t >> 5;
 
@@ -141,12 +176,22 @@ __global__ void __launch_bounds__(128, 1) dense_bf16_kernel(DenseParams p) {
     return;
   }
   // the 128-byte swizzle needs 1024-byte aligned operand images
-  if ((smem_addr(a_img) & 1023u) != 0) {
+  if ((smem_addr(dsm) & 1023u) != 0) {
     if (t == 0 && p.status) atomicCAS(p.status, 0, 2);
     return;
   }
-  if (warp == 0) tmem_alloc(tmem_slot, SH::TMEM_COLS);
-  if (t == 0) mbar_init(bar, 1);
+  if (warp == 8) tmem_alloc(tmem_slot, SH::TMEM_COLS);
+  if (t == 0) {
+    for (int i = 0; i < SH::STAGES; ++i) {
+      mbar_init(a_full + i, 128);
+      mbar_init(a_free + i, 1);
+    }
+    for (int i = 0; i < SH::ACC; ++i) {
+      mbar_init(acc_full + i, 1);
+      mbar_init(acc_empty + i, 128);
+    }
+    *abort_flag = 0;
+  }
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -156,36 +201,49 @@ __global__ void __launch_bounds__(128, 1) dense_bf16_kernel(DenseParams p) {
   const long long chunk = (ntasks + gridDim.x - 1) / gridDim.x;
   const long long t0 = min(ntasks, (long long)blockIdx.x * chunk);
   const long long t1 = min(ntasks, t0 + chunk);
-  int cached = -1;
-  uint32_t phase = 0;
-  bool ok = true;
-  constexpr uint32_t kIdesc = bf16_idesc(128, N);
+  const int S = p.num_sets;
 
-  for (long long task = t0; task < t1 && ok; ++task) {
-    const int slot = (int)(task * 128);
-    const int bucket = bucket_of_slot(p.starts, p.num_sets, slot);
-    const int b = __ldg(p.order + slot + t);
-    const bool active = b >= 0 && b < p.nblocks;
-    if (bucket >= p.num_sets) {  // skip (identity) or bad set (zeros)
-      if (active) {
-        float* y = p.y + (long long)b * N;
-        const int16_t* x = p.x + (long long)b * N;
-        for (int i = 0; i < N; ++i) y[i] = bucket == p.num_sets ? (float)x[i] : 0.f;
-        if (bucket != p.num_sets && p.status) atomicCAS(p.status, 0, 4);
+  if (warp < 4) {
+    // ------------------------------------------------ producer
+    int i = 0, cur_set = -1;
+    for (long long task = t0; task < t1; ++task) {
+      const int slot = (int)(task * 128);
+      const int bucket = bucket_of_slot(p.starts, S, slot);
+      const int b = __ldg(p.order + slot + t);
+      const bool active = b >= 0 && b < p.nblocks;
+      if (bucket >= S) {  // skip (identity) or bad set (zeros)
+        if (active) {
+          float* y = p.y + (long long)b * N;
+          const int16_t* x = p.x + (long long)b * N;
+          for (int k = 0; k < N; ++k) y[k] = bucket == S ? (float)x[k] : 0.f;
+          if (bucket != S && p.status) atomicCAS(p.status, 0, 4);
+        }
+        continue;
       }
-      continue;
-    }
-    // B image of the set (uniform across the CTA, reloaded on change)
-    if (bucket != cached) {
-      const int4* src = reinterpret_cast<const int4*>(p.kimg + (size_t)bucket * SH::B_BYTES);
-      int4* dst = reinterpret_cast<int4*>(b_img);
-      for (int i = t; i < (int)(SH::B_BYTES / 16); i += blockDim.x) dst[i] = __ldg(src + i);
-      cached = bucket;
-    }
-    // A row t: int16 -> bf16, 16-byte chunks at swizzled positions
-    {
+      const int s = i % SH::STAGES;
+      if (i >= SH::STAGES &&
+          !mbar_wait_bounded(a_free + s, (uint32_t)((i / SH::STAGES) - 1) & 1u, abort_flag)) {
+        dense_abort(abort_flag, p.status);
+        break;
+      }
+      if (bucket != cur_set) {
+        // every MMA issued so far must be done before the image is replaced
+        if (i > 0) {
+          const int j = i - 1;
+          if (!mbar_wait_bounded(a_free + j % SH::STAGES, (uint32_t)(j / SH::STAGES) & 1u,
+                                 abort_flag)) {
+            dense_abort(abort_flag, p.status);
+            break;
+          }
+        }
+        const int4* src = reinterpret_cast<const int4*>(p.kimg + (size_t)bucket * SH::B_BYTES);
+        int4* dst = reinterpret_cast<int4*>(b_img);
+        for (int k = t; k < (int)(SH::B_BYTES / 16); k += 128) dst[k] = __ldg(src + k);
+        cur_set = bucket;
+      }
+      // A row t of stage s: int16 -> bf16, 16-byte chunks at swizzled positions
       const int4* xs = reinterpret_cast<const int4*>(p.x + (long long)(active ? b : 0) * N);
-      unsigned char* row = a_img + (t >> 3) * 1024 + (t & 7) * 128;
+      unsigned char* row = dsm + (size_t)s * SH::A_BYTES + (t >> 3) * 1024 + (t & 7) * 128;
 #pragma unroll 4
       for (int c = 0; c < N / 8; ++c) {
         int4 raw = active ? __ldg(xs + c) : make_int4(0, 0, 0, 0);
@@ -198,44 +256,85 @@ __global__ void __launch_bounds__(128, 1) dense_bf16_kernel(DenseParams p) {
         unsigned char* dst = row + kb * (128 * 128) + ((cc ^ (t & 7)) << 4);
         *reinterpret_cast<int4*>(dst) = *reinterpret_cast<int4*>(q);
       }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(a_full + s);
+      ++i;
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (t == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = smem_addr(a_img), b0 = smem_addr(b_img);
-#pragma unroll
-      for (int s = 0; s < N / 16; ++s) {
-        const uint32_t ka = (uint32_t)((s >> 2) * (128 * 128) + (s & 3) * 32);
-        const uint32_t kb = (uint32_t)((s >> 2) * (N * 128) + (s & 3) * 32);
-        mma_bf16(tmem, sw128_desc(a0 + ka), sw128_desc(b0 + kb), kIdesc, s > 0 ? 1u : 0u);
+  } else if (warp < 8) {
+    // ------------------------------------------------ epilogue
+    const int r = t - 128;  // accumulator lane = tile row
+    const uint32_t lane_base = tmem + ((uint32_t)((warp - 4) * 32) << 16);
+    int i = 0;
+    for (long long task = t0; task < t1; ++task) {
+      const int slot = (int)(task * 128);
+      const int bucket = bucket_of_slot(p.starts, S, slot);
+      if (bucket >= S) continue;
+      const int a = i % SH::ACC;
+      const int b = __ldg(p.order + slot + r);
+      const bool active = b >= 0 && b < p.nblocks;
+      if (!mbar_wait_bounded(acc_full + a, (uint32_t)(i / SH::ACC) & 1u, abort_flag)) {
+        dense_abort(abort_flag, p.status);
+        break;
       }
-      mma_commit(bar);
-    }
-    ok = __syncthreads_and(mbar_wait(bar, phase, 1u << 26) ? 1 : 0) != 0;
-    phase ^= 1u;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       float* y = p.y + (long long)(active ? b : 0) * N;
-      const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
       for (int c0 = 0; c0 < N; c0 += 16) {
-        float r[16];
-        tmem_ld16(lane_addr + (uint32_t)c0, r);
+        float v[16];
+        tmem_ld16(lane_base + (uint32_t)(a * N + c0), v);
         if (active) {
 #pragma unroll
           for (int k = 0; k < 16; k += 4)
-            *reinterpret_cast<float4*>(y + c0 + k) = make_float4(r[k], r[k + 1], r[k + 2], r[k + 3]);
+            *reinterpret_cast<float4*>(y + c0 + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
         }
       }
-    } else if (t == 0 && p.status) {
-      atomicCAS(p.status, 0, 2);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(acc_empty + a);
+      ++i;
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
+  } else if (t == 256) {
+    // ------------------------------------------------ MMA issuer
+    constexpr uint32_t kIdesc = bf16_idesc(128, N);
+    const uint32_t b0 = smem_addr(b_img);
+    int i = 0;
+    for (long long task = t0; task < t1; ++task) {
+      const int slot = (int)(task * 128);
+      const int bucket = bucket_of_slot(p.starts, S, slot);
+      if (bucket >= S) continue;
+      const int s = i % SH::STAGES, a = i % SH::ACC;
+      if (!mbar_wait_bounded(a_full + s, (uint32_t)(i / SH::STAGES) & 1u, abort_flag) ||
+          (i >= SH::ACC &&
+           !mbar_wait_bounded(acc_empty + a, (uint32_t)((i / SH::ACC) - 1) & 1u, abort_flag))) {
+        dense_abort(abort_flag, p.status);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_addr(dsm + (size_t)s * SH::A_BYTES);
+#pragma unroll
+      for (int k = 0; k < N / 16; ++k) {
+        const uint32_t ka = (uint32_t)((k >> 2) * (128 * 128) + (k & 3) * 32);
+        const uint32_t kb = (uint32_t)((k >> 2) * (N * 128) + (k & 3) * 32);
+        mma_bf16(tmem + (uint32_t)(a * N), sw128_desc(a0 + ka), sw128_desc(b0 + kb), kIdesc,
+                 k > 0 ? 1u : 0u);
+      }
+      mma_commit(a_free + s);
+      mma_commit(acc_full + a);
+      ++i;
+    }
+    // the tensor memory is released below: wait for the last MMAs issued,
+    // also after an abort
+    if (i > 0) {
+      const int j = i - 1;
+      if (!mbar_wait_bounded(a_free + j % SH::STAGES, (uint32_t)(j / SH::STAGES) & 1u, nullptr))
+        dense_abort(abort_flag, p.status);
+    }
   }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, SH::TMEM_COLS);
+  if (warp == 8) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tmem_dealloc(tmem, SH::TMEM_COLS);
+  }
 }
 
 // ---------------------------------------------------------------- int32 kernel
@@ -328,14 +427,14 @@ static cudaError_t launch_bf16(const DenseParams& p, cudaStream_t stream) {
   err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   int occ = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 128, smem);
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, SH::THREADS, smem);
   if (err != cudaSuccess) return err;
   if (occ < 1) return cudaErrorInvalidConfiguration;
   if (occ > max_ctas) return cudaErrorInvalidConfiguration;
   long long grid = (long long)occ * info.sms;
   const long long tiles = (p.nblocks + 127) / 128 + p.num_sets + 2;
   if (grid > tiles) grid = tiles;
-  kern<<<(unsigned)grid, 128, smem, stream>>>(p);
+  kern<<<(unsigned)grid, SH::THREADS, smem, stream>>>(p);
   return cudaGetLastError();
 }
 

@@ -418,23 +418,28 @@ hygt_status hygt_inverse_batch(hygt_plan plan, const void* d_work, const int32_t
 int hygt_mixed_ctas(void) { return hygt::mixed_grid_ctas(); }
 
 // Validates the classes of a mixed launch and fills the kernel parameters.
+// How a mixed batch is run (from the classes' `ctas`).
+enum MixedMode { kMixedSequential, kMixedConcurrent, kMixedSeparate };
+
 static hygt_status mixed_params(const hygt_mixed_class* cls, int nclasses, bool inverse,
-                                int* d_status, hygt::MixedParams* mp) {
+                                int* d_status, hygt::MixedParams* mp, MixedMode* mode) {
   if (!cls || nclasses < 1 || nclasses > hygt::kMaxMixedClasses) return HYGT_ERR_ARG;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return HYGT_ERR_CUDA;
   *mp = hygt::MixedParams{};
-  mp->nclasses = nclasses;
-  double cost[hygt::kMaxMixedClasses] = {0, 0, 0};
-  double total_cost = 0;
-  bool explicit_split = true;
+  bool explicit_split = true, separate = true;
   int explicit_sum = 0;
+  int slot_ctas[hygt::kMaxMixedClasses] = {0, 0, 0};
+  bool seen[hygt::kMaxMixedClasses] = {false, false, false};
   for (int c = 0; c < nclasses; ++c) {
     const hygt_mixed_class& k = cls[c];
     hygt_plan plan = k.plan;
     if (!plan || plan->is_float) return plan ? HYGT_ERR_UNSUPPORTED : HYGT_ERR_ARG;
     if (plan->log2n != 4 && plan->log2n != 6 && plan->log2n != 8) return HYGT_ERR_UNSUPPORTED;
     if (plan->device != dev || k.nblocks < 0 || k.nblocks > kBatchMaxBlocks) return HYGT_ERR_ARG;
+    const int slot = (plan->log2n - 4) / 2;
+    if (seen[slot]) return HYGT_ERR_ARG;  // one class per block size
+    seen[slot] = true;
     const void* in = inverse ? (const void*)k.d_y : (const void*)k.d_x;
     void* out = inverse ? (void*)k.d_xr : (void*)k.d_y;
     if (k.nblocks > 0) {
@@ -444,45 +449,52 @@ static hygt_status mixed_params(const hygt_mixed_class* cls, int nclasses, bool 
       if (k.work_bytes < hygt::batch_layout(plan->num_sets, k.nblocks, group).total)
         return HYGT_ERR_ARG;
     }
-    mp->cls[c] = make_batch_params(plan, k.d_work, in, out, k.nblocks, d_status);
-    mp->log2n[c] = plan->log2n;
-    const double N = (double)(1 << plan->log2n);
-    // relative cost: memory traffic plus butterfly work
-    cost[c] = (double)k.nblocks * N * (6.0 + 0.5 * plan->rounds * plan->log2n);
-    total_cost += cost[c];
+    mp->cls[slot] = make_batch_params(plan, k.d_work, in, out, k.nblocks, d_status);
+    mp->present[slot] = k.nblocks > 0 ? 1 : 0;
+    slot_ctas[slot] = k.ctas;
     if (k.ctas <= 0) explicit_split = false;
+    if (k.ctas != -1) separate = false;
     explicit_sum += k.ctas > 0 ? k.ctas : 0;
   }
   const int grid = hygt::mixed_grid_ctas();
   if (grid < 1) return HYGT_ERR_CUDA;
-  int n[hygt::kMaxMixedClasses] = {0, 0, 0};
-  if (explicit_split && explicit_sum <= 4 * grid) {
-    for (int c = 0; c < nclasses; ++c) n[c] = cls[c].ctas;
-  } else if (total_cost > 0) {
-    int given = 0;
-    for (int c = 0; c < nclasses; ++c) {
-      n[c] = cls[c].nblocks > 0 ? (int)(grid * cost[c] / total_cost) : 0;
-      if (cls[c].nblocks > 0 && n[c] < 1) n[c] = 1;
-      given += n[c];
-    }
-    // hand the rounding remainder to the most expensive class
-    int big = 0;
-    for (int c = 1; c < nclasses; ++c)
-      if (cost[c] > cost[big]) big = c;
-    n[big] += grid - given;
-    if (n[big] < 1) n[big] = 1;
-  }
   mp->cta_begin[0] = 0;
-  for (int c = 0; c < nclasses; ++c) mp->cta_begin[c + 1] = mp->cta_begin[c] + n[c];
+  *mode = separate ? kMixedSeparate
+                   : (explicit_split && explicit_sum <= 4 * grid) ? kMixedConcurrent
+                                                                   : kMixedSequential;
+  if (*mode == kMixedConcurrent) {
+    mp->sequential = 0;
+    for (int k = 0; k < hygt::kMaxMixedClasses; ++k)
+      mp->cta_begin[k + 1] = mp->cta_begin[k] + (mp->present[k] ? slot_ctas[k] : 0);
+  } else {
+    mp->sequential = 1;  // every CTA takes part in every class, one class after the other
+    for (int k = 0; k < hygt::kMaxMixedClasses; ++k) mp->cta_begin[k + 1] = grid;
+  }
   return HYGT_OK;
+}
+
+// One direction of a mixed batch: the mixed kernel, or (separate mode) the
+// batch kernel of each class in turn.
+static cudaError_t mixed_launch(const hygt::MixedParams& mp, MixedMode mode, bool inverse,
+                                cudaStream_t stream) {
+  if (mode != kMixedSeparate) return hygt::launch_mixed(inverse ? 1 : 0, mp, stream);
+  for (int k = 0; k < hygt::kMaxMixedClasses; ++k) {
+    if (!mp.present[k]) continue;
+    const int log2n = hygt::mixed_slot_log2n(k);
+    const cudaError_t e = inverse ? hygt::launch_batch_inv(log2n, mp.cls[k], stream)
+                                  : hygt::launch_batch_fwd(log2n, mp.cls[k], stream);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 static hygt_status mixed_call(const hygt_mixed_class* cls, int nclasses, hygt_stream stream,
                               int* d_status, bool inverse) {
   hygt::MixedParams mp;
-  hygt_status s = mixed_params(cls, nclasses, inverse, d_status, &mp);
+  MixedMode mode;
+  hygt_status s = mixed_params(cls, nclasses, inverse, d_status, &mp, &mode);
   if (s != HYGT_OK) return s;
-  return to_status(hygt::launch_mixed(inverse ? 1 : 0, mp, (cudaStream_t)stream));
+  return to_status(mixed_launch(mp, mode, inverse, (cudaStream_t)stream));
 }
 
 hygt_status hygt_forward_mixed(const hygt_mixed_class* classes, int nclasses, hygt_stream stream,
@@ -505,8 +517,9 @@ hygt_status hygt_mixed_graph_create(hygt_graph* out, const hygt_mixed_class* cla
   if (!out) return HYGT_ERR_ARG;
   *out = nullptr;
   hygt::MixedParams fwd, inv;
-  hygt_status s = mixed_params(classes, nclasses, false, d_status, &fwd);
-  if (s == HYGT_OK) s = mixed_params(classes, nclasses, true, d_status, &inv);
+  MixedMode mode;
+  hygt_status s = mixed_params(classes, nclasses, false, d_status, &fwd, &mode);
+  if (s == HYGT_OK) s = mixed_params(classes, nclasses, true, d_status, &inv, &mode);
   if (s != HYGT_OK) return s;
   cudaStream_t cs = nullptr;
   if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return HYGT_ERR_CUDA;
@@ -522,8 +535,8 @@ hygt_status hygt_mixed_graph_create(hygt_graph* out, const hygt_mixed_class* cla
       e = hygt::batch_build(k.d_set, k.nblocks, k.plan->num_sets, hygt::batch_group(k.plan->log2n),
                             k.d_work, cs);
   }
-  if (e == cudaSuccess) e = hygt::launch_mixed(0, fwd, cs);
-  if (e == cudaSuccess) e = hygt::launch_mixed(1, inv, cs);
+  if (e == cudaSuccess) e = mixed_launch(fwd, mode, false, cs);
+  if (e == cudaSuccess) e = mixed_launch(inv, mode, true, cs);
   cudaGraph_t graph = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
   if (e == cudaSuccess) e = e2;

@@ -498,6 +498,19 @@ __global__ void __launch_bounds__(kBatchThreads, 1) hygt_batch_kernel(BatchParam
   batch_cta<LOG2N, KIND>(p, blockIdx.x, gridDim.x, bsmem);
 }
 
+// Set tables a CTA keeps in shared memory: as many as its share of the
+// sorted order usually spans (a CTA that spans more reads the tables from
+// global memory), and no more -- shared memory not taken stays L1 cache,
+// which the kernels' global loads depend on.
+__host__ inline int batch_cached_sets(size_t max_smem, size_t pbuf, size_t set_bytes,
+                                      int num_sets, int ctas) {
+  long long cap = 2 + (num_sets + ctas - 1) / (ctas > 0 ? ctas : 1);
+  if (cap < 4) cap = 4;
+  if (cap > 64) cap = 64;
+  long long fit = max_smem > pbuf ? (long long)((max_smem - pbuf) / set_bytes) : 0;
+  return (int)(fit < cap ? fit : cap);
+}
+
 // Host launchers (batch_int.cu).
 cudaError_t batch_build(const uint16_t* d_set, long long nblocks, int num_sets, int group,
                         void* d_work, cudaStream_t stream);

@@ -2,11 +2,15 @@
 //
 // A frame tiled into 4x4, 8x8 and 16x16 blocks gives one bucketed batch per
 // block size (each with its own plan and schedule).  The mixed kernel runs
-// all of them in a single launch: CTAs [begin[c], begin[c + 1]) work on
-// class c exactly like the batch kernel of that block size, so the classes
-// proceed concurrently on disjoint SMs.  The split of CTAs among the classes
-// is a launch parameter (chosen by the autotuner, or proportional to an
-// estimate of each class's cost).
+// all of them in a single launch, in one of two ways: sequential -- every
+// CTA works on class 0 exactly like the batch kernel of that block size,
+// then on class 1, ... (a CTA that finishes its share of a class goes on to
+// the next without waiting for the others); or concurrent -- CTAs
+// [begin[c], begin[c + 1]) work on class c only, so the classes proceed on
+// disjoint SMs.  Which, and the split, is a launch parameter (chosen by the
+// autotuner).
+#include <algorithm>
+
 #include "hygt_batch.cuh"
 #include "hygt_launch.cuh"
 #include "hygt_mixed.cuh"
@@ -16,17 +20,26 @@ namespace hygt {
 template <int KIND>
 __global__ void __launch_bounds__(kBatchThreads, 1) hygt_mixed_kernel(MixedParams mp) {
   extern __shared__ __align__(16) int32_t msmem[];
-  int c = 0;
-  while (c + 1 < mp.nclasses && (int)blockIdx.x >= mp.cta_begin[c + 1]) ++c;
-  const long long cta = (long long)blockIdx.x - mp.cta_begin[c];
-  const long long ncta = (long long)mp.cta_begin[c + 1] - mp.cta_begin[c];
-  if (ncta <= 0) return;
-  switch (mp.log2n[c]) {
-    case 4: batch_cta<4, KIND>(mp.cls[c], cta, ncta, msmem); break;
-    case 6: batch_cta<6, KIND>(mp.cls[c], cta, ncta, msmem); break;
-    case 8: batch_cta<8, KIND>(mp.cls[c], cta, ncta, msmem); break;
-    default: break;
+  if (mp.sequential) {
+    // every CTA works through the classes in turn; shared memory is reused
+    if (mp.present[0]) {
+      batch_cta<4, KIND>(mp.cls[0], blockIdx.x, gridDim.x, msmem);
+      __syncthreads();
+    }
+    if (mp.present[1]) {
+      batch_cta<6, KIND>(mp.cls[1], blockIdx.x, gridDim.x, msmem);
+      __syncthreads();
+    }
+    if (mp.present[2]) batch_cta<8, KIND>(mp.cls[2], blockIdx.x, gridDim.x, msmem);
+    return;
   }
+  const int b = (int)blockIdx.x;
+  if (b < mp.cta_begin[1])
+    batch_cta<4, KIND>(mp.cls[0], b, mp.cta_begin[1], msmem);
+  else if (b < mp.cta_begin[2])
+    batch_cta<6, KIND>(mp.cls[1], b - mp.cta_begin[1], mp.cta_begin[2] - mp.cta_begin[1], msmem);
+  else
+    batch_cta<8, KIND>(mp.cls[2], b - mp.cta_begin[2], mp.cta_begin[3] - mp.cta_begin[2], msmem);
 }
 
 template <int KIND>
@@ -52,22 +65,25 @@ static cudaError_t launch_mixed_kind(MixedParams mp, cudaStream_t stream) {
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
   const DeviceInfo info = device_info(dev);
-  const size_t smem = (size_t)info.max_smem_optin;
-  for (int c = 0; c < mp.nclasses; ++c) {
-    const size_t pbuf = pbuf_for<KIND>(mp.log2n[c]);
-    const size_t set_bytes = (size_t)mp.cls[c].set_words * 4;
-    long long fit = ((long long)smem - (long long)pbuf) / (long long)set_bytes;
-    if (fit > 64) fit = 64;
-    if (fit < 0) fit = 0;
-    mp.cls[c].max_cached_sets = (int)fit;
+  // one shared-memory size for the launch: the largest any present class asks for
+  size_t smem = 0;
+  for (int k = 0; k < kMaxMixedClasses; ++k) {
+    if (!mp.present[k]) continue;
+    const size_t pbuf = pbuf_for<KIND>(mixed_slot_log2n(k));
+    const size_t set_bytes = (size_t)mp.cls[k].set_words * 4;
+    const int fit = batch_cached_sets((size_t)info.max_smem_optin, pbuf, set_bytes,
+                                      mp.cls[k].num_sets, info.sms);
+    mp.cls[k].max_cached_sets = fit;
+    smem = std::max(smem, pbuf + (size_t)fit * set_bytes);
   }
+  if (smem == 0) return cudaSuccess;
   static std::atomic<int> attr_set{0};
   if ((int)smem > attr_set.load()) {
     err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     attr_set.store((int)smem);
   }
-  const int grid = mp.cta_begin[mp.nclasses];
+  const int grid = mp.cta_begin[kMaxMixedClasses];
   if (grid < 1) return cudaSuccess;
   kern<<<grid, kBatchThreads, smem, stream>>>(mp);
   return cudaGetLastError();

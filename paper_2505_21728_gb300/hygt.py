@@ -492,7 +492,9 @@ class MixedBatch:
         self.n = len(classes)
 
     def set_split(self, ctas):
-        """CTAs of the mixed launch per class (None or zeros: automatic)."""
+        """CTAs of the mixed launch per class: all > 0, the classes run
+        concurrently on these CTAs; all -1, one batch launch per class; None
+        or zeros, every CTA runs every class in turn."""
         for i in range(self.n):
             self.classes[i].ctas = 0 if ctas is None else int(ctas[i])
 

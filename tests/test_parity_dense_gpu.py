@@ -51,7 +51,10 @@ def test_dense_int_bit_exact(gpu, orc, log2n, S, B):
     assert np.array_equal(y, ye)
 
 
-@pytest.mark.parametrize("log2n,S,B", [(6, 5, 2000), (6, 105, 30000), (8, 4, 1500)])
+# the larger cases give every CTA of the persistent launch many tiles (deep
+# pipelining) and, with 105 sets, several changes of the set matrix
+@pytest.mark.parametrize("log2n,S,B", [(6, 5, 2000), (6, 105, 30000), (8, 4, 1500),
+                                       (6, 2, 200000), (6, 105, 400000), (8, 3, 40000)])
 def test_dense_bf16_tensor_cores(gpu, orc, log2n, S, B):
     import torch
     N = 1 << log2n

@@ -36,6 +36,7 @@ def check_against_oracle(orc, mb, datas):
 
 @pytest.mark.parametrize("scale_down", [400, 40])
 def test_mixed_launch(gpu, orc, scale_down):
+    """Default launch: every CTA works through the three classes in turn."""
     import torch
     from paper_2505_21728_gb300 import workloads
     w = workloads.get_mixed("mixed_frame_2160p16", scale_down=scale_down)
@@ -76,8 +77,11 @@ def test_mixed_autotune_keeps_results(gpu, orc, tmp_path, monkeypatch):
     mb, datas = make_mixed(gpu, w)
     mb.build()
     split = autotune.tune_split(mb, reps=2)
-    assert len(split) == 3 and all(c >= 1 for c in split)
-    assert sum(split) == gpu.hygt_mixed_ctas()
+    assert len(split) == 3
+    # the sequential launch (all zeros), separate launches (all -1), or a
+    # concurrent split of all CTAs
+    assert (all(c == 0 for c in split) or all(c == -1 for c in split) or
+            (all(c >= 1 for c in split) and sum(split) == gpu.hygt_mixed_ctas()))
     assert (tmp_path / "tune.json").exists()
     assert autotune.tune_split(mb, reps=2) == split  # cached
     mb.forward()
@@ -115,3 +119,47 @@ def test_mixed_frame_full(gpu, orc):
     torch.cuda.synchronize()
     assert int(st.item()) == 0
     check_against_oracle(orc, mb, datas)
+
+
+def test_mixed_class_order_empty_and_duplicate(gpu, orc):
+    """Classes given in any order (they are stored by block size), a class
+    without blocks, and two classes of one size (rejected)."""
+    import torch
+    from paper_2505_21728_gb300 import workloads
+    w = workloads.get_mixed("mixed_frame_2160p16", scale_down=400)
+    cws = list(w.classes())
+    classes, datas = [], []
+    for cw in reversed(cws):  # N = 256, 64, 16
+        d = cw.generate()
+        plan = gpu.Plan(cw.log2n, cw.rounds, d["angle_idx"], d["perms"])
+        classes.append((plan, _t(d["x"]), _t(d["sets"])))
+        datas.append((cw, d))
+    mb = gpu.MixedBatch(classes).build()
+    for split in (None, [3, 11, 5], [-1, -1, -1]):
+        mb.set_split(split)
+        for e in mb.entries:
+            e["y"].zero_()
+            e["xr"].zero_()
+        mb.forward()
+        mb.inverse()
+        torch.cuda.synchronize()
+        check_against_oracle(orc, mb, datas)
+
+    # the 8x8 class without blocks: the others are unaffected
+    cw, d = datas[1]
+    plan = classes[1][0]
+    empty = (plan, torch.empty((0, cw.N), dtype=torch.int16, device="cuda"),
+             torch.empty((0,), dtype=torch.int16, device="cuda"))
+    mb2 = gpu.MixedBatch([classes[0], empty, classes[2]]).build()
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    mb2.forward(status=st)
+    mb2.inverse(status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    check_against_oracle(orc, type("M", (), {"entries": [mb2.entries[0], mb2.entries[2]]}),
+                         [datas[0], datas[2]])
+
+    mb3 = gpu.MixedBatch([classes[1], classes[1]]).build()
+    with pytest.raises(gpu.HygtError) as ei:
+        mb3.forward()
+    assert ei.value.code == gpu.HYGT_ERR_ARG
