@@ -108,6 +108,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&r)[16]) {
 // producer alone (every role walks the same tile list and skips them).
 // Every wait is bounded by a time limit; a role that gives up raises the
 // CTA's abort flag, which the other roles' waits observe.
+// Shared memory: A stages (BF16 tiles, swizzled), the B image, the raw
+// ring (int16 tiles as gathered), the output row buffers (FP32 rows on their
+// way to global memory), barriers.  Raw and output rows are padded to an odd
+// number of 16-byte units, so that thread t accessing row t hits distinct
+// banks.
 template <int N>
 struct DenseBf16Shape {
   static constexpr int KB = N / 64;                     // K blocks of 64 elements
@@ -115,11 +120,22 @@ struct DenseBf16Shape {
   static constexpr size_t B_BYTES = (size_t)N * N * 2;
   static constexpr int STAGES = N <= 64 ? 4 : 1;         // A stages
   static constexpr int ACC = N <= 64 ? 4 : 2;            // accumulators in tensor memory
+  static constexpr int RAW = N <= 64 ? 4 : 0;            // raw tiles in flight (0: direct loads)
+  static constexpr int ROW = N * 2 + 16;                 // raw row pitch (bytes)
+  static constexpr size_t RAW_BYTES = (size_t)128 * ROW;
   static constexpr uint32_t TMEM_COLS = (uint32_t)(N * ACC);  // 256 or 512 (a power of 2)
+  static constexpr int OUT = N <= 64 ? 2 : 0;            // output row buffers per thread (0: direct stores)
+  static constexpr int OROW = N * 4 + 16;                // output row pitch (bytes)
+  static constexpr size_t OUT_BYTES = (size_t)128 * OROW;
   static constexpr size_t B_OFF = STAGES * A_BYTES;
-  static constexpr size_t BAR_OFF = B_OFF + B_BYTES;
+  static constexpr size_t RAW_OFF = B_OFF + B_BYTES;
+  static constexpr size_t OUT_OFF = RAW_OFF + RAW * RAW_BYTES;
+  static constexpr size_t BAR_OFF = OUT_OFF + OUT * OUT_BYTES;
   static constexpr size_t SMEM = BAR_OFF + 256;
   static constexpr int THREADS = 288;                   // 4 producer + 4 epilogue + 1 MMA warp
+  static_assert(RAW_OFF % 16 == 0 && ROW % 16 == 0 && OUT_OFF % 16 == 0 && OROW % 16 == 0 &&
+                    BAR_OFF % 16 == 0,
+                "alignment");
 };
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -151,10 +167,69 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's accumulator row, without
+// waiting (tcgen05.wait::ld before use).
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t* u) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]),
+        "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]),
+        "=r"(u[14]), "=r"(u[15])
+      : "r"(taddr));
+}
+
+// Bulk copy shared -> global (16-byte aligned, size a multiple of 16), in
+// this thread's current bulk group.
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_addr(src)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// Wait until at most one of this thread's bulk groups still reads its source.
+__device__ __forceinline__ void bulk_wait_read1() {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// Bulk copy global -> shared (16-byte aligned, size a multiple of 16),
+// completing on `bar`.
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ void dense_abort(volatile int* abort_flag, int* status) {
   *abort_flag = 1;
   if (status) atomicCAS(status, 0, 2);
 }
+
+// Bucket of consecutive tiles: a binary search over the bucket starts only
+// when a tile leaves the current bucket.
+struct BucketTracker {
+  int bucket = 0, end = 0;
+  __device__ __forceinline__ int at(const int* starts, int num_sets, int slot) {
+    if (slot >= end) {
+      bucket = bucket_of_slot(starts, num_sets, slot);
+      end = __ldg(starts + bucket + 1);
+    }
+    return bucket;
+  }
+};
 
 template <int N>
 __global__ void __launch_bounds__(288, 1) dense_bf16_kernel(DenseParams p) {
@@ -166,7 +241,10 @@ __global__ void __launch_bounds__(288, 1) dense_bf16_kernel(DenseParams p) {
   uint64_t* a_free = bars + SH::STAGES;          // [STAGES], MMA commit
   uint64_t* acc_full = bars + 2 * SH::STAGES;    // [ACC], MMA commit
   uint64_t* acc_empty = acc_full + SH::ACC;      // [ACC], 128 epilogue arrivals
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + SH::ACC);
+  uint64_t* raw_full = acc_empty + SH::ACC;      // [RAW], 128 producer arrivals + bytes
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(raw_full + SH::RAW);
+  unsigned char* raw = dsm + SH::RAW_OFF;
+  unsigned char* out = dsm + SH::OUT_OFF;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int t = threadIdx.x;
   const int warp = t >> 5;
@@ -190,6 +268,7 @@ __global__ void __launch_bounds__(288, 1) dense_bf16_kernel(DenseParams p) {
       mbar_init(acc_full + i, 1);
       mbar_init(acc_empty + i, 128);
     }
+    for (int i = 0; i < SH::RAW; ++i) mbar_init(raw_full + i, 128);
     *abort_flag = 0;
   }
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -205,72 +284,141 @@ __global__ void __launch_bounds__(288, 1) dense_bf16_kernel(DenseParams p) {
 
   if (warp < 4) {
     // ------------------------------------------------ producer
+    // Thread t handles row t of every tile.  With a raw ring, the rows of the
+    // next RAW tiles are in flight as bulk copies while this one is converted;
+    // block ids are loaded one tile ahead of their use (idq holds the ids of
+    // the tiles in flight, id_ahead the next one's).
+    constexpr int IDQ = SH::RAW > 0 ? SH::RAW : 1;
+    auto load_id = [&](long long task) {
+      return task < t1 ? __ldg(p.order + task * 128 + t) : -1;
+    };
+    auto issue_raw = [&](long long task, int b) {
+      if constexpr (SH::RAW > 0) {
+        const int rs = (int)((task - t0) % SH::RAW);
+        if (b >= 0 && b < p.nblocks) {
+          mbar_arrive_expect_tx(raw_full + rs, N * 2);
+          bulk_copy(raw + (size_t)rs * SH::RAW_BYTES + (size_t)t * SH::ROW,
+                    p.x + (long long)b * N, N * 2, raw_full + rs);
+        } else {
+          mbar_arrive(raw_full + rs);
+        }
+      }
+    };
+    int idq[IDQ];
+#pragma unroll
+    for (int d = 0; d < IDQ; ++d) idq[d] = load_id(t0 + d);
+    if constexpr (SH::RAW > 0) {
+#pragma unroll
+      for (int d = 0; d < IDQ; ++d)
+        if (t0 + d < t1) issue_raw(t0 + d, idq[d]);
+    }
+    int id_ahead = load_id(t0 + IDQ);
     int i = 0, cur_set = -1;
+    bool aborted = false;
+    BucketTracker bt;
     for (long long task = t0; task < t1; ++task) {
       const int slot = (int)(task * 128);
-      const int bucket = bucket_of_slot(p.starts, S, slot);
-      const int b = __ldg(p.order + slot + t);
+      const int bucket = bt.at(p.starts, S, slot);
+      const int b = idq[0];
       const bool active = b >= 0 && b < p.nblocks;
+      // this thread's row of the tile: from the raw ring, or straight from global memory
+      const int4* xs;
+      if constexpr (SH::RAW > 0) {
+        const int rs = (int)((task - t0) % SH::RAW);
+        if (!mbar_wait_bounded(raw_full + rs, (uint32_t)((task - t0) / SH::RAW) & 1u,
+                               abort_flag)) {
+          dense_abort(abort_flag, p.status);
+          aborted = true;
+          break;
+        }
+        xs = reinterpret_cast<const int4*>(raw + (size_t)rs * SH::RAW_BYTES + (size_t)t * SH::ROW);
+      } else {
+        xs = reinterpret_cast<const int4*>(p.x + (long long)(active ? b : 0) * N);
+      }
       if (bucket >= S) {  // skip (identity) or bad set (zeros)
         if (active) {
           float* y = p.y + (long long)b * N;
-          const int16_t* x = p.x + (long long)b * N;
-          for (int k = 0; k < N; ++k) y[k] = bucket == S ? (float)x[k] : 0.f;
+          for (int c = 0; c < N / 8; ++c) {
+            const int4 raw8 = SH::RAW > 0 ? xs[c] : __ldg(xs + c);
+            const int16_t* h = reinterpret_cast<const int16_t*>(&raw8);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) y[8 * c + k] = bucket == S ? (float)h[k] : 0.f;
+          }
           if (bucket != S && p.status) atomicCAS(p.status, 0, 4);
         }
-        continue;
-      }
-      const int s = i % SH::STAGES;
-      if (i >= SH::STAGES &&
-          !mbar_wait_bounded(a_free + s, (uint32_t)((i / SH::STAGES) - 1) & 1u, abort_flag)) {
-        dense_abort(abort_flag, p.status);
-        break;
-      }
-      if (bucket != cur_set) {
-        // every MMA issued so far must be done before the image is replaced
-        if (i > 0) {
-          const int j = i - 1;
-          if (!mbar_wait_bounded(a_free + j % SH::STAGES, (uint32_t)(j / SH::STAGES) & 1u,
-                                 abort_flag)) {
-            dense_abort(abort_flag, p.status);
-            break;
-          }
+      } else {
+        const int s = i % SH::STAGES;
+        if (i >= SH::STAGES &&
+            !mbar_wait_bounded(a_free + s, (uint32_t)((i / SH::STAGES) - 1) & 1u, abort_flag)) {
+          dense_abort(abort_flag, p.status);
+          aborted = true;
+          break;
         }
-        const int4* src = reinterpret_cast<const int4*>(p.kimg + (size_t)bucket * SH::B_BYTES);
-        int4* dst = reinterpret_cast<int4*>(b_img);
-        for (int k = t; k < (int)(SH::B_BYTES / 16); k += 128) dst[k] = __ldg(src + k);
-        cur_set = bucket;
-      }
-      // A row t of stage s: int16 -> bf16, 16-byte chunks at swizzled positions
-      const int4* xs = reinterpret_cast<const int4*>(p.x + (long long)(active ? b : 0) * N);
-      unsigned char* row = dsm + (size_t)s * SH::A_BYTES + (t >> 3) * 1024 + (t & 7) * 128;
-#pragma unroll 4
-      for (int c = 0; c < N / 8; ++c) {
-        int4 raw = active ? __ldg(xs + c) : make_int4(0, 0, 0, 0);
-        const int16_t* h = reinterpret_cast<const int16_t*>(&raw);
-        __nv_bfloat162 q[4];
+        if (bucket != cur_set) {
+          // every MMA issued so far must be done before the image is replaced
+          if (i > 0) {
+            const int j = i - 1;
+            if (!mbar_wait_bounded(a_free + j % SH::STAGES, (uint32_t)(j / SH::STAGES) & 1u,
+                                   abort_flag)) {
+              dense_abort(abort_flag, p.status);
+              aborted = true;
+              break;
+            }
+          }
+          const int4* src = reinterpret_cast<const int4*>(p.kimg + (size_t)bucket * SH::B_BYTES);
+          int4* dst = reinterpret_cast<int4*>(b_img);
+          for (int k = t; k < (int)(SH::B_BYTES / 16); k += 128) dst[k] = __ldg(src + k);
+          cur_set = bucket;
+        }
+        // A row t of stage s: int16 -> bf16, 16-byte chunks at swizzled positions
+        unsigned char* row = dsm + (size_t)s * SH::A_BYTES + (t >> 3) * 1024 + (t & 7) * 128;
+#pragma unroll 8
+        for (int c = 0; c < N / 8; ++c) {
+          int4 raw8 = !active ? make_int4(0, 0, 0, 0) : SH::RAW > 0 ? xs[c] : __ldg(xs + c);
+          const int16_t* h = reinterpret_cast<const int16_t*>(&raw8);
+          __nv_bfloat162 q[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          q[k] = __floats2bfloat162_rn((float)h[2 * k], (float)h[2 * k + 1]);
-        const int kb = c >> 3, cc = c & 7;
-        unsigned char* dst = row + kb * (128 * 128) + ((cc ^ (t & 7)) << 4);
-        *reinterpret_cast<int4*>(dst) = *reinterpret_cast<int4*>(q);
+          for (int k = 0; k < 4; ++k)
+            q[k] = __floats2bfloat162_rn((float)h[2 * k], (float)h[2 * k + 1]);
+          const int kb = c >> 3, cc = c & 7;
+          unsigned char* dst = row + kb * (128 * 128) + ((cc ^ (t & 7)) << 4);
+          *reinterpret_cast<int4*>(dst) = *reinterpret_cast<int4*>(q);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(a_full + s);
+        ++i;
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(a_full + s);
-      ++i;
+      // advance the id queue; this thread's raw row is read, so its slot takes
+      // the tile RAW ahead (generic reads ordered before the asynchronous write)
+#pragma unroll
+      for (int d = 0; d + 1 < IDQ; ++d) idq[d] = idq[d + 1];
+      idq[IDQ - 1] = id_ahead;
+      if constexpr (SH::RAW > 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (task + SH::RAW < t1) issue_raw(task + SH::RAW, id_ahead);
+      }
+      id_ahead = load_id(task + IDQ + 1);
+    }
+    if (SH::RAW > 0 && aborted) {
+      // let bulk copies still in flight land before the CTA exits
+      const uint64_t ts = global_ns();
+      while (global_ns() - ts < 200000ull) {
+      }
     }
   } else if (warp < 8) {
     // ------------------------------------------------ epilogue
     const int r = t - 128;  // accumulator lane = tile row
     const uint32_t lane_base = tmem + ((uint32_t)((warp - 4) * 32) << 16);
     int i = 0;
+    BucketTracker bt;
+    int b_next = t0 < t1 ? __ldg(p.order + t0 * 128 + r) : -1;
     for (long long task = t0; task < t1; ++task) {
       const int slot = (int)(task * 128);
-      const int bucket = bucket_of_slot(p.starts, S, slot);
+      const int bucket = bt.at(p.starts, S, slot);
+      const int b = b_next;  // ids one tile ahead
+      b_next = task + 1 < t1 ? __ldg(p.order + (task + 1) * 128 + r) : -1;
       if (bucket >= S) continue;
       const int a = i % SH::ACC;
-      const int b = __ldg(p.order + slot + r);
       const bool active = b >= 0 && b < p.nblocks;
       if (!mbar_wait_bounded(acc_full + a, (uint32_t)(i / SH::ACC) & 1u, abort_flag)) {
         dense_abort(abort_flag, p.status);
@@ -278,28 +426,51 @@ __global__ void __launch_bounds__(288, 1) dense_bf16_kernel(DenseParams p) {
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       float* y = p.y + (long long)(active ? b : 0) * N;
-#pragma unroll 1
-      for (int c0 = 0; c0 < N; c0 += 16) {
-        float v[16];
-        tmem_ld16(lane_base + (uint32_t)(a * N + c0), v);
+      if constexpr (SH::OUT > 0) {
+        // whole row into registers, accumulator released, row staged in
+        // shared memory and written by one bulk copy
+        uint32_t u[N];
+#pragma unroll
+        for (int c0 = 0; c0 < N; c0 += 16) tmem_ld16_async(lane_base + (uint32_t)(a * N + c0), u + c0);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(acc_empty + a);
+        unsigned char* orow = out + (size_t)(i & 1) * SH::OUT_BYTES + (size_t)r * SH::OROW;
+        bulk_wait_read1();  // the copy that last read this buffer is done with it
         if (active) {
 #pragma unroll
-          for (int k = 0; k < 16; k += 4)
-            *reinterpret_cast<float4*>(y + c0 + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+          for (int c = 0; c < N; c += 4)
+            *reinterpret_cast<uint4*>(orow + 4 * c) = make_uint4(u[c], u[c + 1], u[c + 2], u[c + 3]);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          bulk_store(y, orow, N * 4);
         }
+        bulk_commit();  // one group per tile, so groups alternate between the two buffers
+      } else {
+#pragma unroll 1
+        for (int c0 = 0; c0 < N; c0 += 16) {
+          float v[16];
+          tmem_ld16(lane_base + (uint32_t)(a * N + c0), v);
+          if (active) {
+#pragma unroll
+            for (int k = 0; k < 16; k += 4)
+              *reinterpret_cast<float4*>(y + c0 + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(acc_empty + a);
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mbar_arrive(acc_empty + a);
       ++i;
     }
+    if constexpr (SH::OUT > 0) bulk_wait_all();
   } else if (t == 256) {
     // ------------------------------------------------ MMA issuer
     constexpr uint32_t kIdesc = bf16_idesc(128, N);
     const uint32_t b0 = smem_addr(b_img);
     int i = 0;
+    BucketTracker bt;
     for (long long task = t0; task < t1; ++task) {
       const int slot = (int)(task * 128);
-      const int bucket = bucket_of_slot(p.starts, S, slot);
+      const int bucket = bt.at(p.starts, S, slot);
       if (bucket >= S) continue;
       const int s = i % SH::STAGES, a = i % SH::ACC;
       if (!mbar_wait_bounded(a_full + s, (uint32_t)(i / SH::STAGES) & 1u, abort_flag) ||
@@ -356,9 +527,10 @@ __global__ void __launch_bounds__(256) dense_int_kernel(DenseParams p) {
   const long long t1 = min(ntasks, t0 + chunk);
   const int half = 1 << (p.frac_bits - 1);
   int cached = -1;  // the bucket is CTA-uniform, so every thread tracks the same value
+  BucketTracker bt;
   for (long long task = t0; task < t1; ++task) {
     const int slot = (int)(task * 128);
-    const int bucket = bucket_of_slot(p.starts, p.num_sets, slot);
+    const int bucket = bt.at(p.starts, p.num_sets, slot);
     if (bucket < p.num_sets && bucket != cached) {
       __syncthreads();
       const int16_t* K = p.kint + (size_t)bucket * N * N;
