@@ -322,10 +322,138 @@ __device__ __forceinline__ int bucket_of_slot(const int* starts, int num_sets, i
   return lo;
 }
 
+// ---------------------------------------------------------------- staging
+// Inverse kernels read int32 coefficients, 32 or 64 contiguous bytes per
+// lane per block; for N = 32 and 64 their input is copied into shared memory
+// with cp.async one
+// task ahead (and the block ids two tasks ahead), so the global-memory
+// latency is off the critical path.  Stage layout, per warp: piece j (CH
+// bytes) of lane l of lane group g in block k of the task at
+// ((k J + j) 32 + g L + l) CH -- the reads of one (k, j) step are 32
+// consecutive pieces (no bank conflicts) while the copies walk the task's
+// blocks in global order (coalesced).
+__host__ __device__ constexpr bool batch_staged(int log2n, int kind) {
+  // measured: a gain where a block spans several lanes (N = 32, 64); larger
+  // blocks leave no room for the stage next to the permutation buffer
+  return kind == 1 && (log2n == 5 || log2n == 6);
+}
+
+template <int LOG2N, int KIND>
+struct BatchStage {
+  static constexpr int N = 1 << LOG2N;
+  static constexpr int IB = KIND == 0 ? 2 : 4;  // input bytes per value
+  static constexpr int E = 1 << batch_log2e(LOG2N);
+  static constexpr int L = N / E;
+  static constexpr int K = batch_k(LOG2N, KIND == 1);
+  static constexpr int GROUPS = 32 / L;
+  static constexpr int G = GROUPS * K;
+  static constexpr int LANE_BYTES = E * IB;
+  static constexpr int CH = LANE_BYTES < 16 ? LANE_BYTES : 16;  // bytes per copy
+  static constexpr int J = LANE_BYTES / CH;                     // copies per lane and block
+  static constexpr int CPB = L * J;                             // copies per block
+  static constexpr int PER_LANE = K * J;                        // copies per lane and task
+  static constexpr int BYTES = G * N * IB;
+  static constexpr int IDS_BYTES = 2 * G * 4;                   // block ids of two tasks
+  static_assert(G % 4 == 0 && BYTES % 16 == 0, "stage alignment");
+};
+
+// Shared memory of one warp: permutation buffer, then (staged kernels) the
+// stage and the block ids.
+template <int LOG2N, int KIND>
+__host__ __device__ constexpr int batch_warp_bytes() {
+  return batch_task_group(LOG2N, KIND == 1) * perm_region_words(LOG2N) * 4 +
+         (batch_staged(LOG2N, KIND)
+              ? BatchStage<LOG2N, KIND>::BYTES + BatchStage<LOG2N, KIND>::IDS_BYTES
+              : 0);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Asynchronous global -> shared copy of BYTES (4, 8 or 16); zero-filled
+// without reading when !valid.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(uint32_t dst, const void* src, bool valid) {
+  const int n = valid ? BYTES : 0;
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(n)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(dst), "l"(src),
+                 "n"(BYTES), "r"(n)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// Copy the G block ids of task t into `ids` (16-byte pieces).
+template <int G>
+__device__ __forceinline__ void stage_order(const BatchParams& p, long long t, int* ids,
+                                            int lane32) {
+  if (lane32 < G / 4)
+    cp_async<16>(smem_u32(ids + 4 * lane32), p.order + t * G + 4 * lane32, true);
+}
+
+// Copy the input blocks listed in `ids` into the stage.
+template <int LOG2N, int KIND>
+__device__ __forceinline__ void stage_blocks(const BatchParams& p, const int* ids, char* stage,
+                                             int lane32) {
+  using St = BatchStage<LOG2N, KIND>;
+  const char* in = static_cast<const char*>(p.in);
+  const uint32_t sbase = smem_u32(stage);
+#pragma unroll
+  for (int u = 0; u < St::PER_LANE; ++u) {
+    const int c = lane32 + 32 * u;
+    const int s = c / St::CPB, q = c % St::CPB;
+    const int b = ids[s];
+    const bool valid = b >= 0 && (long long)b < p.nblocks;
+    const int k = s / St::GROUPS, g = s % St::GROUPS;
+    const int l = q / St::J, j = q % St::J;
+    const uint32_t dst = sbase + (uint32_t)(((k * St::J + j) * 32 + g * St::L + l) * St::CH);
+    const char* src = valid ? in + ((long long)b * St::N * St::IB + q * St::CH) : in;
+    cp_async<St::CH>(dst, src, valid);
+  }
+}
+
+// This lane's E values of block k of the staged task.
+template <int LOG2N, int KIND>
+__device__ __forceinline__ void stage_read(const char* stage, int k, int lane32,
+                                           int32_t (&v)[BatchStage<LOG2N, KIND>::E]) {
+  using St = BatchStage<LOG2N, KIND>;
+  constexpr int VPC = St::CH / St::IB;  // values per copy
+#pragma unroll
+  for (int j = 0; j < St::J; ++j) {
+    const char* src = stage + ((k * St::J + j) * 32 + lane32) * St::CH;
+    uint32_t w[St::CH / 4];
+    if constexpr (St::CH == 16) {
+      const uint4 t = *reinterpret_cast<const uint4*>(src);
+      w[0] = t.x; w[1] = t.y; w[2] = t.z; w[3] = t.w;
+    } else if constexpr (St::CH == 8) {
+      const uint2 t = *reinterpret_cast<const uint2*>(src);
+      w[0] = t.x; w[1] = t.y;
+    } else {
+      w[0] = *reinterpret_cast<const uint32_t*>(src);
+    }
+#pragma unroll
+    for (int x = 0; x < VPC; ++x) {
+      if constexpr (St::IB == 2)
+        v[j * VPC + x] = (x & 1) ? (int32_t)w[x / 2] >> 16 : (int32_t)(int16_t)(w[x / 2] & 0xffffu);
+      else
+        v[j * VPC + x] = (int32_t)w[x];
+    }
+  }
+}
+
 // The tasks [t0, t1) of one warp.  `cache` holds the tables of sets
 // [set_lo, set_lo + cached count) when CACHED, else tables are read from
-// global memory.  `pbuf` is the warp's part of the permutation buffer: G
-// block regions of perm_region_words(LOG2N) words.
+// global memory.  `pbuf` is the warp's shared memory: G block regions of
+// perm_region_words(LOG2N) words (the permutation buffer), then for staged
+// kernels the stage and the block ids (batch_warp_bytes in all).
 template <int LOG2N, int KIND, bool CACHED>
 __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, long long t1,
                                             const int* cache, int set_lo, int32_t* pbuf) {
@@ -347,6 +475,20 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
   const SetTableShape sh{LOG2N, M::LOG2E, R, p.perms};
   const int rw = sh.round_words();
 
+  constexpr bool STAGED = batch_staged(LOG2N, KIND);
+  char* stage = reinterpret_cast<char*>(pbuf + G * RW);
+  int* ids = reinterpret_cast<int*>(stage + BatchStage<LOG2N, KIND>::BYTES);  // [2][G]
+  if constexpr (STAGED) {
+    if (t0 >= t1) return;
+    // prologue: ids of the first task, then its blocks and the next task's ids
+    stage_order<G>(p, t0, ids + (t0 & 1) * G, lane32);
+    cp_async_wait_all();
+    __syncwarp();
+    if (t0 + 1 < t1) stage_order<G>(p, t0 + 1, ids + ((t0 + 1) & 1) * G, lane32);
+    stage_blocks<LOG2N, KIND>(p, ids + (t0 & 1) * G, stage, lane32);
+    cp_async_commit();
+  }
+
   int bucket = 0, bucket_end = 0;
   for (long long t = t0; t < t1; ++t) {
     const int slot = (int)(t * G);
@@ -357,15 +499,32 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
     int b[K];
     bool active[K];
     int32_t v[K][E];
+    if constexpr (STAGED) {
+      cp_async_wait_all();
+      __syncwarp();
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      b[k] = __ldg(p.order + slot + k * GROUPS + grp);
-      active[k] = b[k] >= 0 && b[k] < p.nblocks;
-      if (active[k]) {
-        batch_load<LOG2N, KIND>(p, b[k], lane, v[k]);
-      } else {
+      for (int k = 0; k < K; ++k) {
+        b[k] = ids[(t & 1) * G + k * GROUPS + grp];
+        active[k] = b[k] >= 0 && b[k] < p.nblocks;
+        stage_read<LOG2N, KIND>(stage, k, lane32, v[k]);  // zero-filled when inactive
+      }
+      __syncwarp();
+      if (t + 1 < t1) {  // next task's blocks, and the ids of the one after
+        if (t + 2 < t1) stage_order<G>(p, t + 2, ids + (t & 1) * G, lane32);
+        stage_blocks<LOG2N, KIND>(p, ids + ((t + 1) & 1) * G, stage, lane32);
+      }
+      cp_async_commit();
+    } else {
 #pragma unroll
-        for (int i = 0; i < E; ++i) v[k][i] = 0;
+      for (int k = 0; k < K; ++k) {
+        b[k] = __ldg(p.order + slot + k * GROUPS + grp);
+        active[k] = b[k] >= 0 && b[k] < p.nblocks;
+        if (active[k]) {
+          batch_load<LOG2N, KIND>(p, b[k], lane, v[k]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < E; ++i) v[k][i] = 0;
+        }
       }
     }
     if (bucket < S) {
@@ -428,11 +587,12 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
     for (int k = 0; k < K; ++k)
       if (active[k]) batch_store<LOG2N, KIND>(p, b[k], lane, v[k]);
   }
+  if constexpr (STAGED) cp_async_wait_all();
 }
 
 // One CTA's share of a bucketed batch: CTA `cta` of `ncta` walks a contiguous
 // range of warp tasks.  `smem` is the dynamic shared memory: the cached set
-// tables (max_cached_sets x set_words) followed by the permutation buffer.
+// tables (max_cached_sets x set_words) followed by batch_warp_bytes per warp.
 // KIND 0: int16 -> int32 forward; KIND 1: int32 -> int16 inverse.
 template <int LOG2N, int KIND>
 __device__ __forceinline__ void batch_cta(const BatchParams& p, long long cta, long long ncta,
@@ -477,7 +637,7 @@ __device__ __forceinline__ void batch_cta(const BatchParams& p, long long cta, l
   }
   __syncthreads();
 
-  int32_t* wbuf = pbuf + (size_t)warp * G * RW;
+  int32_t* wbuf = pbuf + (size_t)warp * (batch_warp_bytes<LOG2N, KIND>() / 4);
   if (cached)
     batch_tasks<LOG2N, KIND, true>(p, t0, t1, cache, set_lo, wbuf);
   else
@@ -485,11 +645,10 @@ __device__ __forceinline__ void batch_cta(const BatchParams& p, long long cta, l
 }
 
 // Dynamic shared memory of batch_cta for block size 2^LOG2N without the set
-// tables: the permutation buffer (one region per block of a warp task).
+// tables: batch_warp_bytes per warp.
 template <int LOG2N, int KIND>
 __host__ __device__ inline size_t batch_pbuf_bytes(int threads) {
-  return (size_t)(threads / 32) * batch_task_group(LOG2N, KIND == 1) * perm_region_words(LOG2N) *
-         4;
+  return (size_t)(threads / 32) * batch_warp_bytes<LOG2N, KIND>();
 }
 
 template <int LOG2N, int KIND>
