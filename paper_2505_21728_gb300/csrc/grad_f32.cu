@@ -23,44 +23,54 @@ __global__ void hygt_theta_to_table(const float* __restrict__ theta, float2* __r
 }
 
 template <int LOG2N>
-static void config_sized(int angles, long long nblocks, int* threads, int* grid, size_t* smem) {
+static void config_sized(int num_sets, int rounds, long long nblocks, int* threads, int* grid,
+                         size_t* smem, int* cache_tables, int* group) {
+  using M = GradMap<LOG2N>;
   int dev = 0;
   cudaGetDevice(&dev);
   const DeviceInfo info = device_info(dev);
-  // up to two CTAs per SM; each warp needs its accumulators and scratch
-  const size_t per_warp = grad_smem_bytes<LOG2N>(1, angles);
-  const size_t budget2 = (size_t)info.max_smem_optin / 2;
-  int warps = (int)(budget2 / per_warp);
-  if (warps > kGradThreadsMax / 32) warps = kGradThreadsMax / 32;
-  if (warps < 1) warps = per_warp <= (size_t)info.max_smem_optin ? 1 : 0;
-  *threads = warps * 32;
-  *smem = grad_smem_bytes<LOG2N>(warps, angles);
-  if (warps == 0) {
+  const int angles = num_sets * rounds * LOG2N * (M::N / 2);
+  const size_t per_warp = grad_warp_bytes<LOG2N>(angles);
+  const size_t tables = grad_table_bytes<LOG2N>(num_sets, rounds);
+  const size_t budget = (size_t)info.max_smem_optin;
+  *group = M::G;
+  // one CTA per SM: as many warps as fit next to the tables (up to 12)
+  *cache_tables = tables + per_warp <= budget && tables <= budget / 4 ? 1 : 0;
+  const size_t avail = budget - (*cache_tables ? tables : 0);
+  int warps = (int)(avail / per_warp);
+  if (warps > kGradThreads / 32) warps = kGradThreads / 32;
+  if (warps < 1) {
+    *threads = 0;
     *grid = 0;
+    *smem = 0;
     return;
   }
-  int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hygt_grad_kernel<LOG2N>, *threads, *smem);
-  if (occ < 1) occ = 1;
-  const long long per_cta = (long long)warps * GradMap<LOG2N>::G;
-  long long need = (nblocks + per_cta - 1) / per_cta;
-  long long g = (long long)occ * info.sms;
-  if (need < g) g = need;
+  *threads = warps * 32;
+  *smem = (*cache_tables ? tables : 0) + (size_t)warps * per_warp;
+  const long long tasks = (nblocks + M::G - 1) / M::G + num_sets + 2;
+  long long g = info.sms;
+  if (tasks < g * warps) g = (tasks + warps - 1) / warps;
   if (g < 1) g = 1;
   *grid = (int)g;
 }
 
-void grad_config(int log2n, int angles, long long nblocks, int* threads, int* grid, size_t* smem) {
+void grad_config(int log2n, int num_sets, int rounds, long long nblocks, int* threads, int* grid,
+                 size_t* smem, int* cache_tables, int* group) {
   switch (log2n) {
-    case 1: config_sized<1>(angles, nblocks, threads, grid, smem); break;
-    case 2: config_sized<2>(angles, nblocks, threads, grid, smem); break;
-    case 3: config_sized<3>(angles, nblocks, threads, grid, smem); break;
-    case 4: config_sized<4>(angles, nblocks, threads, grid, smem); break;
-    case 5: config_sized<5>(angles, nblocks, threads, grid, smem); break;
-    case 6: config_sized<6>(angles, nblocks, threads, grid, smem); break;
-    case 7: config_sized<7>(angles, nblocks, threads, grid, smem); break;
-    case 8: config_sized<8>(angles, nblocks, threads, grid, smem); break;
-    default: *threads = 0; *grid = 0; *smem = 0;
+#define HYGT_GRAD_CASE(n)                                                                  \
+  case n:                                                                                  \
+    config_sized<n>(num_sets, rounds, nblocks, threads, grid, smem, cache_tables, group);  \
+    break;
+    HYGT_GRAD_CASE(1)
+    HYGT_GRAD_CASE(2)
+    HYGT_GRAD_CASE(3)
+    HYGT_GRAD_CASE(4)
+    HYGT_GRAD_CASE(5)
+    HYGT_GRAD_CASE(6)
+    HYGT_GRAD_CASE(7)
+    HYGT_GRAD_CASE(8)
+#undef HYGT_GRAD_CASE
+    default: *threads = 0; *grid = 0; *smem = 0; *cache_tables = 0; *group = 0;
   }
 }
 

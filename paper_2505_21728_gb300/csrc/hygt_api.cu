@@ -12,6 +12,7 @@
 #include "../../include/hygt.h"
 #include "hygt_batch.cuh"
 #include "hygt_dense.cuh"
+#include "hygt_f32u.cuh"
 #include "hygt_grad.cuh"
 #include "hygt_mixed.cuh"
 #include "hygt_launch.cuh"
@@ -335,20 +336,39 @@ hygt_status hygt_inverse(hygt_plan plan, const int32_t* d_y, int16_t* d_x, const
   return to_status(hygt::launch_int_inv(plan->log2n, p, (cudaStream_t)stream));
 }
 
+// FP32 transform.  Without set indices every block uses set 0: the one-set
+// kernels (four blocks per lane group, the set's table in shared memory);
+// with set indices, the direct kernels.
+static hygt_status f32_call(hygt_plan plan, const float* in, float* out, const uint16_t* d_set,
+                            int64_t nblocks, hygt_stream stream, int* d_status, bool inverse) {
+  hygt_status s = check_io(plan, in, out, nblocks);
+  if (s != HYGT_OK || nblocks == 0) return s;
+  if (!d_set) {
+    hygt::F32uParams u{};
+    u.in = in;
+    u.out = out;
+    u.nblocks = nblocks;
+    u.tab = static_cast<const float2*>(plan->d_tab_f32);
+    u.perm = plan->d_perm;
+    u.perm_mask = plan->perm_mask;
+    u.rounds = plan->rounds;
+    const cudaError_t e = hygt::launch_f32u(plan->log2n, inverse ? 1 : 0, u, (cudaStream_t)stream);
+    if (e != cudaErrorInvalidConfiguration) return to_status(e);
+    cudaGetLastError();  // table too large for shared memory: direct kernels
+  }
+  hygt::Params p = base_params(plan, in, out, d_set, nblocks, d_status, true);
+  return to_status(inverse ? hygt::launch_f32_inv(plan->log2n, p, (cudaStream_t)stream)
+                           : hygt::launch_f32_fwd(plan->log2n, p, (cudaStream_t)stream));
+}
+
 hygt_status hygt_forward_f32(hygt_plan plan, const float* d_x, float* d_y, const uint16_t* d_set,
                              int64_t nblocks, hygt_stream stream, int* d_status) {
-  hygt_status s = check_io(plan, d_x, d_y, nblocks);
-  if (s != HYGT_OK || nblocks == 0) return s;
-  hygt::Params p = base_params(plan, d_x, d_y, d_set, nblocks, d_status, true);
-  return to_status(hygt::launch_f32_fwd(plan->log2n, p, (cudaStream_t)stream));
+  return f32_call(plan, d_x, d_y, d_set, nblocks, stream, d_status, false);
 }
 
 hygt_status hygt_inverse_f32(hygt_plan plan, const float* d_y, float* d_x, const uint16_t* d_set,
                              int64_t nblocks, hygt_stream stream, int* d_status) {
-  hygt_status s = check_io(plan, d_y, d_x, nblocks);
-  if (s != HYGT_OK || nblocks == 0) return s;
-  hygt::Params p = base_params(plan, d_y, d_x, d_set, nblocks, d_status, true);
-  return to_status(hygt::launch_f32_inv(plan->log2n, p, (cudaStream_t)stream));
+  return f32_call(plan, d_y, d_x, d_set, nblocks, stream, d_status, true);
 }
 
 size_t hygt_batch_workspace_bytes(hygt_plan plan, int64_t nblocks) {
@@ -577,42 +597,53 @@ static int plan_angles(hygt_plan plan) {
   return plan->num_sets * plan->rounds * plan->log2n * (1 << (plan->log2n - 1));
 }
 
+// Backward workspace: the CTA partials of dL/dtheta, then (used when set
+// indices are given) the set-bucketed schedule of the backward's task size.
+struct GradWork {
+  int threads, grid, cache_tables, group;
+  size_t smem, partials, sched_off, total;
+};
+
+static GradWork grad_work(hygt_plan plan, int64_t nblocks) {
+  GradWork w{};
+  hygt::grad_config(plan->log2n, plan->num_sets, plan->rounds, nblocks, &w.threads, &w.grid,
+                    &w.smem, &w.cache_tables, &w.group);
+  if (w.threads == 0) return w;
+  w.partials = (size_t)(w.grid > 0 ? w.grid : 1) * plan_angles(plan) * sizeof(double);
+  w.sched_off = hygt::align16(w.partials);
+  w.total = w.sched_off + hygt::batch_layout(plan->num_sets, nblocks, w.group).total;
+  return w;
+}
+
 size_t hygt_backward_workspace_bytes(hygt_plan plan, int64_t nblocks) {
-  if (!plan || nblocks < 0) return 0;
-  int threads = 0, grid = 0;
-  size_t smem = 0;
-  hygt::grad_config(plan->log2n, plan_angles(plan), nblocks, &threads, &grid, &smem);
-  if (threads == 0) return 0;
-  return (size_t)(grid > 0 ? grid : 1) * plan_angles(plan) * sizeof(double);
+  if (!plan || nblocks < 0 || nblocks > kBatchMaxBlocks) return 0;
+  const GradWork w = grad_work(plan, nblocks);
+  return w.threads == 0 ? 0 : w.total;
 }
 
 hygt_status hygt_backward_f32(hygt_plan plan, const float* d_y, const float* d_gy, float* d_gx,
                               double* d_gtheta, const uint16_t* d_set, int64_t nblocks,
                               void* d_work, size_t work_bytes, hygt_stream stream, int* d_status) {
-  if (!plan || nblocks < 0 || !d_gtheta) return HYGT_ERR_ARG;
+  if (!plan || nblocks < 0 || nblocks > kBatchMaxBlocks || !d_gtheta) return HYGT_ERR_ARG;
   hygt_status s = check_io(plan, d_y, d_gx, nblocks);
   if (s != HYGT_OK) return s;
   if (nblocks > 0 && (!d_gy || !aligned16(d_gy))) return HYGT_ERR_ARG;
   const int angles = plan_angles(plan);
-  int threads = 0, grid = 0;
-  size_t smem = 0;
-  hygt::grad_config(plan->log2n, angles, nblocks, &threads, &grid, &smem);
-  if (threads == 0) return HYGT_ERR_UNSUPPORTED;
-  if (!d_work || work_bytes < (size_t)(grid > 0 ? grid : 1) * angles * sizeof(double))
-    return HYGT_ERR_ARG;
+  const GradWork w = grad_work(plan, nblocks);
+  if (w.threads == 0) return HYGT_ERR_UNSUPPORTED;
+  if (!d_work || !aligned16(d_work) || work_bytes < w.total) return HYGT_ERR_ARG;
   if (nblocks == 0) {
     return to_status(cudaMemsetAsync(d_gtheta, 0, (size_t)angles * sizeof(double),
                                      (cudaStream_t)stream));
   }
   hygt::GradLaunch gl{};
   gl.log2n = plan->log2n;
-  gl.threads = threads;
-  gl.grid = grid;
-  gl.smem = smem;
+  gl.threads = w.threads;
+  gl.grid = w.grid;
+  gl.smem = w.smem;
   gl.p.y = d_y;
   gl.p.gy = d_gy;
   gl.p.gx = d_gx;
-  gl.p.set = d_set;
   gl.p.nblocks = nblocks;
   gl.p.tab = static_cast<const float2*>(plan->d_tab_f32);
   gl.p.perm = plan->d_perm;
@@ -620,8 +651,21 @@ hygt_status hygt_backward_f32(hygt_plan plan, const float* d_y, const float* d_g
   gl.p.rounds = plan->rounds;
   gl.p.num_sets = plan->num_sets;
   gl.p.angles = angles;
+  gl.p.cache_tables = w.cache_tables;
   gl.p.partials = static_cast<double*>(d_work);
   gl.p.status = d_status;
+  if (d_set) {
+    // tasks of one set each: bucket the blocks by set
+    char* sched = static_cast<char*>(d_work) + w.sched_off;
+    const hygt::BatchLayout L = hygt::batch_layout(plan->num_sets, nblocks, w.group);
+    cudaError_t e = hygt::batch_build(d_set, nblocks, plan->num_sets, w.group, sched,
+                                      (cudaStream_t)stream);
+    if (e != cudaSuccess) return to_status(e);
+    gl.p.order = reinterpret_cast<const int*>(sched + L.order);
+    gl.p.starts = reinterpret_cast<const int*>(sched + L.starts);
+    gl.p.meta = reinterpret_cast<const int*>(sched + L.meta);
+    gl.p.tmax = L.tmax;
+  }
   return to_status(hygt::launch_grad(gl, d_gtheta, (cudaStream_t)stream));
 }
 

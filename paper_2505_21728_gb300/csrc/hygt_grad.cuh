@@ -11,30 +11,37 @@
 // passes in reverse (permutation slots undone by scatter), recomputing each
 // pass's input instead of storing it, and ends with dL/dx.
 //
-// Mapping as in hygt_device.cuh: a block is held by L = N / 8 sub-warp lanes
-// with 8 values each; cross-lane passes exchange y and g with
-// __shfl_xor_sync.  dL/dtheta: every pair of a pass is owned by exactly one
-// lane of the block (the lane that holds its m side), which adds the term to
-// a private shared-memory accumulator of its (warp, block slot).  The
-// accumulation order is fixed, so the result is deterministic.  At the end
-// each CTA sums its accumulators in FP64 into one partial vector; a second
-// kernel sums the partials of all CTAs in a fixed order.
+// Mapping.  A block is held by L = N / E lanes with E = 8 values each (a lane
+// group); every lane group holds K = 4 blocks of the same set, so each
+// (cos, sin) pair read from shared memory serves K rotations and the K
+// contributions to a dL/dtheta entry are summed in a register before they
+// reach the accumulators.  Cross-lane passes exchange y and g with
+// __shfl_xor_sync.  A warp task is G = (32 / L) K blocks of one set: the
+// blocks in order when no set indices are given, else the slots of the
+// set-bucketed schedule (skip and bad-set buckets are whole tasks).
+//
+// dL/dtheta: every pair of a pass is owned by exactly one lane of the group
+// (the lane that holds its m side), which adds the K-block sum to a private
+// shared-memory accumulator row of its (warp, lane group).  The accumulation
+// order within a row is fixed by the task order.  At the end each CTA sums
+// its rows in FP64 into one partial vector; a second kernel sums the
+// partials of all CTAs in a fixed order.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "hygt_batch.cuh"
 #include "hygt_device.cuh"
 
 namespace hygt {
 
-constexpr int kGradThreadsMax = 256;
+constexpr int kGradThreads = 384;
 
 struct GradParams {
   const float* y;       // [B][N] forward output
   const float* gy;      // [B][N] dL/dy
   float* gx;            // [B][N] dL/dx
-  const uint16_t* set;  // nullable
   long long nblocks;
   const float2* tab;    // (cos, sin) per pair, [S][R][k][N/2]
   const uint8_t* perm;  // [S][R][N] or nullptr
@@ -42,6 +49,12 @@ struct GradParams {
   int rounds;
   int num_sets;
   int angles;           // S * R * k * N/2
+  // schedule (set-bucketed, task size G) or nullptr: blocks in order, set 0
+  const int* order;
+  const int* starts;
+  const int* meta;
+  long long tmax;
+  int cache_tables;     // the tables of all sets are copied to shared memory
   double* partials;     // [gridDim.x][angles]
   int* status;
 };
@@ -52,28 +65,46 @@ struct GradMap {
   static constexpr int LOG2E = LOG2N < 3 ? LOG2N : 3;
   static constexpr int E = 1 << LOG2E;
   static constexpr int L = N / E;
-  static constexpr int G = 32 / L;
+  static constexpr int GROUPS = 32 / L;
+  static constexpr int K = 4;
+  static constexpr int G = GROUPS * K;
+  static constexpr int RW = N + L;  // words per block region of the permutation buffer
 };
 
-// Shared memory: accumulators [warps][G][angles + pad] floats, then the
-// permutation scratch [warps][32 * E] (y) and [warps][32 * E] (g).  The
-// accumulator stride is padded to an odd multiple of the 4-word lane step,
-// so the G block slots of a warp, updating the same angle index, use
-// different banks.
+// Shared memory (bytes): the tables of all sets when cached (float2 per pair,
+// then the permutation bytes, 16-byte padded), then per warp GROUPS
+// accumulator rows of grad_acc_stride(angles) floats and the permutation
+// buffer (y and g regions of GROUPS blocks).  The row stride is odd, so the
+// lane groups of a warp updating the same angle use different banks.
 __host__ __device__ inline int grad_acc_stride(int angles) { return ((angles + 3) & ~3) + 4 + 1; }
 
 template <int LOG2N>
-__host__ __device__ inline size_t grad_smem_bytes(int warps, int angles) {
-  return (size_t)warps * GradMap<LOG2N>::G * grad_acc_stride(angles) * 4 +
-         (size_t)warps * 2 * 32 * GradMap<LOG2N>::E * 4;
+__host__ __device__ inline size_t grad_table_bytes(int num_sets, int rounds) {
+  using M = GradMap<LOG2N>;
+  const size_t tab = (size_t)num_sets * rounds * LOG2N * (M::N / 2) * 8;
+  const size_t perm = ((size_t)num_sets * rounds * M::N + 15) & ~(size_t)15;
+  return tab + perm;
+}
+
+template <int LOG2N>
+__host__ __device__ inline size_t grad_warp_bytes(int angles) {
+  using M = GradMap<LOG2N>;
+  return (size_t)M::GROUPS * grad_acc_stride(angles) * 4 + (size_t)2 * M::GROUPS * M::RW * 4;
+}
+
+// word of element e in a block region: one padding word after each lane's E values
+template <int LOG2N>
+__device__ __forceinline__ int grad_word(int e) {
+  return e + (e >> GradMap<LOG2N>::LOG2E);
 }
 
 template <int LOG2N, int P>
-__device__ __forceinline__ void grad_pass(float (&v)[GradMap<LOG2N>::E],
-                                          float (&g)[GradMap<LOG2N>::E], const float2* row,
-                                          float* acc, int lane, bool counts) {
+__device__ __forceinline__ void grad_pass(float (&v)[GradMap<LOG2N>::K][GradMap<LOG2N>::E],
+                                          float (&g)[GradMap<LOG2N>::K][GradMap<LOG2N>::E],
+                                          const float2* row, float* acc, int lane) {
   using M = GradMap<LOG2N>;
   constexpr int E = M::E;
+  constexpr int K = M::K;
   if constexpr (P < M::LOG2E) {
 #pragma unroll
     for (int jl = 0; jl < E / 2; ++jl) {
@@ -81,12 +112,18 @@ __device__ __forceinline__ void grad_pass(float (&v)[GradMap<LOG2N>::E],
       const int in = im | (1 << P);
       const int j = lane * (E / 2) + jl;
       const float2 cs = row[j];
-      const float ym = v[im], yn = v[in], gm = g[im], gn = g[in];
-      if (counts) acc[j] += gm * yn - gn * ym;
-      v[im] = cs.x * ym - cs.y * yn;
-      v[in] = cs.y * ym + cs.x * yn;
-      g[im] = cs.x * gm - cs.y * gn;
-      g[in] = cs.y * gm + cs.x * gn;
+      float sum = 0.f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const float ym = v[k][im], yn = v[k][in], gm = g[k][im], gn = g[k][in];
+        sum = fmaf(gm, yn, sum);
+        sum = fmaf(-gn, ym, sum);
+        v[k][im] = cs.x * ym - cs.y * yn;
+        v[k][in] = cs.y * ym + cs.x * yn;
+        g[k][im] = cs.x * gm - cs.y * gn;
+        g[k][in] = cs.y * gm + cs.x * gn;
+      }
+      acc[j] += sum;
     }
   } else {
     constexpr int Q = P - M::LOG2E;
@@ -96,113 +133,161 @@ __device__ __forceinline__ void grad_pass(float (&v)[GradMap<LOG2N>::E],
 #pragma unroll
     for (int i = 0; i < E; ++i) {
       const float2 cs = row[jbase + i];
-      const float yo = v[i], go = g[i];
-      const float yp = __shfl_xor_sync(kFullMask, yo, D);
-      const float gp = __shfl_xor_sync(kFullMask, go, D);
-      if (counts && !upper) acc[jbase + i] += go * yp - gp * yo;  // m side owns the pair
       const float sp = upper ? cs.y : -cs.y;
-      v[i] = cs.x * yo + sp * yp;
-      g[i] = cs.x * go + sp * gp;
+      float sum = 0.f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const float yo = v[k][i], go = g[k][i];
+        const float yp = __shfl_xor_sync(kFullMask, yo, D);
+        const float gp = __shfl_xor_sync(kFullMask, go, D);
+        sum = fmaf(go, yp, sum);
+        sum = fmaf(-gp, yo, sum);
+        v[k][i] = cs.x * yo + sp * yp;
+        g[k][i] = cs.x * go + sp * gp;
+      }
+      if (!upper) acc[jbase + i] += sum;  // the m side owns the pair
     }
   }
 }
 
-template <int LOG2N, int K>
-__device__ __forceinline__ void grad_round(float (&v)[GradMap<LOG2N>::E],
-                                           float (&g)[GradMap<LOG2N>::E], const float2* rtab,
-                                           float* racc, int lane, bool counts) {
+template <int LOG2N, int J>
+__device__ __forceinline__ void grad_round(float (&v)[GradMap<LOG2N>::K][GradMap<LOG2N>::E],
+                                           float (&g)[GradMap<LOG2N>::K][GradMap<LOG2N>::E],
+                                           const float2* rtab, float* racc, int lane) {
   constexpr int N = 1 << LOG2N;
-  if constexpr (K < LOG2N) {
-    constexpr int P = LOG2N - 1 - K;  // passes in reverse order
-    grad_pass<LOG2N, P>(v, g, rtab + P * (N / 2), racc + P * (N / 2), lane, counts);
-    grad_round<LOG2N, K + 1>(v, g, rtab, racc, lane, counts);
+  if constexpr (J < LOG2N) {
+    constexpr int P = LOG2N - 1 - J;  // passes in reverse order
+    grad_pass<LOG2N, P>(v, g, rtab + P * (N / 2), racc + P * (N / 2), lane);
+    grad_round<LOG2N, J + 1>(v, g, rtab, racc, lane);
   }
 }
 
 template <int LOG2N>
-__global__ void __launch_bounds__(kGradThreadsMax) hygt_grad_kernel(GradParams p) {
+__global__ void __launch_bounds__(kGradThreads, 1) hygt_grad_kernel(GradParams p) {
   using M = GradMap<LOG2N>;
   constexpr int N = M::N;
   constexpr int E = M::E;
   constexpr int L = M::L;
+  constexpr int K = M::K;
+  constexpr int GROUPS = M::GROUPS;
   constexpr int G = M::G;
-  extern __shared__ __align__(16) float gsm[];
+  constexpr int RW = M::RW;
+  extern __shared__ __align__(16) unsigned char gsm[];
 
+  const int S = p.num_sets;
+  const int R = p.rounds;
+  const int rowlen = LOG2N * (N / 2);  // angles per round
+  const float2* tab = p.tab;
+  const uint8_t* perm = p.perm;
+  size_t off = 0;
+  if (p.cache_tables) {
+    const size_t tb = (size_t)S * R * rowlen * 8;
+    const int4* src = reinterpret_cast<const int4*>(p.tab);
+    int4* dst = reinterpret_cast<int4*>(gsm);
+    for (size_t i = threadIdx.x; i < tb / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+    tab = reinterpret_cast<const float2*>(gsm);
+    if (p.perm) {
+      uint8_t* pd = gsm + tb;
+      for (size_t i = threadIdx.x; i < (size_t)S * R * N; i += blockDim.x) pd[i] = __ldg(p.perm + i);
+      perm = pd;
+    }
+    off = grad_table_bytes<LOG2N>(S, R);
+  }
   const int warps = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5;
   const int lane32 = threadIdx.x & 31;
-  const int sub = lane32 / L;
+  const int grp = lane32 / L;
   const int lane = lane32 % L;
   const int stride = grad_acc_stride(p.angles);
-  float* acc_all = gsm;
-  float* acc = acc_all + (size_t)(warp * G + sub) * stride;
-  float* ybuf = gsm + (size_t)warps * G * stride + (size_t)warp * 2 * 32 * E + sub * N;
-  float* gbuf = ybuf + 32 * E;
-  for (int i = threadIdx.x; i < warps * G * stride; i += blockDim.x) acc_all[i] = 0.f;
+  float* acc_all = reinterpret_cast<float*>(gsm + off);
+  float* acc = acc_all + (size_t)(warp * GROUPS + grp) * stride;
+  float* ybuf = acc_all + (size_t)warps * GROUPS * stride + (size_t)warp * 2 * GROUPS * RW +
+                grp * RW;
+  float* gbuf = ybuf + GROUPS * RW;
+  for (int i = threadIdx.x; i < warps * GROUPS * stride; i += blockDim.x) acc_all[i] = 0.f;
   __syncthreads();
 
-  const long long warps_total = (long long)gridDim.x * warps;
-  const long long gw = (long long)blockIdx.x * warps + warp;
-  const int R = p.rounds;
-  const int rowlen = LOG2N * (N / 2);  // angles per round
-
-  for (long long base = gw * G; base < p.nblocks; base += warps_total * G) {
-    const long long b = base + sub;
-    const bool valid = b < p.nblocks;
-    unsigned set = 0;
-    if (valid && p.set) set = __ldg(p.set + b);
-    const bool skip = set == 0xFFFFu;
-    const bool bad = !skip && set >= (unsigned)p.num_sets;
-    const unsigned cset = (skip || bad) ? 0u : set;
-    float v[E], g[E];
-    if (valid) {
-      load_f32<E>(p.y + b * N + lane * E, v);
-      load_f32<E>(p.gy + b * N + lane * E, g);
+  // this warp's contiguous range of tasks
+  long long ntasks;
+  if (p.order) {
+    if (p.meta[1] != (int)p.nblocks || p.meta[2] != S || p.meta[3] != G) {
+      if (threadIdx.x == 0 && blockIdx.x == 0 && p.status) atomicCAS(p.status, 0, 1);
+      ntasks = 0;
     } else {
-#pragma unroll
-      for (int i = 0; i < E; ++i) v[i] = g[i] = 0.f;
+      ntasks = max(0LL, min((long long)p.meta[0], p.tmax));
     }
-    // skip, bad and tail blocks run the passes like set 0 (the warp stays
-    // converged for the shuffles) but add nothing to dL/dtheta
-    const bool counts = valid && !skip && !bad;
-    float keep[E];
+  } else {
+    ntasks = (p.nblocks + G - 1) / G;
+  }
+  const long long warps_total = (long long)gridDim.x * warps;
+  const long long chunk = (ntasks + warps_total - 1) / warps_total;
+  const long long t0 = min(ntasks, ((long long)blockIdx.x * warps + warp) * chunk);
+  const long long t1 = min(ntasks, t0 + chunk);
+
+  int bucket = 0, bucket_end = 0;
+  for (long long t = t0; t < t1; ++t) {
+    const long long slot = t * G;
+    if (p.order && slot >= bucket_end) {  // warp-uniform
+      bucket = bucket_of_slot(p.starts, S, (int)slot);
+      bucket_end = __ldg(p.starts + bucket + 1);
+    }
+    long long b[K];
+    bool valid[K];
+    float v[K][E], g[K][E];
 #pragma unroll
-    for (int i = 0; i < E; ++i) keep[i] = g[i];
-    for (int r = R - 1; r >= 0; --r) {
-      if (p.perm && ((p.perm_mask >> r) & 1u)) {
-        const uint8_t* prow = p.perm + ((size_t)cset * R + r) * N;
+    for (int k = 0; k < K; ++k) {
+      const long long s = slot + k * GROUPS + grp;
+      b[k] = p.order ? (long long)__ldg(p.order + s) : s;
+      valid[k] = b[k] >= 0 && b[k] < p.nblocks;
+      if (valid[k]) {
+        load_f32<E>(p.y + b[k] * N + lane * E, v[k]);
+        load_f32<E>(p.gy + b[k] * N + lane * E, g[k]);
+      } else {
 #pragma unroll
-        for (int i = 0; i < E; ++i) {
-          const int d = prow[lane * E + i];
-          ybuf[d] = v[i];
-          gbuf[d] = g[i];
-        }
-        __syncwarp();
-#pragma unroll
-        for (int i = 0; i < E; ++i) {
-          v[i] = ybuf[lane * E + i];
-          g[i] = gbuf[lane * E + i];
-        }
-        __syncwarp();
+        for (int i = 0; i < E; ++i) v[k][i] = g[k][i] = 0.f;
       }
-      const size_t off = ((size_t)cset * R + r) * rowlen;
-      grad_round<LOG2N, 0>(v, g, p.tab + off, acc + off, lane, counts);
     }
-    if (skip) {
+    if (bucket < S) {
+      for (int r = R - 1; r >= 0; --r) {
+        if (perm && ((p.perm_mask >> r) & 1u)) {  // undo the gather: v_prev[perm[e]] = v[e]
+          const uint8_t* prow = perm + ((size_t)bucket * R + r) * N + lane * E;
 #pragma unroll
-      for (int i = 0; i < E; ++i) g[i] = keep[i];
-    } else if (bad) {
+          for (int k = 0; k < K; ++k) {
 #pragma unroll
-      for (int i = 0; i < E; ++i) g[i] = 0.f;
-      if (valid && lane == 0 && p.status) atomicCAS(p.status, 0, 4);
-    }
-    if (valid) store_f32<E>(p.gx + b * N + lane * E, g);
+            for (int i = 0; i < E; ++i) {
+              const int d = grad_word<LOG2N>(prow[i]);
+              ybuf[d] = v[k][i];
+              gbuf[d] = g[k][i];
+            }
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+              v[k][i] = ybuf[grad_word<LOG2N>(lane * E + i)];
+              g[k][i] = gbuf[grad_word<LOG2N>(lane * E + i)];
+            }
+            __syncwarp();
+          }
+        }
+        const size_t o = ((size_t)bucket * R + r) * rowlen;
+        grad_round<LOG2N, 0>(v, g, tab + o, acc + o, lane);
+      }
+    } else if (bucket == S + 1) {  // bad set index: zero gradient, status
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) g[k][i] = 0.f;
+        if (valid[k] && lane == 0 && p.status) atomicCAS(p.status, 0, 4);
+      }
+    }  // skip bucket (S): identity, dL/dx = dL/dy
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (valid[k]) store_f32<E>(p.gx + b[k] * N + lane * E, g[k]);
   }
   __syncthreads();
-  // CTA partial: sum of all (warp, block slot) accumulators, in FP64, fixed order
+  // CTA partial: sum of all (warp, lane group) rows, in FP64, fixed order
   for (int a = threadIdx.x; a < p.angles; a += blockDim.x) {
     double s = 0.0;
-    for (int k = 0; k < warps * G; ++k) s += (double)acc_all[(size_t)k * stride + a];
+    for (int k = 0; k < warps * GROUPS; ++k) s += (double)acc_all[(size_t)k * stride + a];
     p.partials[(size_t)blockIdx.x * p.angles + a] = s;
   }
 }
@@ -224,8 +309,10 @@ struct GradLaunch {
 };
 
 cudaError_t launch_grad(GradLaunch& gl, double* gtheta, cudaStream_t stream);
-// Grid, threads and shared memory of the backward launch (0 threads: too
-// many angles for the shared-memory accumulators).
-void grad_config(int log2n, int angles, long long nblocks, int* threads, int* grid, size_t* smem);
+// Launch shape of the backward: threads, grid and shared memory (0 threads:
+// too many angles for the shared-memory accumulators), whether the tables are
+// cached, and the task size G of its schedule.
+void grad_config(int log2n, int num_sets, int rounds, long long nblocks, int* threads, int* grid,
+                 size_t* smem, int* cache_tables, int* group);
 
 }  // namespace hygt

@@ -194,6 +194,30 @@ def test_f32_parity_free_theta(gpu, orc, log2n, rounds):
     assert e.value.code == gpu.HYGT_ERR_UNSUPPORTED
 
 
+@pytest.mark.parametrize("log2n,rounds,with_perm", [(1, 2, True), (2, 1, False), (3, 2, True),
+                                                  (4, 2, True), (5, 3, True), (6, 4, False),
+                                                  (6, 2, True), (7, 2, True), (8, 3, True)])
+def test_f32_one_set_parity(gpu, orc, log2n, rounds, with_perm):
+    """FP32 forward and inverse without set indices (every block uses set 0;
+    the one-set kernels): against the FP64 oracle, ragged block count."""
+    import torch
+    N = 1 << log2n
+    S, B = 2, 5003
+    theta = inputs.theta_uniform((S, rounds, log2n, N // 2), seed=11).astype(np.float32)
+    perms = inputs.permutations(S, rounds, N, seed=11) if with_perm else None
+    x = np.random.default_rng(11).standard_normal((B, N)).astype(np.float32)
+    plan = gpu.Plan.from_theta(log2n, rounds, theta, perms)
+    y = plan.forward_f32(_t(x))
+    xr = plan.inverse_f32(y)
+    torch.cuda.synchronize()
+    ye, _ = orc.fwd_f64(x.astype(np.float64), theta.astype(np.float64), log2n, rounds, perms, None)
+    assert _rel_err(y.cpu().numpy().astype(np.float64), ye) <= FP_TOL
+    xe, _ = orc.inv_f64(y.cpu().numpy().astype(np.float64), theta.astype(np.float64), log2n,
+                        rounds, perms, None)
+    assert _rel_err(xr.cpu().numpy().astype(np.float64), xe) <= FP_TOL
+    assert _rel_err(xr.cpu().numpy().astype(np.float64), x.astype(np.float64)) <= 1e-4
+
+
 # ---------------------------------------------------------------- workloads
 def test_workload_4x4_full(gpu, orc):
     """4x4 blocks (N=16), 2 rounds, one set, 65,536 blocks: every block."""
