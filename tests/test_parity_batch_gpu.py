@@ -130,3 +130,30 @@ def test_batch_workload_8x8_full(gpu, orc):
     del ye
     xe, _ = orc.inv_int(y, d["angle_idx"], w.log2n, w.rounds, d["perms"], d["sets"])
     assert np.array_equal(xr, xe)
+
+
+def test_batch_workload_16x16_full(gpu, orc):
+    """16x16 blocks (N=256), 3 rounds, 16 sets, all 16,777,216 blocks through
+    the bucketed path; four 131,072-block windows spread over the batch
+    (start, thirds, end) compared with the oracle bit for bit."""
+    import torch
+    from paper_2505_21728_gb300 import workloads
+    w = workloads.get("hygt16x16_r3_s16")
+    d = w.generate()
+    n = w.nblocks
+    plan = gpu.Plan(w.log2n, w.rounds, d["angle_idx"], d["perms"])
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    b = gpu.Batch(plan, n).build(_t(d["sets"]))
+    y = b.forward(_t(d["x"]), status=st)
+    xr = b.inverse(y, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    CH = 131072
+    for off in (0, n // 3, 2 * n // 3, n - CH):
+        sl = slice(off, off + CH)
+        ye, ste = orc.fwd_int(d["x"][sl], d["angle_idx"], w.log2n, w.rounds, d["perms"],
+                              d["sets"][sl])
+        assert ste == 0
+        assert np.array_equal(y[sl].cpu().numpy(), ye), off
+        xe, _ = orc.inv_int(ye, d["angle_idx"], w.log2n, w.rounds, d["perms"], d["sets"][sl])
+        assert np.array_equal(xr[sl].cpu().numpy(), xe), off

@@ -244,3 +244,25 @@ def test_workload_8x8_105_sets_full(gpu, orc):
     xe, ste = orc.inv_int(y, d["angle_idx"], w.log2n, w.rounds, d["perms"], d["sets"])
     assert ste == 0
     assert np.array_equal(xr, xe)
+
+
+def test_f32_workload_16x16_sample(gpu, orc):
+    """FP32 path of the 16x16 / 3-round / 16-set workload (the first 262,144
+    blocks, set indices given): forward and inverse within the FP32 bound."""
+    import torch
+    from paper_2505_21728_gb300 import workloads
+    w = workloads.truncated(workloads.get("hygt16x16_r3_s16"), 262144)
+    d = w.generate()
+    plan = gpu.Plan(w.log2n, w.rounds, d["angle_idx"], d["perms"])
+    x = d["x"].astype(np.float32)
+    st = _status()
+    y = plan.forward_f32(_t(x), _t(d["sets"]), status=st)
+    xr = plan.inverse_f32(y, _t(d["sets"]), status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    theta = inputs.theta_from_indices(d["angle_idx"])
+    ye, _ = orc.fwd_f64(x.astype(np.float64), theta, w.log2n, w.rounds, d["perms"], d["sets"])
+    assert _rel_err(y.cpu().numpy().astype(np.float64), ye) <= FP_TOL
+    xe, _ = orc.inv_f64(y.cpu().numpy().astype(np.float64), theta, w.log2n, w.rounds, d["perms"],
+                        d["sets"])
+    assert _rel_err(xr.cpu().numpy().astype(np.float64), xe) <= FP_TOL
