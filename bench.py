@@ -460,8 +460,9 @@ def mixed_leg(dev, stream, steps=20, name="mixed_frame_2160p16"):
 
 def dense_leg(w, data, d_x, d_s, dev, stream, steps, hygt_step_ms):
     """The dense matrix transform of the same blocks and sets (one N x N
-    matrix per set, the HyGT's own matrices): tcgen05 BF16 and int32 CUDA-core
-    kernels, one direction; the HyGT step is forward + inverse."""
+    matrix per set, the HyGT's own matrices): tcgen05 BF16 and FP8 (E4M3,
+    per-block scales) and int32 CUDA-core kernels, one direction; the HyGT
+    step is forward + inverse."""
     import torch
     from paper_2505_21728_gb300 import hygt
     K = hygt.Plan(w.log2n, w.rounds, data["angle_idx"], data["perms"]).dense_matrices()
@@ -488,8 +489,9 @@ def dense_leg(w, data, d_x, d_s, dev, stream, steps, hygt_step_ms):
     peak, kind = measured_peaks()
     bytes_per_block = 2 * N + 4 * N + 4  # int16 in, 32-bit out, slot id
     for name, kd, buf in (("bf16_tcgen05", hygt.DENSE_KLT_BF16, y),
+                          ("fp8_e4m3_tcgen05", hygt.DENSE_KLT_FP8, y),
                           ("int32_cuda_core", hygt.DENSE_KLT_INT, yi)):
-        if (kd == hygt.DENSE_KLT_BF16 and N < 64) or (kd == hygt.DENSE_KLT_INT and N > 64):
+        if (kd != hygt.DENSE_KLT_INT and N < 64) or (kd == hygt.DENSE_KLT_INT and N > 64):
             continue
         ms = timed(lambda: d.apply(d_x, kind=kd, out=buf))
         gbs = nb * bytes_per_block / (ms / 1000.0) / 1e9

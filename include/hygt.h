@@ -258,21 +258,27 @@ void hygt_graph_destroy(hygt_graph graph);
  * Eq. 2 is such a matrix).  Blocks are bucketed by set in tiles of 128.
  *
  *   dense_klt_create  h_K host float [num_sets][N][N], row-major (y = K x);
- *        N = 16, 64 or 256; builds BF16 operand images (N = 64, 256) and
- *        the integer matrices round(2^frac_bits K) (|entries| <= 32767,
- *        else HYGT_ERR_ARG).  Synchronous.
+ *        N = 16, 64 or 256; builds BF16 and E4M3 operand images (N = 64,
+ *        256; the E4M3 image of a set is K * 448 / max|K|) and the integer
+ *        matrices round(2^frac_bits K) (|entries| <= 32767, else
+ *        HYGT_ERR_ARG).  Synchronous.
  *   dense_klt_workspace_bytes / dense_klt_build  schedule of nblocks blocks
  *        (as hygt_batch_build), async on stream.
  *   dense_klt_apply  kind DENSE_KLT_BF16: BF16 x BF16 products with FP32
  *        accumulation on the tensor cores (tcgen05), d_y float [nblocks][N],
- *        N = 64 or 256; kind DENSE_KLT_INT: d_y int32 [nblocks][N] =
- *        floor((round(2^f K) x + 2^(f-1)) / 2^f) on the CUDA cores, N = 16
- *        or 64.  Skip blocks are copied, bad set indices give zeros and
- *        HYGT_ERR_SET_INDEX in d_status.
+ *        N = 64 or 256; kind DENSE_KLT_FP8: E4M3 x E4M3 products with FP32
+ *        accumulation on the tensor cores, each block scaled by 448 /
+ *        max|x| (FP32) before rounding to E4M3 (saturating), the result
+ *        scaled back by the block's and the set's scales, d_y float
+ *        [nblocks][N], N = 64 or 256; kind DENSE_KLT_INT: d_y int32
+ *        [nblocks][N] = floor((round(2^f K) x + 2^(f-1)) / 2^f) on the CUDA
+ *        cores, N = 16 or 64.  Skip blocks are copied, bad set indices give
+ *        zeros and HYGT_ERR_SET_INDEX in d_status.
  */
 typedef struct dense_klt_s *dense_klt;
 #define DENSE_KLT_BF16 0
 #define DENSE_KLT_INT 1
+#define DENSE_KLT_FP8 2
 hygt_status dense_klt_create(dense_klt *out, int log2n, int num_sets, const float *h_K,
                              int frac_bits);
 void dense_klt_destroy(dense_klt d);

@@ -14,6 +14,7 @@
 // set, each lane one output row at a time.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <stdint.h>
 
 #include "hygt_batch.cuh"
@@ -39,10 +40,12 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major.
-__host__ __device__ constexpr uint32_t bf16_idesc(int m, int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
-         ((uint32_t)(m >> 4) << 24);
+// Instruction descriptor, FP32 accumulator, both operands K-major:
+// kind::f16 with BF16 A and B (format 1), or kind::f8f6f4 with E4M3 A and B
+// (format 0).
+__host__ __device__ constexpr uint32_t tc_idesc(int m, int n, bool fp8) {
+  return (1u << 4) | ((fp8 ? 0u : 1u) << 7) | ((fp8 ? 0u : 1u) << 10) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -62,13 +65,21 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
                : "memory");
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
-                                         uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d_tmem),
-      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-      : "memory");
+template <bool FP8>
+__device__ __forceinline__ void mma_tc(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                       uint32_t idesc, uint32_t accumulate) {
+  if constexpr (FP8)
+    asm volatile(
+        "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p; }" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  else
+    asm volatile(
+        "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -108,16 +119,20 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&r)[16]) {
 // producer alone (every role walks the same tile list and skips them).
 // Every wait is bounded by a time limit; a role that gives up raises the
 // CTA's abort flag, which the other roles' waits observe.
-// Shared memory: A stages (BF16 tiles, swizzled), the B image, the raw
-// ring (int16 tiles as gathered), the output row buffers (FP32 rows on their
-// way to global memory), barriers.  Raw and output rows are padded to an odd
+// Shared memory: A stages (BF16 or E4M3 tiles, swizzled), the B image, the
+// raw ring (int16 tiles as gathered), the output row buffers (FP32 rows on
+// their way to global memory), the FP8 row scales, barriers.  Raw and output rows are padded to an odd
 // number of 16-byte units, so that thread t accessing row t hits distinct
 // banks.
-template <int N>
-struct DenseBf16Shape {
-  static constexpr int KB = N / 64;                     // K blocks of 64 elements
-  static constexpr size_t A_BYTES = (size_t)128 * N * 2;
-  static constexpr size_t B_BYTES = (size_t)N * N * 2;
+template <int N, bool FP8>
+struct DenseTcShape {
+  static constexpr int EB = FP8 ? 1 : 2;                  // operand bytes per element
+  static constexpr int KP = FP8 && N < 128 ? 128 : N;     // K padded to whole 128-byte rows
+  static constexpr int ROWB = KP * EB;                    // bytes of one operand row
+  static constexpr int KB = ROWB / 128;                   // K blocks of 128 bytes
+  static constexpr int KSTEPS = ROWB / 32;                // MMAs per tile (32 bytes of K each)
+  static constexpr size_t A_BYTES = (size_t)128 * ROWB;
+  static constexpr size_t B_BYTES = (size_t)N * ROWB;
   static constexpr int STAGES = N <= 64 ? 4 : 1;         // A stages
   static constexpr int ACC = N <= 64 ? 4 : 2;            // accumulators in tensor memory
   static constexpr int RAW = N <= 64 ? 4 : 0;            // raw tiles in flight (0: direct loads)
@@ -127,15 +142,20 @@ struct DenseBf16Shape {
   static constexpr int OUT = N <= 64 ? 2 : 0;            // output row buffers per thread (0: direct stores)
   static constexpr int OROW = N * 4 + 16;                // output row pitch (bytes)
   static constexpr size_t OUT_BYTES = (size_t)128 * OROW;
+  // FP8: per-row scales of the last SR tiles (the producer runs at most
+  // STAGES + ACC tiles ahead of the epilogue)
+  static constexpr int SR = FP8 ? STAGES + ACC + 1 : 0;
   static constexpr size_t B_OFF = STAGES * A_BYTES;
   static constexpr size_t RAW_OFF = B_OFF + B_BYTES;
   static constexpr size_t OUT_OFF = RAW_OFF + RAW * RAW_BYTES;
-  static constexpr size_t BAR_OFF = OUT_OFF + OUT * OUT_BYTES;
-  static constexpr size_t SMEM = BAR_OFF + 256;
+  static constexpr size_t SC_OFF = OUT_OFF + OUT * OUT_BYTES;
+  static constexpr size_t BAR_OFF = SC_OFF + (size_t)SR * 128 * 4;
+  static constexpr size_t SMEM = BAR_OFF + 320;
   static constexpr int THREADS = 288;                   // 4 producer + 4 epilogue + 1 MMA warp
   static_assert(RAW_OFF % 16 == 0 && ROW % 16 == 0 && OUT_OFF % 16 == 0 && OROW % 16 == 0 &&
-                    BAR_OFF % 16 == 0,
+                    BAR_OFF % 16 == 0 && ROWB % 128 == 0,
                 "alignment");
+  static_assert((2 * STAGES + 2 * ACC + RAW + SR) * 8 + 8 <= 320, "barrier area");
 };
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -231,9 +251,9 @@ struct BucketTracker {
   }
 };
 
-template <int N>
-__global__ void __launch_bounds__(288, 1) dense_bf16_kernel(DenseParams p) {
-  using SH = DenseBf16Shape<N>;
+template <int N, bool FP8>
+__global__ void __launch_bounds__(288, 1) dense_tc_kernel(DenseParams p) {
+  using SH = DenseTcShape<N, FP8>;
   extern __shared__ __align__(1024) unsigned char dsm[];
   unsigned char* b_img = dsm + SH::B_OFF;
   uint64_t* bars = reinterpret_cast<uint64_t*>(dsm + SH::BAR_OFF);
@@ -242,7 +262,9 @@ __global__ void __launch_bounds__(288, 1) dense_bf16_kernel(DenseParams p) {
   uint64_t* acc_full = bars + 2 * SH::STAGES;    // [ACC], MMA commit
   uint64_t* acc_empty = acc_full + SH::ACC;      // [ACC], 128 epilogue arrivals
   uint64_t* raw_full = acc_empty + SH::ACC;      // [RAW], 128 producer arrivals + bytes
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(raw_full + SH::RAW);
+  uint64_t* sc_full = raw_full + SH::RAW;        // [SR], 128 producer arrivals (FP8)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sc_full + SH::SR);
+  float* scale_ring = reinterpret_cast<float*>(dsm + SH::SC_OFF);  // [SR][128]
   unsigned char* raw = dsm + SH::RAW_OFF;
   unsigned char* out = dsm + SH::OUT_OFF;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -269,6 +291,7 @@ __global__ void __launch_bounds__(288, 1) dense_bf16_kernel(DenseParams p) {
       mbar_init(acc_empty + i, 128);
     }
     for (int i = 0; i < SH::RAW; ++i) mbar_init(raw_full + i, 128);
+    for (int i = 0; i < SH::SR; ++i) mbar_init(sc_full + i, 128);
     *abort_flag = 0;
   }
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -365,27 +388,65 @@ __global__ void __launch_bounds__(288, 1) dense_bf16_kernel(DenseParams p) {
               break;
             }
           }
-          const int4* src = reinterpret_cast<const int4*>(p.kimg + (size_t)bucket * SH::B_BYTES);
+          const int4* src = reinterpret_cast<const int4*>((FP8 ? p.kimg8 : p.kimg) +
+                                                          (size_t)bucket * SH::B_BYTES);
           int4* dst = reinterpret_cast<int4*>(b_img);
           for (int k = t; k < (int)(SH::B_BYTES / 16); k += 128) dst[k] = __ldg(src + k);
           cur_set = bucket;
         }
-        // A row t of stage s: int16 -> bf16, 16-byte chunks at swizzled positions
+        // A row t of stage s, 16-byte chunks at swizzled positions
         unsigned char* row = dsm + (size_t)s * SH::A_BYTES + (t >> 3) * 1024 + (t & 7) * 128;
+        if constexpr (!FP8) {  // int16 -> bf16, 8 values per chunk
 #pragma unroll 8
-        for (int c = 0; c < N / 8; ++c) {
-          int4 raw8 = !active ? make_int4(0, 0, 0, 0) : SH::RAW > 0 ? xs[c] : __ldg(xs + c);
-          const int16_t* h = reinterpret_cast<const int16_t*>(&raw8);
-          __nv_bfloat162 q[4];
+          for (int c = 0; c < N / 8; ++c) {
+            int4 raw8 = !active ? make_int4(0, 0, 0, 0) : SH::RAW > 0 ? xs[c] : __ldg(xs + c);
+            const int16_t* h = reinterpret_cast<const int16_t*>(&raw8);
+            __nv_bfloat162 q[4];
 #pragma unroll
-          for (int k = 0; k < 4; ++k)
-            q[k] = __floats2bfloat162_rn((float)h[2 * k], (float)h[2 * k + 1]);
-          const int kb = c >> 3, cc = c & 7;
-          unsigned char* dst = row + kb * (128 * 128) + ((cc ^ (t & 7)) << 4);
-          *reinterpret_cast<int4*>(dst) = *reinterpret_cast<int4*>(q);
+            for (int k = 0; k < 4; ++k)
+              q[k] = __floats2bfloat162_rn((float)h[2 * k], (float)h[2 * k + 1]);
+            const int kb = c >> 3, cc = c & 7;
+            unsigned char* dst = row + kb * (128 * 128) + ((cc ^ (t & 7)) << 4);
+            *reinterpret_cast<int4*>(dst) = *reinterpret_cast<int4*>(q);
+          }
+        } else {  // int16 -> e4m3 with a per-row scale, 16 values per chunk
+          int amax = 0;
+          if (active) {
+#pragma unroll 8
+            for (int c = 0; c < N / 8; ++c) {
+              const int4 raw8 = SH::RAW > 0 ? xs[c] : __ldg(xs + c);
+              const int16_t* h = reinterpret_cast<const int16_t*>(&raw8);
+#pragma unroll
+              for (int k = 0; k < 8; ++k) amax = max(amax, abs((int)h[k]));
+            }
+          }
+          const float inv = amax > 0 ? 448.f / (float)amax : 1.f;
+          scale_ring[(i % SH::SR) * 128 + t] = amax > 0 ? (float)amax / 448.f : 1.f;
+#pragma unroll 4
+          for (int c = 0; c < SH::KP / 16; ++c) {
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+            if (active && c < N / 16) {
+#pragma unroll
+              for (int hh = 0; hh < 2; ++hh) {
+                const int4 raw8 = SH::RAW > 0 ? xs[2 * c + hh] : __ldg(xs + 2 * c + hh);
+                const int16_t* h = reinterpret_cast<const int16_t*>(&raw8);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                  const __nv_fp8x2_storage_t q2 = __nv_cvt_float2_to_fp8x2(
+                      make_float2((float)h[2 * k] * inv, (float)h[2 * k + 1] * inv),
+                      __NV_SATFINITE, __NV_E4M3);
+                  w[2 * hh + (k >> 1)] |= (uint32_t)q2 << (16 * (k & 1));
+                }
+              }
+            }
+            const int kb = c >> 3, cc = c & 7;
+            unsigned char* dst = row + kb * (128 * 128) + ((cc ^ (t & 7)) << 4);
+            *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+          }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(a_full + s);
+        if constexpr (FP8) mbar_arrive(sc_full + i % SH::SR);
         ++i;
       }
       // advance the id queue; this thread's raw row is read, so its slot takes
@@ -426,6 +487,14 @@ __global__ void __launch_bounds__(288, 1) dense_bf16_kernel(DenseParams p) {
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       float* y = p.y + (long long)(active ? b : 0) * N;
+      float osc = 1.f;  // FP8: row scale x set scale
+      if constexpr (FP8) {
+        if (!mbar_wait_bounded(sc_full + i % SH::SR, (uint32_t)(i / SH::SR) & 1u, abort_flag)) {
+          dense_abort(abort_flag, p.status);
+          break;
+        }
+        osc = scale_ring[(i % SH::SR) * 128 + r] * __ldg(p.kscale + bucket);
+      }
       if constexpr (SH::OUT > 0) {
         // whole row into registers, accumulator released, row staged in
         // shared memory and written by one bulk copy
@@ -439,8 +508,15 @@ __global__ void __launch_bounds__(288, 1) dense_bf16_kernel(DenseParams p) {
         bulk_wait_read1();  // the copy that last read this buffer is done with it
         if (active) {
 #pragma unroll
-          for (int c = 0; c < N; c += 4)
-            *reinterpret_cast<uint4*>(orow + 4 * c) = make_uint4(u[c], u[c + 1], u[c + 2], u[c + 3]);
+          for (int c = 0; c < N; c += 4) {
+            if constexpr (FP8) {
+              *reinterpret_cast<float4*>(orow + 4 * c) =
+                  make_float4(__uint_as_float(u[c]) * osc, __uint_as_float(u[c + 1]) * osc,
+                              __uint_as_float(u[c + 2]) * osc, __uint_as_float(u[c + 3]) * osc);
+            } else {
+              *reinterpret_cast<uint4*>(orow + 4 * c) = make_uint4(u[c], u[c + 1], u[c + 2], u[c + 3]);
+            }
+          }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           bulk_store(y, orow, N * 4);
         }
@@ -453,7 +529,8 @@ __global__ void __launch_bounds__(288, 1) dense_bf16_kernel(DenseParams p) {
           if (active) {
 #pragma unroll
             for (int k = 0; k < 16; k += 4)
-              *reinterpret_cast<float4*>(y + c0 + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+              *reinterpret_cast<float4*>(y + c0 + k) =
+                  make_float4(v[k] * osc, v[k + 1] * osc, v[k + 2] * osc, v[k + 3] * osc);
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -464,7 +541,7 @@ __global__ void __launch_bounds__(288, 1) dense_bf16_kernel(DenseParams p) {
     if constexpr (SH::OUT > 0) bulk_wait_all();
   } else if (t == 256) {
     // ------------------------------------------------ MMA issuer
-    constexpr uint32_t kIdesc = bf16_idesc(128, N);
+    constexpr uint32_t kIdesc = tc_idesc(128, N, FP8);
     const uint32_t b0 = smem_addr(b_img);
     int i = 0;
     BucketTracker bt;
@@ -482,11 +559,11 @@ __global__ void __launch_bounds__(288, 1) dense_bf16_kernel(DenseParams p) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a0 = smem_addr(dsm + (size_t)s * SH::A_BYTES);
 #pragma unroll
-      for (int k = 0; k < N / 16; ++k) {
+      for (int k = 0; k < SH::KSTEPS; ++k) {
         const uint32_t ka = (uint32_t)((k >> 2) * (128 * 128) + (k & 3) * 32);
         const uint32_t kb = (uint32_t)((k >> 2) * (N * 128) + (k & 3) * 32);
-        mma_bf16(tmem + (uint32_t)(a * N), sw128_desc(a0 + ka), sw128_desc(b0 + kb), kIdesc,
-                 k > 0 ? 1u : 0u);
+        mma_tc<FP8>(tmem + (uint32_t)(a * N), sw128_desc(a0 + ka), sw128_desc(b0 + kb), kIdesc,
+                    k > 0 ? 1u : 0u);
       }
       mma_commit(a_free + s);
       mma_commit(acc_full + a);
@@ -580,10 +657,10 @@ __global__ void __launch_bounds__(256) dense_int_kernel(DenseParams p) {
 }
 
 // ---------------------------------------------------------------- launchers
-template <int N>
-static cudaError_t launch_bf16(const DenseParams& p, cudaStream_t stream) {
-  using SH = DenseBf16Shape<N>;
-  auto kern = dense_bf16_kernel<N>;
+template <int N, bool FP8>
+static cudaError_t launch_tc(const DenseParams& p, cudaStream_t stream) {
+  using SH = DenseTcShape<N, FP8>;
+  auto kern = dense_tc_kernel<N, FP8>;
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
@@ -628,10 +705,11 @@ static cudaError_t launch_int(const DenseParams& p, cudaStream_t stream) {
 }
 
 cudaError_t launch_dense(int log2n, int kind, const DenseParams& p, cudaStream_t stream) {
-  if (kind == 0) {
+  if (kind == 0 || kind == 2) {
+    const bool fp8 = kind == 2;
     switch (log2n) {
-      case 6: return launch_bf16<64>(p, stream);
-      case 8: return launch_bf16<256>(p, stream);
+      case 6: return fp8 ? launch_tc<64, true>(p, stream) : launch_tc<64, false>(p, stream);
+      case 8: return fp8 ? launch_tc<256, true>(p, stream) : launch_tc<256, false>(p, stream);
       default: return cudaErrorInvalidValue;
     }
   }

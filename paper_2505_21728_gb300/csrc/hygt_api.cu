@@ -1,7 +1,9 @@
 // hygt_api.cu -- C ABI of libhygt.so: plan builder (host) and launch entry
 // points.  See include/hygt.h for the contract of every call.
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -671,8 +673,10 @@ hygt_status hygt_backward_f32(hygt_plan plan, const float* d_y, const float* d_g
 
 struct dense_klt_s {
   int log2n = 0, num_sets = 0, frac_bits = 0, device = 0;
-  unsigned char* d_kimg = nullptr;  // BF16 images (N = 64, 256)
-  int16_t* d_kint = nullptr;        // round(2^f K)
+  unsigned char* d_kimg = nullptr;   // BF16 images (N = 64, 256)
+  unsigned char* d_kimg8 = nullptr;  // E4M3 images (N = 64, 256)
+  float* d_kscale = nullptr;         // E4M3 scale per set
+  int16_t* d_kint = nullptr;         // round(2^f K)
 };
 
 // Round-to-nearest-even FP32 -> BF16 (finite inputs).
@@ -716,6 +720,36 @@ hygt_status dense_klt_create(dense_klt* out, int log2n, int num_sets, const floa
             }
     }
   }
+  // E4M3 image: each set's matrix scaled by 448 / max|K| (its scale is
+  // max|K| / 448), K padded with zeros to rows of KP = max(N, 128) bytes; per
+  // 128-column K block, N rows of 128 bytes, 8-row groups of 1024 bytes,
+  // 16-byte chunk c of row i stored at chunk c ^ (i % 8).
+  std::vector<uint8_t> img8;
+  std::vector<float> kscale;
+  if (N >= 64) {
+    const int KP = N < 128 ? 128 : N;
+    img8.assign((size_t)N * KP * num_sets, 0);
+    kscale.assign(num_sets, 1.f);
+    for (int s = 0; s < num_sets; ++s) {
+      const float* K = h_K + (size_t)s * per;
+      float amax = 0.f;
+      for (size_t i = 0; i < per; ++i) amax = std::max(amax, std::fabs(K[i]));
+      const float inv = amax > 0.f ? 448.f / amax : 1.f;
+      kscale[s] = amax > 0.f ? amax / 448.f : 1.f;
+      uint8_t* base = img8.data() + (size_t)s * N * KP;
+      for (int kb = 0; kb < KP / 128; ++kb)
+        for (int i = 0; i < N; ++i)
+          for (int c = 0; c < 8; ++c)
+            for (int e = 0; e < 16; ++e) {
+              const int k = kb * 128 + c * 16 + e;
+              const size_t byte = (size_t)kb * N * 128 + (size_t)(i / 8) * 1024 +
+                                  (size_t)(i % 8) * 128 + (size_t)((c ^ (i % 8)) * 16) + e;
+              base[byte] = k < N ? (uint8_t)__nv_cvt_float_to_fp8(K[(size_t)i * N + k] * inv,
+                                                                  __NV_SATFINITE, __NV_E4M3)
+                                 : (uint8_t)0;
+            }
+    }
+  }
   dense_klt d = new (std::nothrow) dense_klt_s();
   if (!d) return HYGT_ERR_OOM;
   d->log2n = log2n;
@@ -730,6 +764,12 @@ hygt_status dense_klt_create(dense_klt* out, int log2n, int num_sets, const floa
   if (st == HYGT_OK && !img.empty())
     st = upload(reinterpret_cast<void**>(&d->d_kimg), img.data(), img.size() * 2,
                 pad16(img.size() * 2));
+  if (st == HYGT_OK && !img8.empty())
+    st = upload(reinterpret_cast<void**>(&d->d_kimg8), img8.data(), img8.size(),
+                pad16(img8.size()));
+  if (st == HYGT_OK && !kscale.empty())
+    st = upload(reinterpret_cast<void**>(&d->d_kscale), kscale.data(), kscale.size() * 4,
+                pad16(kscale.size() * 4));
   if (st != HYGT_OK) {
     dense_klt_destroy(d);
     return st;
@@ -741,6 +781,8 @@ hygt_status dense_klt_create(dense_klt* out, int log2n, int num_sets, const floa
 void dense_klt_destroy(dense_klt d) {
   if (!d) return;
   if (d->d_kimg) cudaFree(d->d_kimg);
+  if (d->d_kimg8) cudaFree(d->d_kimg8);
+  if (d->d_kscale) cudaFree(d->d_kscale);
   if (d->d_kint) cudaFree(d->d_kint);
   delete d;
 }
@@ -764,8 +806,10 @@ hygt_status dense_klt_apply(dense_klt d, const void* d_work, const int16_t* d_x,
   if (nblocks == 0) return HYGT_OK;
   if (!d_work || !aligned16(d_work) || !d_x || !d_y || !aligned16(d_x) || !aligned16(d_y))
     return HYGT_ERR_ARG;
-  if (kind != DENSE_KLT_BF16 && kind != DENSE_KLT_INT) return HYGT_ERR_ARG;
-  if (kind == DENSE_KLT_BF16 && d->log2n < 6) return HYGT_ERR_UNSUPPORTED;
+  if (kind != DENSE_KLT_BF16 && kind != DENSE_KLT_INT && kind != DENSE_KLT_FP8)
+    return HYGT_ERR_ARG;
+  if ((kind == DENSE_KLT_BF16 || kind == DENSE_KLT_FP8) && d->log2n < 6)
+    return HYGT_ERR_UNSUPPORTED;
   if (kind == DENSE_KLT_INT && d->log2n > 6) return HYGT_ERR_UNSUPPORTED;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return HYGT_ERR_CUDA;
@@ -782,6 +826,8 @@ hygt_status dense_klt_apply(dense_klt d, const void* d_work, const int16_t* d_x,
   p.nblocks = nblocks;
   p.tmax = L.tmax;
   p.kimg = d->d_kimg;
+  p.kimg8 = d->d_kimg8;
+  p.kscale = d->d_kscale;
   p.kint = d->d_kint;
   p.num_sets = d->num_sets;
   p.frac_bits = d->frac_bits;

@@ -27,6 +27,7 @@ HYGT_ERR_TOO_LARGE = 7
 HYGT_SKIP_SET = 0xFFFF
 DENSE_KLT_BF16 = 0
 DENSE_KLT_INT = 1
+DENSE_KLT_FP8 = 2
 
 
 class HygtError(RuntimeError):
@@ -636,7 +637,7 @@ class DenseKLT:
     def apply(self, x, kind=DENSE_KLT_BF16, out=None, status=None, stream=None):
         import torch
         if out is None:
-            dt = torch.float32 if kind == DENSE_KLT_BF16 else torch.int32
+            dt = torch.int32 if kind == DENSE_KLT_INT else torch.float32
             out = torch.empty((x.shape[0], self.N), dtype=dt, device=x.device)
         pst = None if status is None else _dptr(status, torch.int32, None, "status")
         _check(dense_klt_apply(self.handle, self.work.data_ptr(), _dptr(x, torch.int16, self.N, "x"),

@@ -26,6 +26,17 @@ def bf16_round(a):
     return (u.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
 
 
+def e4m3_round(a):
+    """Round-to-nearest-even to FP8 E4M3 (4 exponent bits, bias 7, 3 mantissa
+    bits, subnormals below 2^-6), saturating at +-448; returned as float64."""
+    a = np.asarray(a, np.float64)
+    m = np.abs(a)
+    e = np.maximum(np.floor(np.log2(np.where(m > 0, m, 1.0))), -6.0)
+    q = 2.0 ** (e - 3)  # spacing of the binade
+    r = np.minimum(np.round(m / q) * q, 448.0)  # np.round: half to even
+    return np.sign(a) * r
+
+
 def hygt_matrices(orc, log2n, rounds, S, seed):
     N = 1 << log2n
     theta = inputs.theta_uniform((S, rounds, log2n, N // 2), seed=seed)
@@ -78,6 +89,52 @@ def test_dense_bf16_tensor_cores(gpu, orc, log2n, S, B):
     assert rel < 2 ** -7  # BF16 has 8 significant bits
 
 
+def test_e4m3_rounding_reference():
+    """The test's E4M3 rounding against values fixed by the format."""
+    v = np.array([0.0, 1.0, 1.0625, 1.1875, 448.0, 460.0, 470.0, 1e6, -3.3, 2.0 ** -9,
+                  2.0 ** -10, 3 * 2.0 ** -11, 0.013671875])
+    want = np.array([0.0, 1.0, 1.0, 1.25, 448.0, 448.0, 448.0, 448.0, -3.25, 2.0 ** -9,
+                     0.0, 2.0 ** -9, 0.013671875])
+    assert np.array_equal(e4m3_round(v), want)
+
+
+@pytest.mark.parametrize("log2n,S,B", [(6, 5, 3000), (6, 105, 200000), (8, 3, 20000)])
+def test_dense_fp8_tensor_cores(gpu, orc, log2n, S, B):
+    """E4M3 x E4M3 with FP32 accumulation: equal to the FP64 product of the
+    same E4M3-rounded, scaled operands within FP32 accumulation error, and
+    within the E4M3 precision of the exact transform."""
+    import torch
+    N = 1 << log2n
+    K = hygt_matrices(orc, log2n, 2, S, seed=3 * log2n).astype(np.float32)
+    x = inputs.laplacian_blocks(B, N, 60.0, -2048, 2047, seed=5)
+    sets = inputs.set_indices(B, S, seed=5, skip_frac=0.05)
+    d = gpu.DenseKLT(log2n, K).build(_t(sets), B)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    y = d.apply(_t(x), kind=gpu.DENSE_KLT_FP8, status=st).cpu().numpy().astype(np.float64)
+    assert int(st.item()) == 0
+    # operands as the library forms them (FP32 scale factors, E4M3 rounding)
+    kamax = np.abs(K).reshape(S, -1).max(axis=1).astype(np.float32)
+    kinv = np.float32(448.0) / kamax
+    kscale = kamax / np.float32(448.0)
+    K8 = e4m3_round((K * kinv[:, None, None]).astype(np.float32))
+    xamax = np.abs(x.astype(np.int32)).max(axis=1).astype(np.float32)
+    xinv = np.where(xamax > 0, np.float32(448.0) / np.maximum(xamax, 1), np.float32(1.0))
+    xscale = np.where(xamax > 0, xamax / np.float32(448.0), np.float32(1.0)).astype(np.float32)
+    x8 = e4m3_round((x.astype(np.float32) * xinv[:, None].astype(np.float32)).astype(np.float32))
+    osc = (xscale * kscale[np.where(sets == 0xFFFF, 0, np.minimum(sets, S - 1))]).astype(np.float32)
+    skip = sets == 0xFFFF
+    kk = K8[np.where(skip, 0, sets)]
+    yq = np.einsum("bij,bj->bi", kk, x8) * osc[:, None].astype(np.float64)
+    scale = np.einsum("bij,bj->bi", np.abs(kk), np.abs(x8)) * osc[:, None].astype(np.float64)
+    yq[skip] = x[skip]
+    scale[skip] = 0.0
+    assert np.all(np.abs(y - yq) <= (N * 2.0 ** -23 + 2.0 ** -22) * scale + 1e-9)
+    ye, _ = orc.dense_apply_f64(x.astype(np.float64), K.astype(np.float64), sets)
+    ye[skip] = x[skip]
+    rel = np.max(np.abs(y - ye)) / np.max(np.abs(ye))
+    assert rel < 2 ** -3  # E4M3 has 4 significant bits
+
+
 def test_dense_bad_set_and_empty(gpu, orc):
     import torch
     K = hygt_matrices(orc, 6, 2, 3, seed=9)
@@ -85,7 +142,7 @@ def test_dense_bad_set_and_empty(gpu, orc):
     sets = inputs.set_indices(300, 3, seed=9)
     sets[10] = 77
     d = gpu.DenseKLT(6, K.astype(np.float32)).build(_t(sets), 300)
-    for kind in (gpu.DENSE_KLT_BF16, gpu.DENSE_KLT_INT):
+    for kind in (gpu.DENSE_KLT_BF16, gpu.DENSE_KLT_INT, gpu.DENSE_KLT_FP8):
         st = torch.zeros(1, dtype=torch.int32, device="cuda")
         y = d.apply(_t(x), kind=kind, status=st).cpu().numpy()
         assert int(st.item()) == 4 and np.all(y[10] == 0)
