@@ -318,6 +318,36 @@ hygt_status hygt_forward_static(hygt_plan plan, const int16_t *d_x, int32_t *d_y
                                 const uint16_t *d_set, int64_t nblocks, hygt_stream stream,
                                 int *d_status);
 
+/*
+ * Host-buffer round trip of an integer batch: the forward transform of the
+ * blocks in host memory, their coefficients, and the inverse transform
+ * (reconstruction), all returned to host memory.  The paper's transform is
+ * what runs (bucketing + hygt_forward_batch + hygt_inverse_batch); the pipe
+ * adds the transfers: the batch goes through the GPU in chunks of
+ * chunk_blocks blocks on three streams, so the host-to-device copy of one
+ * chunk, the kernels of another and the device-to-host copies of a third
+ * overlap.  Host buffers should be page-locked (cudaHostAlloc or
+ * cudaHostRegister) for the copies to overlap; pageable memory works but
+ * serialises them.
+ *
+ *   hygt_host_pipe_create  allocates, on the current device, three chunk
+ *        slots (input, set indices, coefficients, reconstruction,
+ *        schedule workspace, a stream and a status word each); chunk_blocks
+ *        in 1 .. 2^26.  Synchronous.
+ *   hygt_host_roundtrip    h_x int16 [nblocks][N] in; h_set uint16 [nblocks]
+ *        or NULL (set 0); h_y int32 [nblocks][N] and h_xr int16 [nblocks][N]
+ *        out.  Synchronous: returns when every result is in host memory;
+ *        *h_status (nullable) receives the first device-side status
+ *        (HYGT_ERR_SET_INDEX for an out-of-range set index).  Calls on one
+ *        pipe must not overlap.
+ *   hygt_host_pipe_destroy frees the slots (waits for them first).
+ */
+typedef struct hygt_host_pipe_s *hygt_host_pipe;
+hygt_status hygt_host_pipe_create(hygt_host_pipe *out, hygt_plan plan, int64_t chunk_blocks);
+hygt_status hygt_host_roundtrip(hygt_host_pipe pipe, const int16_t *h_x, const uint16_t *h_set,
+                                int32_t *h_y, int16_t *h_xr, int64_t nblocks, int *h_status);
+void hygt_host_pipe_destroy(hygt_host_pipe pipe);
+
 /* Plan shape: any out-pointer may be NULL. */
 hygt_status hygt_plan_info(hygt_plan plan, int *log2n, int *rounds, int *num_sets,
                            int *is_float);

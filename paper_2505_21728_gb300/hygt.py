@@ -70,6 +70,12 @@ def _load() -> ctypes.CDLL:
         f.restype = i32
     L.hygt_forward_static.argtypes = [P, P, P, P, i64, P, P]
     L.hygt_forward_static.restype = i32
+    L.hygt_host_pipe_create.argtypes = [ctypes.POINTER(P), P, i64]
+    L.hygt_host_pipe_create.restype = i32
+    L.hygt_host_roundtrip.argtypes = [P, P, P, P, P, i64, ctypes.POINTER(i32)]
+    L.hygt_host_roundtrip.restype = i32
+    L.hygt_host_pipe_destroy.argtypes = [P]
+    L.hygt_host_pipe_destroy.restype = None
     L.hygt_update_theta.argtypes = [P, P, P]
     L.hygt_update_theta.restype = i32
     L.hygt_backward_workspace_bytes.argtypes = [P, i64]
@@ -184,6 +190,22 @@ def hygt_inverse_batch(plan, d_work, d_y, d_x, nblocks, stream, d_status):
 
 def hygt_forward_static(plan, d_x, d_y, d_set, nblocks, stream, d_status):
     return int(_lib.hygt_forward_static(plan, d_x, d_y, d_set, nblocks, stream, d_status))
+
+
+def hygt_host_pipe_create(plan, chunk_blocks):
+    h = ctypes.c_void_p()
+    st = int(_lib.hygt_host_pipe_create(ctypes.byref(h), plan, chunk_blocks))
+    return st, h.value
+
+
+def hygt_host_roundtrip(pipe, h_x, h_set, h_y, h_xr, nblocks):
+    status = ctypes.c_int(0)
+    st = int(_lib.hygt_host_roundtrip(pipe, h_x, h_set, h_y, h_xr, nblocks, ctypes.byref(status)))
+    return st, int(status.value)
+
+
+def hygt_host_pipe_destroy(pipe):
+    _lib.hygt_host_pipe_destroy(pipe)
 
 
 def hygt_update_theta(plan, d_theta, stream):
@@ -404,6 +426,54 @@ class Plan:
             out = torch.empty(y.shape, dtype=torch.float32, device=y.device)
         return self._call(hygt_inverse_f32, "hygt_inverse_f32", y, out, sets, torch.float32,
                           torch.float32, status, stream)
+
+
+class HostPipe:
+    """Round trips of integer batches held in host memory (hygt_host_roundtrip):
+    forward coefficients and inverse reconstruction come back to host
+    tensors.  Host tensors should be pinned (``tensor.pin_memory()``) for the
+    copies to overlap the kernels."""
+
+    def __init__(self, plan, chunk_blocks=1 << 19):
+        st, h = hygt_host_pipe_create(plan.handle, int(chunk_blocks))
+        _check(st, "hygt_host_pipe_create")
+        self.handle = h
+        self.plan = plan
+
+    def roundtrip(self, x, sets=None, y=None, xr=None):
+        """x: int16 CPU tensor [B, N]; sets: int16/uint16 CPU tensor [B] or
+        None.  Returns (y int32 [B, N], xr int16 [B, N], status)."""
+        import torch
+        N = self.plan.N
+        if x.is_cuda or x.dtype != torch.int16 or x.dim() != 2 or x.shape[1] != N or \
+                not x.is_contiguous():
+            raise ValueError("x must be a contiguous int16 CPU tensor [nblocks, %d]" % N)
+        B = x.shape[0]
+        if y is None:
+            y = torch.empty((B, N), dtype=torch.int32, pin_memory=x.is_pinned())
+        if xr is None:
+            xr = torch.empty((B, N), dtype=torch.int16, pin_memory=x.is_pinned())
+        ps = None
+        if sets is not None:
+            if sets.is_cuda or sets.numel() != B or not sets.is_contiguous() or \
+                    sets.dtype not in (torch.int16, torch.uint16):
+                raise ValueError("sets must be a contiguous 16-bit CPU tensor [nblocks]")
+            ps = sets.data_ptr()
+        st, status = hygt_host_roundtrip(self.handle, x.data_ptr(), ps, y.data_ptr(),
+                                         xr.data_ptr(), B)
+        _check(st, "hygt_host_roundtrip")
+        return y, xr, status
+
+    def close(self):
+        if getattr(self, "handle", None):
+            hygt_host_pipe_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:
