@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -124,12 +125,58 @@ hygt_status upload_perms(hygt_plan p, const std::vector<uint8_t>& perm, unsigned
   return upload(reinterpret_cast<void**>(&p->d_perm), perm.data(), perm.size(), p->perm_bytes);
 }
 
+// Region layout of one permutation slot of the batch kernels (see
+// hygt::perm_region_words): word[x] = L q(x) + c(x) for element x, with the
+// L-colouring c found as L successive perfect matchings of the bipartite
+// multigraph joining each element's natural group (x mod E) to its source
+// group (the register index i of the position it is gathered to).  Removing
+// a perfect matching from an L-regular bipartite multigraph leaves an
+// (L-1)-regular one, so every step succeeds.  Host only.
+std::vector<int> perm_region_layout(int N, int E, const uint8_t* perm) {
+  const int L = N / E;
+  std::vector<int> word(N);
+  if (L == 1) {
+    for (int x = 0; x < N; ++x) word[x] = x;
+    return word;
+  }
+  std::vector<int> pos(N);  // pos[x]: position gathering element x
+  for (int e = 0; e < N; ++e) pos[perm[e]] = e;
+  std::vector<int> color(N, -1), match(E);
+  std::vector<char> seen(E);
+  // augmenting path from natural group w over uncoloured elements (Kuhn)
+  std::function<bool(int)> augment = [&](int w) -> bool {
+    for (int l = 0; l < L; ++l) {
+      const int x = l * E + w;
+      if (color[x] >= 0) continue;
+      const int r = pos[x] % E;
+      if (seen[r]) continue;
+      seen[r] = 1;
+      if (match[r] < 0 || augment(match[r] % E)) {
+        match[r] = x;
+        return true;
+      }
+    }
+    return false;
+  };
+  for (int c = 0; c < L; ++c) {
+    std::fill(match.begin(), match.end(), -1);
+    for (int w = 0; w < E; ++w) {
+      std::fill(seen.begin(), seen.end(), 0);
+      if (!augment(w)) return {};
+    }
+    for (int r = 0; r < E; ++r) color[match[r]] = c;
+  }
+  std::vector<int> count(L, 0);
+  for (int x = 0; x < N; ++x) word[x] = L * count[color[x]]++ + color[x];
+  return word;
+}
+
 // Per-set tables of the batch kernels (layout: hygt::SetTableShape).  Register
 // passes store (c, s - c, -(c + s)) per pair in per-lane segments; lane passes
 // store (c, s) for the m side and (c, -s) for the n side of each pair; then
 // the permutation gather sources as byte offsets in a block's permutation
 // region, per lane.
-void build_ktab(int log2n, int rounds, int num_sets, const uint8_t* q, const std::vector<int>& ct,
+bool build_ktab(int log2n, int rounds, int num_sets, const uint8_t* q, const std::vector<int>& ct,
                 const std::vector<int>& st, const std::vector<uint8_t>& perm, unsigned mask,
                 std::vector<int>* out, int* words) {
   const int N = 1 << log2n;
@@ -162,14 +209,22 @@ void build_ktab(int log2n, int rounds, int num_sets, const uint8_t* q, const std
         }
       }
       if (mask) {
-        int* prow = t + sh.perm_offset(r);
-        for (int i = 0; i < N; ++i) {
-          const int src = perm.empty() ? i : perm[((size_t)s * rounds + r) * N + i];
-          prow[(i / E) * sh.perm_seg() + (i % E)] = 4 * hygt::perm_word(src, sh.log2e);
+        std::vector<uint8_t> ident(N);
+        for (int i = 0; i < N; ++i) ident[i] = (uint8_t)i;
+        const uint8_t* pr = perm.empty() ? ident.data() : perm.data() + ((size_t)s * rounds + r) * N;
+        const std::vector<int> word = perm_region_layout(N, E, pr);
+        if (word.empty()) return false;
+        for (int l = 0; l < N / E; ++l) {
+          uint8_t* b = reinterpret_cast<uint8_t*>(t + sh.perm_offset(r) + l * sh.perm_seg());
+          for (int i = 0; i < E; ++i) {
+            b[i] = (uint8_t)word[l * E + i];
+            b[E + i] = (uint8_t)word[pr[l * E + i]];
+          }
         }
       }
     }
   }
+  return true;
 }
 
 hygt_status check_io(hygt_plan plan, const void* in, const void* out, int64_t nblocks) {
@@ -269,7 +324,11 @@ hygt_status hygt_create(hygt_plan* out, int log2n, int rounds, int num_sets,
   if (s == HYGT_OK) s = upload_perms(p, perm, mask);
   if (s == HYGT_OK) {
     std::vector<int> kt;
-    build_ktab(log2n, rounds, num_sets, h_angle_idx, ct, st, perm, mask, &kt, &p->ktab_words);
+    if (!build_ktab(log2n, rounds, num_sets, h_angle_idx, ct, st, perm, mask, &kt,
+                    &p->ktab_words)) {
+      free_plan(p);
+      return HYGT_ERR_ARG;
+    }
     s = upload(reinterpret_cast<void**>(&p->d_ktab), kt.data(), kt.size() * 4, kt.size() * 4);
   }
   if (s != HYGT_OK) {

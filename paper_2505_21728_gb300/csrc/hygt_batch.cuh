@@ -102,8 +102,11 @@ __host__ __device__ inline BatchLayout batch_layout(int num_sets, long long nblo
 //                 n side; 16-byte chunk c = 2 (j / 2) + side holds pairs
 //                 j & ~1 and j | 1 of that side and is stored at chunk
 //                 c + 2 ((c / E) mod 4);
-//   then, if the plan permutes, for each round r: lane l's E gather sources
-//   (byte offsets in a block's permutation region) at l * (E + 4).
+//   then, if the plan permutes, for each round r: lane l's permutation
+//   segment of perm_seg() words at l * perm_seg(): bytes [0, E) the words
+//   of its elements l E + i in a block's permutation region, bytes [E, 2E)
+//   the words of their gather sources perm[l E + i] (layout of the region
+//   below).
 // The segment strides are odd numbers of 16-byte chunks and the chunk skew
 // spreads the (up to 8) lanes of a block over distinct bank groups.
 struct SetTableShape {
@@ -116,7 +119,11 @@ struct SetTableShape {
   }
   __host__ __device__ constexpr int reg_row() const { return lanes() * seg(); }
   __host__ __device__ constexpr int lane_row() const { return 2 * n() + 24; }
-  __host__ __device__ constexpr int perm_seg() const { return e() >= 4 ? e() + 4 : e(); }
+  __host__ __device__ constexpr int perm_seg() const {
+    // 2E bytes in whole 16-byte chunks, an odd number of them when a block
+    // spans several lanes
+    return 4 * (((2 * e() + 15) / 16) | (lanes() > 1 ? 1 : 0));
+  }
   __host__ __device__ constexpr int pass_offset(int p) const {
     return reg_row() * (p < log2e ? p : log2e) + lane_row() * (p < log2e ? 0 : p - log2e);
   }
@@ -133,15 +140,23 @@ struct SetTableShape {
   }
 };
 
-// Words per block in the permutation buffer and the word of element e: one
-// padding word after each lane's E elements, so lane l's element i is at
-// l (E + 1) + i.  With the block slots of a warp task numbered block-major
-// (k (32 / L) + g), the 32 lanes of a warp writing register i of their
-// k-th block land on 32 distinct banks (E + 1 is odd).
+// Words per block region of the permutation buffer: N + L, so that with the
+// regions of a warp task numbered k (32 / L) + g, region g starts at a bank
+// offset of g L (mod 32).  Within a region, element x of the block sits at
+// word L q(x) + c(x), where c is an L-colouring of the elements under which
+// the L elements that one register index i covers -- the lanes' own
+// elements l E + i (written in natural order) as well as their gather
+// sources perm[l E + i] -- always have distinct colours.  Such a colouring
+// exists for every permutation: it is a proper edge colouring with L colours
+// of the L-regular bipartite multigraph joining, for every element, its
+// natural group to its source group (Konig's theorem); the host finds it as
+// L successive perfect matchings.  A warp's 32 lanes (GROUPS lane groups x L
+// lanes) then reach 32 distinct banks in every permutation access.  q(x)
+// numbers the elements of one colour in increasing order, so the words
+// cover 0 .. N-1.
 __host__ __device__ constexpr int perm_region_words(int log2n) {
   return (1 << log2n) + (1 << (log2n - batch_log2e(log2n)));
 }
-__host__ __device__ constexpr int perm_word(int e, int log2e) { return e + (e >> log2e); }
 
 // ---------------------------------------------------------------- transform
 struct BatchParams {
@@ -300,16 +315,29 @@ __device__ __forceinline__ void batch_store(const BatchParams& p, long long b, i
     store_i16_sat<E>(static_cast<int16_t*>(p.out) + b * N + lane * E, v);
 }
 
-// Gather offset i of a lane's permutation row (vector loads when aligned).
+// A lane's permutation segment (see SetTableShape): 2E bytes in registers.
 template <int E>
-__device__ __forceinline__ int perm_at(const int* prow, int i) {
-  if constexpr (E % 4 == 0) {
-    const int4 q = reinterpret_cast<const int4*>(prow)[i / 4];
-    return (i & 3) == 0 ? q.x : (i & 3) == 1 ? q.y : (i & 3) == 2 ? q.z : q.w;
-  } else {
-    return prow[i];
+struct PermBytes {
+  static constexpr int W = (2 * E + 3) / 4;
+  uint32_t w[W < 4 ? W : (W + 3) / 4 * 4];
+  __device__ __forceinline__ void load(const int* seg) {
+    if constexpr (W % 4 == 0) {
+#pragma unroll
+      for (int q = 0; q < W / 4; ++q) {
+        const int4 t = reinterpret_cast<const int4*>(seg)[q];
+        w[4 * q] = t.x; w[4 * q + 1] = t.y; w[4 * q + 2] = t.z; w[4 * q + 3] = t.w;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < W; ++q) w[q] = (uint32_t)seg[q];
+    }
   }
-}
+  // word of this lane's element i in the region / of the element's gather source
+  __device__ __forceinline__ int own(int i) const { return (w[i >> 2] >> (8 * (i & 3))) & 0xFF; }
+  __device__ __forceinline__ int src(int i) const {
+    return (w[(E + i) >> 2] >> (8 * ((E + i) & 3))) & 0xFF;
+  }
+};
 
 // Bucket of a slot: the largest k with starts[k] <= slot (empty buckets share
 // their start with the next one, so the largest is non-empty).
@@ -533,24 +561,21 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
       for (int rr = 0; rr < R; ++rr) {
         const int r = INV ? (R - 1 - rr) : rr;
         const bool has_perm = p.perms && ((p.perm_mask >> r) & 1u);
-        const int* prow = stab + sh.perm_offset(r) + lane * sh.perm_seg();
+        PermBytes<E> pb;
+        if (has_perm) pb.load(stab + sh.perm_offset(r) + lane * sh.perm_seg());
         if (INV && has_perm) {  // undo the gather of slot r: v_prev[perm[e]] = v[e]
 #pragma unroll
           for (int k = 0; k < K; ++k) {
             int32_t* region = pbuf + (k * GROUPS + grp) * RW;
-            char* rb = reinterpret_cast<char*>(region);
 #pragma unroll
-            for (int i = 0; i < E; ++i) {
-              *reinterpret_cast<int32_t*>(rb + perm_at<E>(prow, i)) = v[k][i];
-              if ((i & 3) == 3) asm volatile("" ::: "memory");
-            }
+            for (int i = 0; i < E; ++i) region[pb.src(i)] = v[k][i];
           }
           __syncwarp();
 #pragma unroll
           for (int k = 0; k < K; ++k) {
             const int32_t* region = pbuf + (k * GROUPS + grp) * RW;
 #pragma unroll
-            for (int i = 0; i < E; ++i) v[k][i] = region[perm_word(lane * E + i, M::LOG2E)];
+            for (int i = 0; i < E; ++i) v[k][i] = region[pb.own(i)];
           }
           __syncwarp();
         }
@@ -560,17 +585,14 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
           for (int k = 0; k < K; ++k) {
             int32_t* region = pbuf + (k * GROUPS + grp) * RW;
 #pragma unroll
-            for (int i = 0; i < E; ++i) region[perm_word(lane * E + i, M::LOG2E)] = v[k][i];
+            for (int i = 0; i < E; ++i) region[pb.own(i)] = v[k][i];
           }
           __syncwarp();
 #pragma unroll
           for (int k = 0; k < K; ++k) {
-            const char* rb = reinterpret_cast<const char*>(pbuf + (k * GROUPS + grp) * RW);
+            const int32_t* region = pbuf + (k * GROUPS + grp) * RW;
 #pragma unroll
-            for (int i = 0; i < E; ++i) {
-              v[k][i] = *reinterpret_cast<const int32_t*>(rb + perm_at<E>(prow, i));
-              if ((i & 3) == 3) asm volatile("" ::: "memory");
-            }
+            for (int i = 0; i < E; ++i) v[k][i] = region[pb.src(i)];
           }
           __syncwarp();
         }
