@@ -38,7 +38,8 @@
 
 namespace hygt {
 
-constexpr int kBatchThreads = 512;   // threads per CTA of the batch transform
+// threads per CTA of the batch transform (forward: KIND 0, inverse: KIND 1)
+__host__ __device__ constexpr int batch_threads(int kind) { return kind == 0 ? 384 : 512; }
 constexpr int kBucketThreads = 512;  // threads per CTA of the bucketing kernels
 constexpr int kBucketTile = 8192;    // blocks per CTA tile in the scatter pass
 
@@ -351,9 +352,8 @@ __device__ __forceinline__ int bucket_of_slot(const int* starts, int num_sets, i
 }
 
 // ---------------------------------------------------------------- staging
-// Inverse kernels read int32 coefficients, 32 or 64 contiguous bytes per
-// lane per block; for N = 32 and 64 their input is copied into shared memory
-// with cp.async one
+// For N = 32 and 64 the kernels' input (int16 blocks forward, int32
+// coefficients inverse) is copied into shared memory with cp.async one
 // task ahead (and the block ids two tasks ahead), so the global-memory
 // latency is off the critical path.  Stage layout, per warp: piece j (CH
 // bytes) of lane l of lane group g in block k of the task at
@@ -363,7 +363,7 @@ __device__ __forceinline__ int bucket_of_slot(const int* starts, int num_sets, i
 __host__ __device__ constexpr bool batch_staged(int log2n, int kind) {
   // measured: a gain where a block spans several lanes (N = 32, 64); larger
   // blocks leave no room for the stage next to the permutation buffer
-  return kind == 1 && (log2n == 5 || log2n == 6);
+  return (kind == 0 || kind == 1) && (log2n == 5 || log2n == 6);
 }
 
 template <int LOG2N, int KIND>
@@ -674,7 +674,7 @@ __host__ __device__ inline size_t batch_pbuf_bytes(int threads) {
 }
 
 template <int LOG2N, int KIND>
-__global__ void __launch_bounds__(kBatchThreads, 1) hygt_batch_kernel(BatchParams p) {
+__global__ void __launch_bounds__(batch_threads(KIND), 1) hygt_batch_kernel(BatchParams p) {
   extern __shared__ __align__(16) int32_t bsmem[];
   batch_cta<LOG2N, KIND>(p, blockIdx.x, gridDim.x, bsmem);
 }
