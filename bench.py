@@ -592,7 +592,7 @@ def e2e_leg(plan, x_np, s_np, N, dev, stream, world, steps=5):
     h_s = torch.from_numpy(s_np.view(np.int16)).pin_memory()
     h_y = torch.empty((count, N), dtype=torch.int32).pin_memory()
     h_xr = torch.empty((count, N), dtype=torch.int16).pin_memory()
-    pipe = hygt.HostPipe(plan, 1 << 19)
+    pipe = hygt.HostPipe(plan, 1 << 17)
 
     def step():
         _, _, status = pipe.roundtrip(h_x, h_s, h_y, h_xr)
@@ -610,7 +610,7 @@ def e2e_leg(plan, x_np, s_np, N, dev, stream, world, steps=5):
     return {"value": count * world * steps / (ms / 1000.0), "unit": "blocks/s",
             "h2d_bytes_per_step": count * (2 * N + 2), "d2h_bytes_per_step": count * 6 * N,
             "steps": steps, "api": "hygt_host_roundtrip (HostPipe), pinned host buffers, "
-                                  "chunks of 524,288 blocks on three streams"}
+                                  "chunks of 131,072 blocks on three streams"}
 
 
 def main():

@@ -434,7 +434,7 @@ class HostPipe:
     tensors.  Host tensors should be pinned (``tensor.pin_memory()``) for the
     copies to overlap the kernels."""
 
-    def __init__(self, plan, chunk_blocks=1 << 19):
+    def __init__(self, plan, chunk_blocks=1 << 17):
         st, h = hygt_host_pipe_create(plan.handle, int(chunk_blocks))
         _check(st, "hygt_host_pipe_create")
         self.handle = h
