@@ -76,13 +76,14 @@ void grad_config(int log2n, int num_sets, int rounds, long long nblocks, int* th
 
 template <int LOG2N>
 static cudaError_t launch_sized(GradLaunch& gl, cudaStream_t stream) {
-  auto kern = hygt_grad_kernel<LOG2N>;
-  static std::atomic<int> attr_set{0};
-  if ((int)gl.smem > attr_set.load()) {
+  auto kern = gl.p.cache_tables ? hygt_grad_kernel<LOG2N, true> : hygt_grad_kernel<LOG2N, false>;
+  static std::atomic<int> attr_set[2] = {{0}, {0}};
+  std::atomic<int>& as = attr_set[gl.p.cache_tables ? 1 : 0];
+  if ((int)gl.smem > as.load()) {
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)gl.smem);
     if (err != cudaSuccess) return err;
-    attr_set.store((int)gl.smem);
+    as.store((int)gl.smem);
   }
   kern<<<gl.grid, gl.threads, gl.smem, stream>>>(gl.p);
   return cudaGetLastError();

@@ -34,8 +34,9 @@ struct F32uParams {
   int rounds;
 };
 
-// Shared memory: the set's table (float2 per pair) and permutation bytes,
-// then per warp GROUPS block regions of the permutation buffer.
+// Shared memory: the set's table (padded layout of hygt_grad.cuh) and
+// permutation bytes, then per warp GROUPS block regions of the permutation
+// buffer.
 template <int LOG2N>
 __host__ __device__ inline size_t f32u_table_bytes(int rounds) {
   return grad_table_bytes<LOG2N>(1, rounds);
@@ -48,16 +49,18 @@ __host__ __device__ inline size_t f32u_smem_bytes(int threads, int rounds) {
 
 template <int LOG2N, bool INV, int P>
 __device__ __forceinline__ void f32u_pass(float (&v)[GradMap<LOG2N>::K][GradMap<LOG2N>::E],
-                                          const float2* row, int lane) {
+                                          const unsigned char* rtab, int lane) {
   using M = GradMap<LOG2N>;
+  using T = GradTab<LOG2N, true>;
   constexpr int E = M::E;
   constexpr int K = M::K;
   if constexpr (P < M::LOG2E) {
+    const float2* seg = reinterpret_cast<const float2*>(rtab + T::pass_off(P) + lane * T::SEG);
 #pragma unroll
     for (int jl = 0; jl < E / 2; ++jl) {
       const int im = ((jl >> P) << (P + 1)) | (jl & ((1 << P) - 1));
       const int in = im | (1 << P);
-      const float2 cs = row[lane * (E / 2) + jl];
+      const float2 cs = seg[jl];
       const float s = INV ? -cs.y : cs.y;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
@@ -71,9 +74,11 @@ __device__ __forceinline__ void f32u_pass(float (&v)[GradMap<LOG2N>::K][GradMap<
     constexpr int D = 1 << Q;
     const bool upper = (lane >> Q) & 1;
     const int jbase = ((lane >> (Q + 1)) << P) + ((lane & (D - 1)) << M::LOG2E);
+    const float2* grp =
+        reinterpret_cast<const float2*>(rtab + T::pass_off(P) + (jbase >> M::LOG2E) * T::GRP);
 #pragma unroll
     for (int i = 0; i < E; ++i) {
-      const float2 cs = row[jbase + i];
+      const float2 cs = grp[i];
       // m side: c own + s partner; n side: c own - s partner (s -> -s inverse)
       const float sp = (upper != INV) ? -cs.y : cs.y;
 #pragma unroll
@@ -88,11 +93,10 @@ __device__ __forceinline__ void f32u_pass(float (&v)[GradMap<LOG2N>::K][GradMap<
 
 template <int LOG2N, bool INV, int J>
 __device__ __forceinline__ void f32u_round(float (&v)[GradMap<LOG2N>::K][GradMap<LOG2N>::E],
-                                           const float2* rtab, int lane) {
-  constexpr int N = 1 << LOG2N;
+                                           const unsigned char* rtab, int lane) {
   if constexpr (J < LOG2N) {
     constexpr int P = INV ? LOG2N - 1 - J : J;
-    f32u_pass<LOG2N, INV, P>(v, rtab + P * (N / 2), lane);
+    f32u_pass<LOG2N, INV, P>(v, rtab, lane);
     f32u_round<LOG2N, INV, J + 1>(v, rtab, lane);
   }
 }
@@ -109,18 +113,11 @@ __global__ void __launch_bounds__(kF32uThreads, 1) hygt_f32u_kernel(F32uParams p
   constexpr int RW = M::RW;
   extern __shared__ __align__(16) unsigned char fsm[];
 
+  using T = GradTab<LOG2N, true>;
   const int R = p.rounds;
-  const int rowlen = LOG2N * (N / 2);
-  {
-    const size_t tb = (size_t)R * rowlen * 8;
-    const int4* src = reinterpret_cast<const int4*>(p.tab);
-    int4* dst = reinterpret_cast<int4*>(fsm);
-    for (size_t i = threadIdx.x; i < tb / 16; i += blockDim.x) dst[i] = __ldg(src + i);
-    if (p.perm)
-      for (size_t i = threadIdx.x; i < (size_t)R * N; i += blockDim.x) fsm[tb + i] = __ldg(p.perm + i);
-  }
-  const float2* tab = reinterpret_cast<const float2*>(fsm);
-  const uint8_t* perm = fsm + (size_t)R * rowlen * 8;
+  grad_copy_tables<LOG2N>(p.tab, R, p.perm, R * N, fsm);
+  const unsigned char* tab = fsm;
+  const uint8_t* perm = fsm + (size_t)R * T::ROUND;
   const int warps = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5;
   const int lane32 = threadIdx.x & 31;
@@ -164,7 +161,7 @@ __global__ void __launch_bounds__(kF32uThreads, 1) hygt_f32u_kernel(F32uParams p
           __syncwarp();
         }
       }
-      f32u_round<LOG2N, INV, 0>(v, tab + (size_t)r * rowlen, lane);
+      f32u_round<LOG2N, INV, 0>(v, tab + (size_t)r * T::ROUND, lane);
       if (!INV && has_perm) {  // gather: v'[e] = v[perm[e]]
 #pragma unroll
         for (int k = 0; k < K; ++k) {

@@ -71,7 +71,32 @@ struct GradMap {
   static constexpr int RW = N + L;  // words per block region of the permutation buffer
 };
 
-// Shared memory (bytes): the tables of all sets when cached (float2 per pair,
+// (cos, sin) tables as the lane groups read them.  Register pass: lane l's
+// E/2 pairs (jl = 0 .. E/2-1, pair j = l E/2 + jl) contiguous in a segment of
+// SEG bytes; cross-lane pass: the E pairs jbase .. jbase + E - 1 that a lane
+// pair reads, in a group of GRP bytes.  PADDED (the shared-memory copy)
+// pads both by 16 bytes, which makes the distinct segments (groups) that the
+// lanes of a group read at once start in distinct banks; unpadded, it is the
+// plan's global layout [S][R][k][N/2] float2.
+template <int LOG2N, bool PADDED>
+struct GradTab {
+  using M = GradMap<LOG2N>;
+  static constexpr int SEG = 4 * M::E + (PADDED ? 16 : 0);
+  static constexpr int GRP = 8 * M::E + (PADDED ? 16 : 0);
+  static constexpr int REG_ROW = M::L * SEG;
+  static constexpr int LANE_ROW = (M::N / 2 / M::E) * GRP;
+  __host__ __device__ static constexpr int pass_off(int p) {
+    return p < M::LOG2E ? p * REG_ROW : M::LOG2E * REG_ROW + (p - M::LOG2E) * LANE_ROW;
+  }
+  static constexpr int ROUND = M::LOG2E * REG_ROW + (LOG2N - M::LOG2E) * LANE_ROW;
+  // byte offset of pair j of pass p within a round
+  __host__ __device__ static constexpr int pair_off(int p, int j) {
+    return p < M::LOG2E ? pass_off(p) + (j / (M::E / 2)) * SEG + (j % (M::E / 2)) * 8
+                        : pass_off(p) + (j / M::E) * GRP + (j % M::E) * 8;
+  }
+};
+
+// Shared memory (bytes): the tables of all sets when cached (padded layout,
 // then the permutation bytes, 16-byte padded), then per warp GROUPS
 // accumulator rows of grad_acc_stride(angles) floats and the permutation
 // buffer (y and g regions of GROUPS blocks).  The row stride is odd, so the
@@ -81,9 +106,28 @@ __host__ __device__ inline int grad_acc_stride(int angles) { return ((angles + 3
 template <int LOG2N>
 __host__ __device__ inline size_t grad_table_bytes(int num_sets, int rounds) {
   using M = GradMap<LOG2N>;
-  const size_t tab = (size_t)num_sets * rounds * LOG2N * (M::N / 2) * 8;
+  const size_t tab = (size_t)num_sets * rounds * GradTab<LOG2N, true>::ROUND;
   const size_t perm = ((size_t)num_sets * rounds * M::N + 15) & ~(size_t)15;
   return tab + perm;
+}
+
+// Copy the plan's (cos, sin) tables of `rows` rounds (all passes) into the
+// padded shared-memory layout, then `pbytes` permutation bytes after them.
+template <int LOG2N>
+__device__ __forceinline__ void grad_copy_tables(const float2* tab, int rows, const uint8_t* perm,
+                                                 int pbytes, unsigned char* dst) {
+  using M = GradMap<LOG2N>;
+  using T = GradTab<LOG2N, true>;
+  constexpr int PAIRS = LOG2N * (M::N / 2);  // pairs per round
+  for (int i = threadIdx.x; i < rows * PAIRS; i += blockDim.x) {
+    const int r = i / PAIRS, q = i % PAIRS;
+    const int pp = q / (M::N / 2), j = q % (M::N / 2);
+    *reinterpret_cast<float2*>(dst + (size_t)r * T::ROUND + T::pair_off(pp, j)) = __ldg(tab + i);
+  }
+  if (perm) {
+    uint8_t* pd = dst + (size_t)rows * T::ROUND;
+    for (int i = threadIdx.x; i < pbytes; i += blockDim.x) pd[i] = __ldg(perm + i);
+  }
 }
 
 template <int LOG2N>
@@ -98,20 +142,22 @@ __device__ __forceinline__ int grad_word(int e) {
   return e + (e >> GradMap<LOG2N>::LOG2E);
 }
 
-template <int LOG2N, int P>
+template <int LOG2N, bool PADDED, int P>
 __device__ __forceinline__ void grad_pass(float (&v)[GradMap<LOG2N>::K][GradMap<LOG2N>::E],
                                           float (&g)[GradMap<LOG2N>::K][GradMap<LOG2N>::E],
-                                          const float2* row, float* acc, int lane) {
+                                          const unsigned char* rtab, float* acc, int lane) {
   using M = GradMap<LOG2N>;
+  using T = GradTab<LOG2N, PADDED>;
   constexpr int E = M::E;
   constexpr int K = M::K;
   if constexpr (P < M::LOG2E) {
+    const float2* seg = reinterpret_cast<const float2*>(rtab + T::pass_off(P) + lane * T::SEG);
 #pragma unroll
     for (int jl = 0; jl < E / 2; ++jl) {
       const int im = ((jl >> P) << (P + 1)) | (jl & ((1 << P) - 1));
       const int in = im | (1 << P);
       const int j = lane * (E / 2) + jl;
-      const float2 cs = row[j];
+      const float2 cs = seg[jl];
       float sum = 0.f;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
@@ -130,9 +176,11 @@ __device__ __forceinline__ void grad_pass(float (&v)[GradMap<LOG2N>::K][GradMap<
     constexpr int D = 1 << Q;
     const bool upper = (lane >> Q) & 1;
     const int jbase = ((lane >> (Q + 1)) << P) + ((lane & (D - 1)) << M::LOG2E);
+    const float2* grp =
+        reinterpret_cast<const float2*>(rtab + T::pass_off(P) + (jbase >> M::LOG2E) * T::GRP);
 #pragma unroll
     for (int i = 0; i < E; ++i) {
-      const float2 cs = row[jbase + i];
+      const float2 cs = grp[i];
       const float sp = upper ? cs.y : -cs.y;
       float sum = 0.f;
 #pragma unroll
@@ -150,19 +198,19 @@ __device__ __forceinline__ void grad_pass(float (&v)[GradMap<LOG2N>::K][GradMap<
   }
 }
 
-template <int LOG2N, int J>
+template <int LOG2N, bool PADDED, int J>
 __device__ __forceinline__ void grad_round(float (&v)[GradMap<LOG2N>::K][GradMap<LOG2N>::E],
                                            float (&g)[GradMap<LOG2N>::K][GradMap<LOG2N>::E],
-                                           const float2* rtab, float* racc, int lane) {
+                                           const unsigned char* rtab, float* racc, int lane) {
   constexpr int N = 1 << LOG2N;
   if constexpr (J < LOG2N) {
     constexpr int P = LOG2N - 1 - J;  // passes in reverse order
-    grad_pass<LOG2N, P>(v, g, rtab + P * (N / 2), racc + P * (N / 2), lane);
-    grad_round<LOG2N, J + 1>(v, g, rtab, racc, lane);
+    grad_pass<LOG2N, PADDED, P>(v, g, rtab, racc + P * (N / 2), lane);
+    grad_round<LOG2N, PADDED, J + 1>(v, g, rtab, racc, lane);
   }
 }
 
-template <int LOG2N>
+template <int LOG2N, bool CACHED>
 __global__ void __launch_bounds__(kGradThreads, 1) hygt_grad_kernel(GradParams p) {
   using M = GradMap<LOG2N>;
   constexpr int N = M::N;
@@ -177,20 +225,14 @@ __global__ void __launch_bounds__(kGradThreads, 1) hygt_grad_kernel(GradParams p
   const int S = p.num_sets;
   const int R = p.rounds;
   const int rowlen = LOG2N * (N / 2);  // angles per round
-  const float2* tab = p.tab;
+  using T = GradTab<LOG2N, CACHED>;
+  const unsigned char* tab = reinterpret_cast<const unsigned char*>(p.tab);
   const uint8_t* perm = p.perm;
   size_t off = 0;
-  if (p.cache_tables) {
-    const size_t tb = (size_t)S * R * rowlen * 8;
-    const int4* src = reinterpret_cast<const int4*>(p.tab);
-    int4* dst = reinterpret_cast<int4*>(gsm);
-    for (size_t i = threadIdx.x; i < tb / 16; i += blockDim.x) dst[i] = __ldg(src + i);
-    tab = reinterpret_cast<const float2*>(gsm);
-    if (p.perm) {
-      uint8_t* pd = gsm + tb;
-      for (size_t i = threadIdx.x; i < (size_t)S * R * N; i += blockDim.x) pd[i] = __ldg(p.perm + i);
-      perm = pd;
-    }
+  if constexpr (CACHED) {
+    grad_copy_tables<LOG2N>(p.tab, S * R, p.perm, S * R * N, gsm);
+    tab = gsm;
+    if (p.perm) perm = gsm + (size_t)S * R * T::ROUND;
     off = grad_table_bytes<LOG2N>(S, R);
   }
   const int warps = blockDim.x >> 5;
@@ -268,8 +310,8 @@ __global__ void __launch_bounds__(kGradThreads, 1) hygt_grad_kernel(GradParams p
             __syncwarp();
           }
         }
-        const size_t o = ((size_t)bucket * R + r) * rowlen;
-        grad_round<LOG2N, 0>(v, g, tab + o, acc + o, lane);
+        const size_t o = (size_t)bucket * R + r;
+        grad_round<LOG2N, CACHED, 0>(v, g, tab + o * T::ROUND, acc + o * rowlen, lane);
       }
     } else if (bucket == S + 1) {  // bad set index: zero gradient, status
 #pragma unroll
