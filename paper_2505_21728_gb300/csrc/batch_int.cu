@@ -163,7 +163,7 @@ static cudaError_t launch_batch_sized(BatchParams p, cudaStream_t stream) {
   if (err != cudaSuccess) return err;
   const DeviceInfo info = device_info(dev);
   constexpr int G = batch_task_group(LOG2N, KIND == 1);
-  const size_t pbuf = batch_pbuf_bytes<LOG2N, KIND>(batch_threads(KIND));
+  const size_t pbuf = batch_pbuf_bytes<LOG2N, KIND>(batch_threads(LOG2N, KIND));
   const size_t set_bytes = (size_t)p.set_words * 4;
   const int fit =
       batch_cached_sets((size_t)info.max_smem_optin, pbuf, set_bytes, p.num_sets, info.sms);
@@ -176,14 +176,14 @@ static cudaError_t launch_batch_sized(BatchParams p, cudaStream_t stream) {
     attr_set.store((int)smem);
   }
   int occ = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, batch_threads(KIND), smem);
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, batch_threads(LOG2N, KIND), smem);
   if (err != cudaSuccess) return err;
   if (occ < 1) occ = 1;
-  const long long per_cta = (long long)(batch_threads(KIND) / 32) * G;
+  const long long per_cta = (long long)(batch_threads(LOG2N, KIND) / 32) * G;
   long long need = (p.nblocks + per_cta - 1) / per_cta + 1;
   long long grid = (long long)occ * info.sms;
   if (need < grid) grid = need;
-  kern<<<(unsigned)grid, batch_threads(KIND), smem, stream>>>(p);
+  kern<<<(unsigned)grid, batch_threads(LOG2N, KIND), smem, stream>>>(p);
   return cudaGetLastError();
 }
 

@@ -38,8 +38,13 @@
 
 namespace hygt {
 
-// threads per CTA of the batch transform (forward: KIND 0, inverse: KIND 1)
-__host__ __device__ constexpr int batch_threads(int kind) { return kind == 0 ? 384 : 512; }
+// Threads per CTA of the batch transform for block size 2^log2n (forward:
+// KIND 0, inverse: KIND 1), measured: where a block spans several lanes the
+// forward (four blocks per lane group) wants the registers of 384 threads and
+// the inverse (two) the warps of 640; whole-block-per-lane sizes run 512.
+__host__ __device__ constexpr int batch_threads(int log2n, int kind) {
+  return log2n <= 4 ? 512 : kind == 0 ? 384 : (log2n <= 6 ? 640 : 512);
+}
 constexpr int kBucketThreads = 512;  // threads per CTA of the bucketing kernels
 constexpr int kBucketTile = 8192;    // blocks per CTA tile in the scatter pass
 
@@ -674,7 +679,7 @@ __host__ __device__ inline size_t batch_pbuf_bytes(int threads) {
 }
 
 template <int LOG2N, int KIND>
-__global__ void __launch_bounds__(batch_threads(KIND), 1) hygt_batch_kernel(BatchParams p) {
+__global__ void __launch_bounds__(batch_threads(LOG2N, KIND), 1) hygt_batch_kernel(BatchParams p) {
   extern __shared__ __align__(16) int32_t bsmem[];
   batch_cta<LOG2N, KIND>(p, blockIdx.x, gridDim.x, bsmem);
 }

@@ -18,7 +18,7 @@
 namespace hygt {
 
 template <int KIND>
-__global__ void __launch_bounds__(batch_threads(KIND), 1) hygt_mixed_kernel(MixedParams mp) {
+__global__ void __launch_bounds__(batch_threads(6, KIND), 1) hygt_mixed_kernel(MixedParams mp) {
   extern __shared__ __align__(16) int32_t msmem[];
   if (mp.sequential) {
     // every CTA works through the classes in turn; shared memory is reused
@@ -45,9 +45,9 @@ __global__ void __launch_bounds__(batch_threads(KIND), 1) hygt_mixed_kernel(Mixe
 template <int KIND>
 static size_t pbuf_for(int log2n) {
   switch (log2n) {
-    case 4: return batch_pbuf_bytes<4, KIND>(batch_threads(KIND));
-    case 6: return batch_pbuf_bytes<6, KIND>(batch_threads(KIND));
-    case 8: return batch_pbuf_bytes<8, KIND>(batch_threads(KIND));
+    case 4: return batch_pbuf_bytes<4, KIND>(batch_threads(6, KIND));
+    case 6: return batch_pbuf_bytes<6, KIND>(batch_threads(6, KIND));
+    case 8: return batch_pbuf_bytes<8, KIND>(batch_threads(6, KIND));
     default: return 0;
   }
 }
@@ -85,7 +85,7 @@ static cudaError_t launch_mixed_kind(MixedParams mp, cudaStream_t stream) {
   }
   const int grid = mp.cta_begin[kMaxMixedClasses];
   if (grid < 1) return cudaSuccess;
-  kern<<<grid, batch_threads(KIND), smem, stream>>>(mp);
+  kern<<<grid, batch_threads(6, KIND), smem, stream>>>(mp);
   return cudaGetLastError();
 }
 
