@@ -616,7 +616,7 @@ def direct_path_ms(plan, d_x, d_s, d_y, d_xr, stream, steps=5):
     return {"fwd_ms": statistics.mean(fw), "inv_ms": statistics.mean(iv)}
 
 
-def e2e_leg(plan, x_np, s_np, N, dev, stream, world, steps=5):
+def e2e_leg(plan, x_np, s_np, N, dev, stream, world, steps=10):
     """Same metric through the public API with host buffers: every step is
     one hygt_host_roundtrip call (HostPipe.roundtrip) on pinned host tensors
     -- the blocks and set indices go host->device, are bucketed, transformed
