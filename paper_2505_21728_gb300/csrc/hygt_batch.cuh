@@ -55,12 +55,14 @@ constexpr int kBucketTile = 8192;    // blocks per CTA tile in the scatter pass
 // of both task sizes, so one schedule serves the forward and the inverse.
 // For 8x8 blocks E = 8 (L = 8 lanes, three cross-lane passes) with K = 8
 // forward and 4 inverse: fewer multiplier bytes per block than E = 16 with
-// K = 4 / 2 (measured 4-9% faster), for the same 64 value registers.
+// K = 4 / 2 (measured 4-9% faster), for the same 64 value registers; for
+// 16x16 blocks likewise E = 16 with K = 4 / 2 rather than E = 32 with K = 2
+// (forward 16% faster).
 __host__ __device__ constexpr int batch_log2e(int log2n) {
-  return log2n <= 4 ? log2n : log2n == 5 ? 4 : log2n == 6 ? 3 : 5;
+  return log2n <= 4 ? log2n : log2n == 5 ? 4 : log2n == 6 ? 3 : log2n == 8 ? 4 : 5;
 }
 __host__ __device__ constexpr int batch_k(int log2n, bool inv) {
-  return log2n <= 2 ? 1 : log2n == 6 ? (inv ? 4 : 8) : log2n == 5 ? (inv ? 2 : 4) : 2;
+  return log2n <= 2 ? 1 : log2n == 6 ? (inv ? 4 : 8) : log2n == 5 || log2n == 8 ? (inv ? 2 : 4) : 2;
 }
 __host__ __device__ constexpr int batch_task_group(int log2n, bool inv) {
   return (32 >> (log2n - batch_log2e(log2n))) * batch_k(log2n, inv);
@@ -110,7 +112,7 @@ __host__ __device__ inline BatchLayout batch_layout(int num_sets, long long nblo
 //     p >= log2e: for each pair j, (c, s) for its m side and (c, -s) for its
 //                 n side; 16-byte chunk c = 2 (j / 2) + side holds pairs
 //                 j & ~1 and j | 1 of that side and is stored at chunk
-//                 c + 2 ((c / E) mod 4);
+//                 c + 2 (c / E);
 //   then, if the plan permutes, for each round r: lane l's permutation
 //   segment of perm_seg() words at l * perm_seg(): bytes [0, E) the words
 //   of its elements l E + i in a block's permutation region, bytes [E, 2E)
@@ -127,7 +129,7 @@ struct SetTableShape {
     return e() >= 8 ? ((3 * e() / 2 + 3) / 4 | 1) * 4 : 3 * e() / 2;
   }
   __host__ __device__ constexpr int reg_row() const { return lanes() * seg(); }
-  __host__ __device__ constexpr int lane_row() const { return 2 * n() + 24; }
+  __host__ __device__ constexpr int lane_row() const { return 2 * n() + 4 * n() / e() - 8; }
   __host__ __device__ constexpr int perm_seg() const {
     // 2E bytes in whole 16-byte chunks, an odd number of them when a block
     // spans several lanes
@@ -145,7 +147,7 @@ struct SetTableShape {
   }
   // word of entry (c, s') of pair j on `side` in a lane-pass row
   __host__ __device__ constexpr int lane_word(int j, int side) const {
-    return 4 * ((2 * (j / 2) + side) + 2 * (((2 * (j / 2) + side) / e()) & 3)) + 2 * (j & 1);
+    return 4 * ((2 * (j / 2) + side) + 2 * ((2 * (j / 2) + side) / e())) + 2 * (j & 1);
   }
 };
 
@@ -259,9 +261,9 @@ struct BatchMath {
     const int jbase = ((lane >> (Q + 1)) << P) + ((lane & (D - 1)) << LOG2E);
     // forward: m side (c, s), n side (c, -s); inverse: the opposite
     const int side = upper ^ (INV ? 1 : 0);
-    // chunk c = jbase + i + side (i even) is stored at c + 2 ((c / E) mod 4);
+    // chunk c = jbase + i + side (i even) is stored at c + 2 (c / E);
     // c / E = jbase / E for every i of this lane
-    const int skew = 2 * ((jbase >> LOG2E) & 3);
+    const int skew = 2 * (jbase >> LOG2E);
     const int4* base = reinterpret_cast<const int4*>(row) + jbase + side + skew;
 #pragma unroll
     for (int i = 0; i < E; i += 2) {
