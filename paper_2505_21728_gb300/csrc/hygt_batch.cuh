@@ -41,9 +41,9 @@ namespace hygt {
 // Threads per CTA of the batch transform for block size 2^log2n (forward:
 // KIND 0, inverse: KIND 1), measured: where a block spans several lanes the
 // forward (more blocks per lane group) wants the registers of 384 threads;
-// the inverse on 32-value blocks the warps of 640.
+// the inverse on 32-value blocks the warps of 640; otherwise 512.
 __host__ __device__ constexpr int batch_threads(int log2n, int kind) {
-  return log2n <= 4 ? 512 : kind == 0 ? 384 : (log2n == 5 ? 640 : 512);
+  return log2n <= 3 ? 512 : kind == 0 ? 384 : (log2n == 5 ? 640 : 512);
 }
 constexpr int kBucketThreads = 512;  // threads per CTA of the bucketing kernels
 constexpr int kBucketTile = 8192;    // blocks per CTA tile in the scatter pass
@@ -57,12 +57,25 @@ constexpr int kBucketTile = 8192;    // blocks per CTA tile in the scatter pass
 // forward and 4 inverse: fewer multiplier bytes per block than E = 16 with
 // K = 4 / 2 (measured 4-9% faster), for the same 64 value registers; for
 // 16x16 blocks likewise E = 16 with K = 4 / 2 rather than E = 32 with K = 2
-// (forward 16% faster).
+// (forward 16% faster); for 4x4 blocks E = 8 (two lanes) with K = 8 / 4
+// rather than one lane per block (forward 5% faster).
 __host__ __device__ constexpr int batch_log2e(int log2n) {
-  return log2n <= 4 ? log2n : log2n == 5 ? 4 : log2n == 6 ? 3 : log2n == 8 ? 4 : 5;
+  switch (log2n) {
+    case 4: return 3;   // 4x4: 8 values per lane, 2 lanes
+    case 5: return 4;
+    case 6: return 3;   // 8x8: 8 values per lane, 8 lanes
+    case 7: return 5;
+    case 8: return 4;   // 16x16: 16 values per lane, 16 lanes
+    default: return log2n;  // N <= 8: one lane per block
+  }
 }
 __host__ __device__ constexpr int batch_k(int log2n, bool inv) {
-  return log2n <= 2 ? 1 : log2n == 6 ? (inv ? 4 : 8) : log2n == 5 || log2n == 8 ? (inv ? 2 : 4) : 2;
+  switch (log2n) {
+    case 1: case 2: return 1;
+    case 4: case 6: return inv ? 4 : 8;
+    case 5: case 8: return inv ? 2 : 4;
+    default: return 2;
+  }
 }
 __host__ __device__ constexpr int batch_task_group(int log2n, bool inv) {
   return (32 >> (log2n - batch_log2e(log2n))) * batch_k(log2n, inv);
