@@ -223,8 +223,9 @@ hygt_status hygt_backward_f32(hygt_plan plan, const float *d_y, const float *d_g
  *        async on stream, with schedules already built (hygt_batch_build).
  *   hygt_mixed_graph_create  captures one whole step -- the schedules of
  *        all classes, the mixed forward, the mixed inverse -- into a CUDA
- *        graph (on a private stream; pointers and sizes are fixed at
- *        capture).  hygt_graph_launch replays it on `stream`;
+ *        graph (on private streams: the schedules are built on parallel
+ *        branches that join before the forward; pointers and sizes are
+ *        fixed at capture).  hygt_graph_launch replays it on `stream`;
  *        hygt_graph_destroy frees it.
  *   hygt_mixed_ctas  CTAs of one mixed launch on the current device.
  */

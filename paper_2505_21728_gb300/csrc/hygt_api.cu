@@ -593,6 +593,48 @@ struct hygt_graph_s {
   cudaGraphExec_t exec = nullptr;
 };
 
+// Streams and events of a capture with one branch per class.
+struct GraphBranches {
+  cudaStream_t stream[hygt::kMaxMixedClasses] = {};
+  cudaEvent_t join[hygt::kMaxMixedClasses] = {};
+  cudaEvent_t fork = nullptr;
+  ~GraphBranches() {
+    for (int k = 0; k < hygt::kMaxMixedClasses; ++k) {
+      if (join[k]) cudaEventDestroy(join[k]);
+      if (stream[k]) cudaStreamDestroy(stream[k]);
+    }
+    if (fork) cudaEventDestroy(fork);
+  }
+};
+
+// The classes' schedules share no data: each is built on a branch of its own
+// that forks from and joins `cs`, so the small launches of one schedule (the
+// one-CTA scan, the small classes' count and scatter) run beside those of
+// the others.  (Branching the transform launches as well was measured slower:
+// persistent launches that start on a few SMs at a time finish late.)
+static cudaError_t capture_schedules(const hygt_mixed_class* classes, int nclasses,
+                                     cudaStream_t cs, GraphBranches& br) {
+  cudaError_t e = cudaEventCreateWithFlags(&br.fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(br.fork, cs);
+  int nb = 0;
+  for (int c = 0; c < nclasses && e == cudaSuccess; ++c) {
+    const hygt_mixed_class& k = classes[c];
+    if (k.nblocks <= 0) continue;
+    e = cudaStreamCreateWithFlags(&br.stream[nb], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&br.join[nb], cudaEventDisableTiming);
+    if (e != cudaSuccess) break;
+    cudaStream_t s = br.stream[nb];
+    e = cudaStreamWaitEvent(s, br.fork, 0);
+    if (e == cudaSuccess)
+      e = hygt::batch_build(k.d_set, k.nblocks, k.plan->num_sets,
+                            hygt::batch_group(k.plan->log2n), k.d_work, s);
+    if (e == cudaSuccess) e = cudaEventRecord(br.join[nb], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, br.join[nb], 0);
+    ++nb;
+  }
+  return e;
+}
+
 hygt_status hygt_mixed_graph_create(hygt_graph* out, const hygt_mixed_class* classes, int nclasses,
                                     int* d_status) {
   if (!out) return HYGT_ERR_ARG;
@@ -609,13 +651,9 @@ hygt_status hygt_mixed_graph_create(hygt_graph* out, const hygt_mixed_class* cla
     cudaStreamDestroy(cs);
     return HYGT_ERR_OOM;
   }
+  GraphBranches br;
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-  for (int c = 0; c < nclasses && e == cudaSuccess; ++c) {
-    const hygt_mixed_class& k = classes[c];
-    if (k.nblocks > 0)
-      e = hygt::batch_build(k.d_set, k.nblocks, k.plan->num_sets, hygt::batch_group(k.plan->log2n),
-                            k.d_work, cs);
-  }
+  if (e == cudaSuccess) e = capture_schedules(classes, nclasses, cs, br);
   if (e == cudaSuccess) e = mixed_launch(fwd, mode, false, cs);
   if (e == cudaSuccess) e = mixed_launch(inv, mode, true, cs);
   cudaGraph_t graph = nullptr;
