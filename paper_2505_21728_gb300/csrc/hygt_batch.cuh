@@ -363,6 +363,54 @@ struct PermBytes {
   }
 };
 
+// Blocks of a lane group per pass through the permutation buffer: the
+// buffer holds GROUPS x batch_perm_k block regions per warp, and a lane
+// group's K blocks go through it in K / batch_perm_k passes.  Measured: one
+// pass is fastest where the kernel's shared memory leaves enough L1 (fewer
+// passes, more independent loads in flight); the 16x16 inverse gains 1-3%
+// from one block per pass (a 16x16 region is 1 KB, so the buffer shrinks by
+// 34 KB per CTA), while two passes cost 4x4 blocks 8-10%.
+__host__ __device__ constexpr int batch_perm_k(int log2n, int kind) {
+  return (log2n == 8 && kind == 1) ? 1 : batch_k(log2n, kind == 1);
+}
+__host__ __device__ constexpr int perm_buf_words(int log2n, int kind) {
+  return (32 >> (log2n - batch_log2e(log2n))) * batch_perm_k(log2n, kind) *
+         perm_region_words(log2n);
+}
+
+// The permutation slot of one round for the K blocks of this lane group
+// (regions of the warp's buffer `pbuf`): forward, the gather
+// v'[e] = v[perm[e]]; inverse, its undoing v'[perm[e]] = v[e].
+template <int LOG2N, int KIND>
+__device__ __forceinline__ void perm_slot(
+    int32_t (&v)[BatchMath<LOG2N, KIND == 1>::K][BatchMath<LOG2N, KIND == 1>::E],
+    const PermBytes<BatchMath<LOG2N, KIND == 1>::E>& pb, int32_t* pbuf, int grp) {
+  using M = BatchMath<LOG2N, KIND == 1>;
+  constexpr int E = M::E;
+  constexpr int K = M::K;
+  constexpr int GROUPS = 32 / M::L;
+  constexpr int RW = perm_region_words(LOG2N);
+  constexpr int KP = batch_perm_k(LOG2N, KIND);
+  static_assert(K % KP == 0, "permutation passes must cover the lane group's blocks");
+#pragma unroll
+  for (int k0 = 0; k0 < K; k0 += KP) {
+#pragma unroll
+    for (int kk = 0; kk < KP; ++kk) {
+      int32_t* region = pbuf + (kk * GROUPS + grp) * RW;
+#pragma unroll
+      for (int i = 0; i < E; ++i) region[KIND == 1 ? pb.src(i) : pb.own(i)] = v[k0 + kk][i];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int kk = 0; kk < KP; ++kk) {
+      const int32_t* region = pbuf + (kk * GROUPS + grp) * RW;
+#pragma unroll
+      for (int i = 0; i < E; ++i) v[k0 + kk][i] = region[KIND == 1 ? pb.own(i) : pb.src(i)];
+    }
+    __syncwarp();
+  }
+}
+
 // Bucket of a slot: the largest k with starts[k] <= slot (empty buckets share
 // their start with the next one, so the largest is non-empty).
 __device__ __forceinline__ int bucket_of_slot(const int* starts, int num_sets, int slot) {
@@ -412,7 +460,7 @@ struct BatchStage {
 // stage and the block ids.
 template <int LOG2N, int KIND>
 __host__ __device__ constexpr int batch_warp_bytes() {
-  return batch_task_group(LOG2N, KIND == 1) * perm_region_words(LOG2N) * 4 +
+  return perm_buf_words(LOG2N, KIND) * 4 +
          (batch_staged(LOG2N, KIND)
               ? BatchStage<LOG2N, KIND>::BYTES + BatchStage<LOG2N, KIND>::IDS_BYTES
               : 0);
@@ -527,7 +575,7 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
   const int rw = sh.round_words();
 
   constexpr bool STAGED = batch_staged(LOG2N, KIND);
-  char* stage = reinterpret_cast<char*>(pbuf + G * RW);
+  char* stage = reinterpret_cast<char*>(pbuf + perm_buf_words(LOG2N, KIND));
   int* ids = reinterpret_cast<int*>(stage + BatchStage<LOG2N, KIND>::BYTES);  // [2][G]
   if constexpr (STAGED) {
     if (t0 >= t1) return;
@@ -586,39 +634,9 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
         const bool has_perm = p.perms && ((p.perm_mask >> r) & 1u);
         PermBytes<E> pb;
         if (has_perm) pb.load(stab + sh.perm_offset(r) + lane * sh.perm_seg());
-        if (INV && has_perm) {  // undo the gather of slot r: v_prev[perm[e]] = v[e]
-#pragma unroll
-          for (int k = 0; k < K; ++k) {
-            int32_t* region = pbuf + (k * GROUPS + grp) * RW;
-#pragma unroll
-            for (int i = 0; i < E; ++i) region[pb.src(i)] = v[k][i];
-          }
-          __syncwarp();
-#pragma unroll
-          for (int k = 0; k < K; ++k) {
-            const int32_t* region = pbuf + (k * GROUPS + grp) * RW;
-#pragma unroll
-            for (int i = 0; i < E; ++i) v[k][i] = region[pb.own(i)];
-          }
-          __syncwarp();
-        }
+        if (INV && has_perm) perm_slot<LOG2N, KIND>(v, pb, pbuf, grp);  // undo slot r's gather
         M::template round<0>(v, stab + r * rw, lane, half, f);
-        if (!INV && has_perm) {  // gather: v'[e] = v[perm[e]]
-#pragma unroll
-          for (int k = 0; k < K; ++k) {
-            int32_t* region = pbuf + (k * GROUPS + grp) * RW;
-#pragma unroll
-            for (int i = 0; i < E; ++i) region[pb.own(i)] = v[k][i];
-          }
-          __syncwarp();
-#pragma unroll
-          for (int k = 0; k < K; ++k) {
-            const int32_t* region = pbuf + (k * GROUPS + grp) * RW;
-#pragma unroll
-            for (int i = 0; i < E; ++i) v[k][i] = region[pb.src(i)];
-          }
-          __syncwarp();
-        }
+        if (!INV && has_perm) perm_slot<LOG2N, KIND>(v, pb, pbuf, grp);  // gather of slot r
       }
     } else if (bucket == S + 1) {  // bad set index: zeros, status
 #pragma unroll

@@ -44,12 +44,13 @@ def test_batch_parity(gpu, orc, log2n, rounds, perm_kind):
     assert np.array_equal(xr, xe)
 
 
-@pytest.mark.parametrize("B", [1, 31, 32, 33, 1000])
-def test_batch_ragged_and_bad_sets(gpu, orc, B):
-    log2n, rounds, S = 6, 2, 105
+@pytest.mark.parametrize("log2n", [4, 6])
+@pytest.mark.parametrize("B", [1, 31, 32, 33, 1000, 3 * 4096 + 77])
+def test_batch_ragged_and_bad_sets(gpu, orc, log2n, B):
+    rounds, S, N = 2, 105, 1 << log2n
     q = inputs.angle_indices(S, rounds, log2n, seed=2)
-    perms = inputs.permutations(S, rounds, 64, seed=2)
-    x = inputs.laplacian_blocks(B, 64, 8.0, -1024, 1023, seed=B)
+    perms = inputs.permutations(S, rounds, N, seed=2)
+    x = inputs.laplacian_blocks(B, N, 8.0, -1024, 1023, seed=B)
     sets = inputs.set_indices(B, S, seed=B, skip_frac=0.1)
     if B > 20:
         sets[3] = 200
@@ -70,6 +71,26 @@ def test_batch_no_sets_one_set(gpu, orc):
     ye, _ = orc.fwd_int(x, q, log2n, rounds, perms)
     xe, _ = orc.inv_int(ye, q, log2n, rounds, perms)
     assert st == 0 and np.array_equal(y, ye) and np.array_equal(xr, xe)
+
+
+@pytest.mark.parametrize("S,rounds", [(200, 2), (105, 8), (128, 2)])
+def test_batch_4x4_runs_of_sets(gpu, orc, S, rounds):
+    """4x4 blocks with long runs: 4096 skip blocks, then 4096 blocks of one
+    set, then uniform sets with one bad index; many sets (200) and large
+    tables (8 rounds)."""
+    log2n, N, B = 4, 16, 2 * 4096 + 4096 + 999
+    q = inputs.angle_indices(S, rounds, log2n, seed=S + rounds)
+    perms = inputs.permutations(S, rounds, N, seed=S)
+    x = inputs.laplacian_blocks(B, N, 12.0, -512, 511, seed=S)
+    sets = inputs.set_indices(B, S, seed=S, skip_frac=0.1)
+    sets[:4096] = 0xFFFF                 # a run of skip blocks
+    sets[4096:8192] = S - 1              # a run of one set
+    sets[9000] = S + 5                   # a bad index
+    y, xr, st = run_batch(gpu, log2n, rounds, q, perms, x, sets)
+    ye, ste = orc.fwd_int(x, q, log2n, rounds, perms, sets)
+    xe, _ = orc.inv_int(ye, q, log2n, rounds, perms, sets)
+    assert st == 4 and ste == orc.ERR_SET
+    assert np.array_equal(y, ye) and np.array_equal(xr, xe)
 
 
 def test_batch_many_sets_uncached(gpu, orc):

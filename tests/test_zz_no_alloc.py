@@ -22,19 +22,20 @@ def _t(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def test_static_scratch_forward_matches_workspace_path(gpu):
+@pytest.mark.parametrize("log2n", [4, 6])
+def test_static_scratch_forward_matches_workspace_path(gpu, log2n):
     import torch
-    log2n, rounds, S = 6, 2, 105
+    rounds, S, N = 2, 105, 1 << log2n
     q = inputs.angle_indices(S, rounds, log2n, seed=21)
-    perms = inputs.permutations(S, rounds, 64, seed=21)
+    perms = inputs.permutations(S, rounds, N, seed=21)
     plan = gpu.Plan(log2n, rounds, q, perms)
     stream = torch.cuda.current_stream().cuda_stream
     for call, B in enumerate([200003, 77777]):  # two calls in a row, different sizes
-        x = inputs.laplacian_blocks(B, 64, 8.0, -1024, 1023, seed=30 + call)
+        x = inputs.laplacian_blocks(B, N, 8.0, -1024, 1023, seed=30 + call)
         sets = inputs.set_indices(B, S, seed=30 + call, skip_frac=0.1)
         dx, ds = _t(x), _t(sets)
         ref = gpu.Batch(plan, B).build(ds).forward(dx)
-        y = torch.full((B, 64), -7, dtype=torch.int32, device="cuda")
+        y = torch.full((B, N), -7, dtype=torch.int32, device="cuda")
         st = torch.zeros(1, dtype=torch.int32, device="cuda")
         code = gpu.hygt_forward_static(plan.handle, dx.data_ptr(), y.data_ptr(), ds.data_ptr(),
                                        B, stream, st.data_ptr())
