@@ -40,10 +40,11 @@ namespace hygt {
 
 // Threads per CTA of the batch transform for block size 2^log2n (forward:
 // KIND 0, inverse: KIND 1), measured: where a block spans several lanes the
-// forward (more blocks per lane group) wants the registers of 384 threads;
-// the inverse on 32-value blocks the warps of 640; otherwise 512.
+// forward (more blocks per lane group) wants the registers of 384 threads,
+// and so does the 16x16 inverse (four blocks per lane group); the inverse on
+// 32-value blocks the warps of 640; otherwise 512.
 __host__ __device__ constexpr int batch_threads(int log2n, int kind) {
-  return log2n <= 3 ? 512 : kind == 0 ? 384 : (log2n == 5 ? 640 : 512);
+  return log2n <= 3 ? 512 : (kind == 0 || log2n == 8) ? 384 : (log2n == 5 ? 640 : 512);
 }
 constexpr int kBucketThreads = 512;  // threads per CTA of the bucketing kernels
 constexpr int kBucketTile = 8192;    // blocks per CTA tile in the scatter pass
@@ -56,9 +57,12 @@ constexpr int kBucketTile = 8192;    // blocks per CTA tile in the scatter pass
 // For 8x8 blocks E = 8 (L = 8 lanes, three cross-lane passes) with K = 8
 // forward and 4 inverse: fewer multiplier bytes per block than E = 16 with
 // K = 4 / 2 (measured 4-9% faster), for the same 64 value registers; for
-// 16x16 blocks likewise E = 16 with K = 4 / 2 rather than E = 32 with K = 2
-// (forward 16% faster); for 4x4 blocks E = 8 (two lanes) with K = 8 / 4
-// rather than one lane per block (forward 5% faster).
+// 16x16 blocks likewise E = 16 with K = 4 rather than E = 32 with K = 2
+// (forward 16% faster), and K = 4 in the inverse too, on 384 threads (13%
+// faster than K = 2 on 512, whose multiplier loads filled the L1 data pipe;
+// the 8x8 inverse with K = 8 on 384 threads is 27% slower than K = 4 on
+// 512); for 4x4 blocks E = 8 (two lanes) with K = 8 / 4 rather than one
+// lane per block (forward 5% faster).
 __host__ __device__ constexpr int batch_log2e(int log2n) {
   switch (log2n) {
     case 4: return 3;   // 4x4: 8 values per lane, 2 lanes
@@ -73,7 +77,8 @@ __host__ __device__ constexpr int batch_k(int log2n, bool inv) {
   switch (log2n) {
     case 1: case 2: return 1;
     case 4: case 6: return inv ? 4 : 8;
-    case 5: case 8: return inv ? 2 : 4;
+    case 5: return inv ? 2 : 4;
+    case 8: return 4;
     default: return 2;
   }
 }
@@ -367,9 +372,9 @@ struct PermBytes {
 // buffer holds GROUPS x batch_perm_k block regions per warp, and a lane
 // group's K blocks go through it in K / batch_perm_k passes.  Measured: one
 // pass is fastest where the kernel's shared memory leaves enough L1 (fewer
-// passes, more independent loads in flight); the 16x16 inverse gains 1-3%
-// from one block per pass (a 16x16 region is 1 KB, so the buffer shrinks by
-// 34 KB per CTA), while two passes cost 4x4 blocks 8-10%.
+// passes, more independent loads in flight); the 16x16 inverse runs one
+// block per pass (a 16x16 region is 1 KB; measured 1-3% faster with two
+// blocks per lane group), while two passes cost 4x4 blocks 8-10%.
 __host__ __device__ constexpr int batch_perm_k(int log2n, int kind) {
   return (log2n == 8 && kind == 1) ? 1 : batch_k(log2n, kind == 1);
 }
