@@ -1,0 +1,106 @@
+"""Host logic of the mixed-launch autotuner (no GPU): the timing call is
+replaced by a cost model, and the tuner must find the mode and CTA split
+that the model makes fastest.
+
+Model: class c alone on all G CTAs takes t_c; on a concurrent share of
+n_c CTAs it takes t_c G / n_c (linear scaling), and the concurrent launch
+ends with its slowest class; the sequential launch takes sum(t_c) times a
+penalty; the separate launches take sum(t_c) times another.
+"""
+import pytest
+
+from paper_2505_21728_gb300 import build as hb
+
+G = 152
+
+
+@pytest.fixture(scope="module")
+def at():
+    hb.build()
+    from paper_2505_21728_gb300 import autotune
+    return autotune
+
+
+class _FakeMixed:
+    def __init__(self, hygt, counts):
+        self.n = len(counts)
+        self.classes = (hygt.MixedClass * self.n)()
+        for i, c in enumerate(counts):
+            self.classes[i].nblocks = c
+        self.entries = [{} for _ in counts]
+        self.split = None
+
+    def set_split(self, split):
+        self.split = None if split is None else list(split)
+
+
+def _model(alone, seq_factor, sep_factor):
+    def time_pair(classes, n, reps):
+        ctas = [classes[i].ctas for i in range(n)]
+        if n == 1:  # one class alone on all CTAs
+            for c, t in alone.items():
+                if classes[0].nblocks == c:
+                    return t
+            raise AssertionError("unknown class")
+        counts = [classes[i].nblocks for i in range(n)]
+        active = [i for i in range(n) if counts[i] > 0]
+        times = [alone[counts[i]] for i in active]
+        if all(ctas[i] == 0 for i in range(n)):
+            return sum(times) * seq_factor
+        if all(ctas[i] == -1 for i in range(n)):
+            return sum(times) * sep_factor
+        assert all(ctas[i] >= 1 for i in active) and sum(ctas[i] for i in active) <= G
+        return max(alone[counts[i]] * G / ctas[i] for i in active)
+    return time_pair
+
+
+def _run(at, monkeypatch, alone, seq_factor, sep_factor):
+    from paper_2505_21728_gb300 import hygt
+    monkeypatch.setattr(at, "_time_pair", _model(alone, seq_factor, sep_factor))
+    monkeypatch.setattr(at, "_key", lambda mb: "cpu-model")
+    monkeypatch.setattr(at.hygt, "hygt_mixed_ctas", lambda: G)
+    mb = _FakeMixed(hygt, list(alone))
+    split = at.tune_split(mb, reps=1, use_cache=False)
+    assert mb.split == split
+    return split, _model(alone, seq_factor, sep_factor)
+
+
+def test_concurrent_split_balances_the_classes(at, monkeypatch):
+    # block counts double as class ids; class times 0.30 / 0.20 / 0.10 ms alone
+    alone = {4147200: 0.30, 725760: 0.20, 77760: 0.10}
+    split, model = _run(at, monkeypatch, alone, seq_factor=1.5, sep_factor=1.5)
+    assert all(c >= 1 for c in split) and sum(split) == G
+    # the best a linear model allows is sum(t) (every class finishing together)
+    from paper_2505_21728_gb300 import hygt
+    mb = _FakeMixed(hygt, list(alone))
+    for i, c in enumerate(split):
+        mb.classes[i].ctas = c
+    t = model(mb.classes, mb.n, 1)
+    assert t <= sum(alone.values()) * 1.02
+    # shares close to proportional
+    for i, c in enumerate(alone):
+        assert abs(split[i] - G * alone[c] / sum(alone.values())) <= 3
+
+
+def test_separate_launches_win_when_cheaper(at, monkeypatch):
+    alone = {1000: 0.3, 2000: 0.2, 3000: 0.1}
+    split, _ = _run(at, monkeypatch, alone, seq_factor=1.2, sep_factor=0.9)
+    assert split == [-1, -1, -1]
+
+
+def test_sequential_launch_wins_when_cheaper(at, monkeypatch):
+    alone = {1000: 0.3, 2000: 0.2, 3000: 0.1}
+    split, _ = _run(at, monkeypatch, alone, seq_factor=0.8, sep_factor=1.1)
+    assert split == [0, 0, 0]
+
+
+def test_single_active_class_takes_every_cta(at, monkeypatch):
+    from paper_2505_21728_gb300 import hygt
+    monkeypatch.setattr(at, "_key", lambda mb: "cpu-model")
+    monkeypatch.setattr(at.hygt, "hygt_mixed_ctas", lambda: G)
+
+    def no_timing(*a, **k):
+        raise AssertionError("nothing to time with one class")
+    monkeypatch.setattr(at, "_time_pair", no_timing)
+    mb = _FakeMixed(hygt, [0, 5000, 0])
+    assert at.tune_split(mb, reps=1, use_cache=False) == [0, G, 0]
