@@ -385,7 +385,13 @@ class Plan:
         """dL/dx (float32 [B, N]) and dL/dtheta (float64, flat) from the
         forward output y and dL/dy."""
         import torch
+        py = _dptr(y, torch.float32, self.N, "y")
+        pgy = _dptr(gy, torch.float32, self.N, "gy")
         nb = y.shape[0]
+        if gy.shape[0] != nb:
+            raise ValueError("gy must have the shape of y")
+        if sets is not None and sets.numel() != nb:
+            raise ValueError("sets must have one entry per block")
         gx = torch.empty_like(y)
         angles = self.num_sets * self.rounds * self.log2n * (self.N // 2)
         gth = torch.empty(angles, dtype=torch.float64, device=y.device)
@@ -397,8 +403,7 @@ class Plan:
         if sets is not None:
             ps = _dptr(sets, torch.int16 if sets.dtype == torch.int16 else torch.uint16, None, "sets")
         pst = None if status is None else _dptr(status, torch.int32, None, "status")
-        _check(hygt_backward_f32(self.handle, _dptr(y, torch.float32, self.N, "y"),
-                                 _dptr(gy, torch.float32, self.N, "gy"), gx.data_ptr(),
+        _check(hygt_backward_f32(self.handle, py, pgy, gx.data_ptr(),
                                  gth.data_ptr(), ps, nb, work.data_ptr(), wb,
                                  _stream_handle(stream), pst), "hygt_backward_f32")
         return gx, gth
@@ -453,6 +458,9 @@ class HostPipe:
             y = torch.empty((B, N), dtype=torch.int32, pin_memory=x.is_pinned())
         if xr is None:
             xr = torch.empty((B, N), dtype=torch.int16, pin_memory=x.is_pinned())
+        for t, dt, name in ((y, torch.int32, "y"), (xr, torch.int16, "xr")):
+            if t.is_cuda or t.dtype != dt or tuple(t.shape) != (B, N) or not t.is_contiguous():
+                raise ValueError("%s must be a contiguous %s CPU tensor [%d, %d]" % (name, dt, B, N))
         ps = None
         if sets is not None:
             if sets.is_cuda or sets.numel() != B or not sets.is_contiguous() or \
@@ -555,6 +563,8 @@ class MixedBatch:
             if sets is not None:
                 ps = _dptr(sets, torch.int16 if sets.dtype == torch.int16 else torch.uint16,
                            None, "sets")
+                if sets.numel() != nb:
+                    raise ValueError("class %d: sets must have one entry per block" % i)
             arr[i] = MixedClass(plan.handle, ps, nb, work.data_ptr(), work.numel(),
                                 x.data_ptr(), y.data_ptr(), xr.data_ptr(), 0)
             self.entries.append({"plan": plan, "x": x, "sets": sets, "y": y, "xr": xr,
@@ -693,26 +703,41 @@ class DenseKLT:
 
     def build(self, sets, nblocks, stream=None):
         import torch
-        self.nblocks = int(nblocks)
-        nbytes = dense_klt_workspace_bytes(self.handle, self.nblocks)
-        if self.work is None or self.work.numel() < nbytes:
-            self.work = torch.empty(max(1, nbytes), dtype=torch.uint8, device="cuda")
+        nblocks = int(nblocks)
+        if sets is not None and sets.numel() != nblocks:
+            raise ValueError("sets must have one entry per block")
+        nbytes = dense_klt_workspace_bytes(self.handle, nblocks)
+        if nbytes == 0 and nblocks > 0:
+            raise HygtError(HYGT_ERR_ARG, "dense_klt_workspace_bytes")
         ps = None
         if sets is not None:
             ps = _dptr(sets, torch.int16 if sets.dtype == torch.int16 else torch.uint16, None, "sets")
+        if self.work is None or self.work.numel() < nbytes:
+            self.work = torch.empty(max(1, nbytes), dtype=torch.uint8, device="cuda")
+        self.nblocks = nblocks
         _check(dense_klt_build(self.handle, ps, self.nblocks, self.work.data_ptr(),
                                self.work.numel(), _stream_handle(stream)), "dense_klt_build")
         return self
 
     def apply(self, x, kind=DENSE_KLT_BF16, out=None, status=None, stream=None):
+        """int16 x [nblocks, N] -> out [nblocks, N]: int32 for DENSE_KLT_INT,
+        float32 otherwise; ``build`` must have been called for nblocks."""
         import torch
+        if self.work is None or self.nblocks is None:
+            raise RuntimeError("DenseKLT.apply before build")
+        if x.dim() != 2 or x.shape[0] != self.nblocks:
+            raise ValueError("schedule built for %d blocks, x has shape %s"
+                             % (self.nblocks, tuple(x.shape)))
+        dt = torch.int32 if kind == DENSE_KLT_INT else torch.float32
         if out is None:
-            dt = torch.int32 if kind == DENSE_KLT_INT else torch.float32
             out = torch.empty((x.shape[0], self.N), dtype=dt, device=x.device)
+        elif out.dim() != 2 or out.shape[0] != self.nblocks:
+            raise ValueError("out must have shape [%d, %d]" % (self.nblocks, self.N))
+        px = _dptr(x, torch.int16, self.N, "x")
+        po = _dptr(out, dt, self.N, "out")
         pst = None if status is None else _dptr(status, torch.int32, None, "status")
-        _check(dense_klt_apply(self.handle, self.work.data_ptr(), _dptr(x, torch.int16, self.N, "x"),
-                               out.data_ptr(), self.nblocks, kind, _stream_handle(stream), pst),
-               "dense_klt_apply")
+        _check(dense_klt_apply(self.handle, self.work.data_ptr(), px, po, self.nblocks, kind,
+                               _stream_handle(stream), pst), "dense_klt_apply")
         return out
 
     def close(self):
