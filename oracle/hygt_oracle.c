@@ -202,7 +202,7 @@ static int inv_int_block(int log2n, int rounds, int set, const uint8_t *angle_id
   return OR_OK;
 }
 
-/* Shared driver for the integer paths: validates the set index, calls the
+/* Shared entry of the integer paths: validates the set index, calls the
    per-block routine, records the first error (lowest block index wins). */
 int oracle_fwd_int(int log2n, int rounds, int num_sets, const uint8_t *angle_idx,
                    const uint16_t *perms, int angle_bits, int frac_bits,
@@ -327,7 +327,7 @@ static void inv_f64_block(int log2n, int rounds, int set, const double *theta,
   }
 }
 
-static int f64_driver(int inverse, int log2n, int rounds, int num_sets, const double *theta,
+static int f64_run(int inverse, int log2n, int rounds, int num_sets, const double *theta,
                       const uint16_t *perms, const double *x, const uint16_t *set_idx,
                       int64_t nblocks, double *y) {
   int st = check_shape(log2n, rounds, num_sets);
@@ -360,12 +360,12 @@ static int f64_driver(int inverse, int log2n, int rounds, int num_sets, const do
 
 int oracle_fwd_f64(int log2n, int rounds, int num_sets, const double *theta, const uint16_t *perms,
                    const double *x, const uint16_t *set_idx, int64_t nblocks, double *y) {
-  return f64_driver(0, log2n, rounds, num_sets, theta, perms, x, set_idx, nblocks, y);
+  return f64_run(0, log2n, rounds, num_sets, theta, perms, x, set_idx, nblocks, y);
 }
 
 int oracle_inv_f64(int log2n, int rounds, int num_sets, const double *theta, const uint16_t *perms,
                    const double *y, const uint16_t *set_idx, int64_t nblocks, double *x) {
-  return f64_driver(1, log2n, rounds, num_sets, theta, perms, y, set_idx, nblocks, x);
+  return f64_run(1, log2n, rounds, num_sets, theta, perms, y, set_idx, nblocks, x);
 }
 
 /* Dense N x N matrix T of one set (row-major, T[i*N + k]): column k is the
