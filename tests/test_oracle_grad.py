@@ -59,3 +59,36 @@ def test_input_gradient_closed_form(orc):
     M = np.diag([0.0] * K + [1.0] * (N - K))
     expect = (2.0 / 10) * (x @ T.T @ M @ T)
     assert np.max(np.abs(gx - expect)) < 1e-12
+
+
+@pytest.mark.parametrize("log2n,rounds,K", [(4, 2, 4), (6, 2, 8)])
+def test_loss_respects_the_ky_fan_bound(orc, log2n, rounds, K):
+    """Energy outside the first K outputs is at least the sum of the N - K
+    smallest eigenvalues of the data's covariance (Ky Fan; the KLT of Eq. 2
+    attains it), for any angles."""
+    N, B = 1 << log2n, 512
+    x = np.random.default_rng(5).standard_normal((B, N)) @ np.linalg.cholesky(
+        0.9 ** np.abs(np.subtract.outer(np.arange(N), np.arange(N)))).T
+    lam = np.sort(np.linalg.eigvalsh(x.T @ x / B))
+    bound = np.sum(lam[:N - K])
+    for seed in range(4):
+        theta = inputs.theta_uniform((rounds, log2n, N // 2), seed=seed)
+        perms = inputs.permutations(1, rounds, N, seed=seed)[0]
+        assert orc.loss_f64(x, theta, log2n, rounds, K, perms) >= bound - 1e-9
+
+
+def test_loss_meets_the_ky_fan_bound_at_its_klt(orc):
+    """Data whose covariance has the rows of a HyGT T0 as eigenvectors, with
+    decreasing eigenvalues: at T0's angles the loss equals the bound and the
+    gradient vanishes."""
+    log2n, rounds, N, K = 4, 2, 16, 5
+    theta = inputs.theta_uniform((rounds, log2n, N // 2), seed=8)
+    perms = inputs.permutations(1, rounds, N, seed=8)[0]
+    T0 = orc.dense_f64(theta, log2n, rounds, perms)
+    d = np.linspace(3.0, 0.2, N)
+    q, _ = np.linalg.qr(np.random.default_rng(9).standard_normal((4 * N, N)))
+    z = q * np.sqrt(4 * N)                       # z^T z / B = I exactly
+    x = (z * d) @ T0                             # x_b = T0^T diag(d) z_b
+    loss, g, _ = orc.loss_grad_f64(x, theta, log2n, rounds, K, perms)
+    assert abs(loss - np.sum(d[K:] ** 2)) < 1e-10
+    assert np.max(np.abs(g)) < 1e-10
