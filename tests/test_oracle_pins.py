@@ -287,23 +287,101 @@ def test_overflow_is_reported(orc):
 
 
 # --------------------------------------------------------------------------
-# Dense matrix transform (Eq. 3): library matmul as the pin
+# Dense matrix transform (Eq. 3).  Pinned by what the mathematics fixes, not
+# by restating y = K x: with K the dense form of a HyGT set (Eq. 5), the
+# matrix transform must reproduce the pass-by-pass FP64 HyGT, which the
+# brute-force Givens product pins above; with K = 2^f times an exact signed
+# permutation (quarter-turn angles, entries in {-1, 0, 1}), the integer
+# transform is exact, since floor((2^f t + 2^(f-1)) / 2^f) = t for every
+# integer t; K = 2^f I returns x; the skip sentinel and bad set indices
+# behave as in the integer HyGT.
 # --------------------------------------------------------------------------
-def test_dense_apply_matches_matmul(orc):
-    rng = np.random.default_rng(0)
-    S, n, B = 3, 16, 40
-    K = rng.standard_normal((S, n, n))
-    x = rng.standard_normal((B, n))
-    sets = rng.integers(0, S, B).astype(np.uint16)
-    y, st = orc.dense_apply_f64(x, K, sets)
+@pytest.mark.parametrize("log2n,rounds", [(4, 2), (6, 2), (8, 3)])
+def test_dense_apply_f64_equals_hygt(orc, log2n, rounds):
+    """Eq. 3 with the Eq. 5 product as K: equal to the FP64 HyGT to 1e-12."""
+    N = 1 << log2n
+    S, B = 3, 60
+    theta = inputs.theta_uniform((S, rounds, log2n, N // 2), seed=20 + log2n)
+    perms = inputs.permutations(S, rounds, N, seed=21)
+    K = np.stack([orc.dense_f64(theta[s], log2n, rounds, perms[s]) for s in range(S)])
+    x = np.random.default_rng(22).standard_normal((B, N)) * 50
+    sets = inputs.set_indices(B, S, seed=23, skip_frac=0.1)
+    y_dense, st = orc.dense_apply_f64(x, K, sets)
     assert st == 0
-    assert np.allclose(y, np.einsum("bij,bj->bi", K[sets], x), rtol=0, atol=1e-12)
-    Ki = rng.integers(-256, 257, (S, n, n)).astype(np.int32)
-    xi = rng.integers(-1024, 1024, (B, n)).astype(np.int16)
-    yi, st = orc.dense_apply_int(xi, Ki, 8, sets)
+    y_hygt, st = orc.fwd_f64(x, theta, log2n, rounds, perms, sets)
     assert st == 0
-    acc = np.einsum("bij,bj->bi", Ki[sets].astype(np.int64), xi.astype(np.int64)) + 128
-    assert np.array_equal(yi, np.floor_divide(acc, 256))
+    assert np.max(np.abs(y_dense - y_hygt)) < 1e-12 * max(1.0, np.max(np.abs(x)))
+    # a different set's matrix would not match: the set lookup matters
+    wrong, _ = orc.dense_apply_f64(x, K[[1, 2, 0]], sets)
+    live = sets != 0xFFFF
+    assert np.max(np.abs(wrong[live] - y_hygt[live])) > 1e-3
+
+
+@pytest.mark.parametrize("log2n,rounds", [(2, 2), (4, 2), (6, 2)])
+def test_dense_apply_int_signed_permutation_exact(orc, log2n, rounds):
+    """K = 256 T with T the exact signed permutation of quarter-turn angles
+    (built from explicit Givens matrices): the integer matrix transform
+    returns x T^T exactly, and so does the integer HyGT of the same angles."""
+    N = 1 << log2n
+    rng = np.random.default_rng(31)
+    q = rng.choice(np.array([0, 64, 128, 192], np.uint8), size=(2, rounds, log2n, N // 2))
+    perms = inputs.permutations(2, rounds, N, seed=32, between_rounds_only=False)
+    T = np.stack([np.rint(brute_force_T(2 * math.pi * q[s].astype(float) / 256, perms[s],
+                                        log2n, rounds)).astype(np.int64) for s in range(2)])
+    assert set(np.unique(T).tolist()) <= {-1, 0, 1}
+    assert np.all(np.abs(T).sum(axis=2) == 1)  # one nonzero per row: a signed permutation
+    x = inputs.laplacian_blocks(40, N, 1000.0, -32768, 32767, seed=33)
+    sets = (np.arange(40) % 2).astype(np.uint16)
+    y, st = orc.dense_apply_int(x, (256 * T).astype(np.int32), 8, sets)
+    assert st == 0
+    expect = np.einsum("bij,bj->bi", T[sets], x.astype(np.int64))  # signed permutation of x
+    assert np.array_equal(y, expect)
+    yh, st = orc.fwd_int(x, q, log2n, rounds, perms, sets)
+    assert st == 0 and np.array_equal(yh, y)
+
+
+@pytest.mark.parametrize("frac_bits", [1, 8, 14])
+def test_dense_apply_int_identity(orc, frac_bits):
+    """K = 2^f I returns x for every f (the rounding offset never carries)."""
+    N, B = 64, 25
+    K = np.broadcast_to(np.eye(N, dtype=np.int32) << frac_bits, (2, N, N)).copy()
+    x = inputs.laplacian_blocks(B, N, 5000.0, -32768, 32767, seed=41)
+    sets = (np.arange(B) % 2).astype(np.uint16)
+    y, st = orc.dense_apply_int(x, K, frac_bits, sets)
+    assert st == 0 and np.array_equal(y, x.astype(np.int32))
+    yf, st = orc.dense_apply_f64(x.astype(float), np.eye(N)[None].repeat(2, 0), sets)
+    assert st == 0 and np.array_equal(yf, x.astype(float))
+
+
+def test_dense_apply_rounding_half_up(orc):
+    """One hand-worked row: K = [[128, 128]] (1/2, 1/2 at f = 8) on
+    (1, 0), (-1, 0), (3, 0), (1, 1): sums 128, -128, 384, 256 plus 128,
+    floored over 256 -> 1, 0, 2, 1 (round half up, like the HyGT butterfly)."""
+    K = np.array([[[128, 128], [0, 256]]], np.int32)
+    x = np.array([[1, 0], [-1, 0], [3, 0], [1, 1]], np.int16)
+    y, st = orc.dense_apply_int(x, K, 8)
+    assert st == 0
+    assert y[:, 0].tolist() == [1, 0, 2, 1]
+    assert y[:, 1].tolist() == [0, 0, 0, 1]
+
+
+def test_dense_apply_skip_and_bad_set_like_hygt(orc):
+    """0xFFFF is the identity (widened) and a set index >= S zeroes the block
+    and reports ERR_SET, exactly as in the integer HyGT."""
+    log2n, rounds, N, S = 4, 2, 16, 2
+    q = inputs.angle_indices(S, rounds, log2n, seed=51)
+    x = inputs.laplacian_blocks(6, N, 100.0, -1024, 1023, seed=52)
+    sets = np.array([0, 0xFFFF, 5, 1, 0xFFFF, 2], np.uint16)
+    yh, sth = orc.fwd_int(x, q, log2n, rounds, None, sets)
+    K = np.stack([np.eye(N, dtype=np.int32) * 256] * S)
+    yd, std = orc.dense_apply_int(x, K, 8, sets)
+    assert sth == std == orc.ERR_SET
+    for b in (1, 2, 4, 5):
+        assert np.array_equal(yd[b], yh[b])
+    assert np.all(yd[2] == 0) and np.all(yd[5] == 0)
+    assert np.array_equal(yd[1], x[1].astype(np.int32))
+    yf, stf = orc.dense_apply_f64(x.astype(float), K.astype(float) / 256, sets)
+    assert stf == orc.ERR_SET and np.all(yf[2] == 0) and np.array_equal(yf[1], x[1].astype(float))
 
 
 # --------------------------------------------------------------------------
