@@ -307,9 +307,15 @@ hygt_status dense_klt_apply(dense_klt d, const void *d_work, const int16_t *d_x,
  *   - nblocks must satisfy hygt_batch_workspace_bytes(plan, nblocks) <=
  *     8,388,608 (about 2 million 8x8 blocks for 105 sets); larger batches
  *     return HYGT_ERR_TOO_LARGE before anything is launched.
- *   - The call itself allocates nothing.  Its first call on a device looks
- *     up the address of that device's array (cudaGetSymbolAddress) with
- *     the device current; make that first call before any stream capture.
+ *   - The call allocates nothing itself.  Every call looks up the address
+ *     of the current device's array (cudaGetSymbolAddress, a host-side
+ *     query), so the call stays valid after a device reset.  The 8 MiB
+ *     array is placed in device memory when the library's device code is
+ *     loaded on that device; under CUDA's default lazy loading that is the
+ *     first call of this function there, which can then fail with
+ *     HYGT_ERR_CUDA when device memory is short.  Make one warm-up call at
+ *     start-up (nblocks = 1 is enough), and make it before any stream
+ *     capture.
  *   - All calls share the array and it keeps the last call's schedule; each
  *     call rebuilds the parts that must start at zero.  Calls whose work
  *     overlaps on the GPU (other streams, other host threads) race on the

@@ -965,32 +965,24 @@ const char* hygt_status_string(int status) {
 // ---------------------------------------------------------------- no allocation
 // hygt_forward_static: the schedule lives in a file-scope device array
 // instead of a caller workspace.  Host code cannot use the array's name as a
-// device address (in host code it names a host-side stand-in), so the
-// address is looked up once per device with cudaGetSymbolAddress, with that
-// device current, and cached.
+// device address (in host code it names a host-side stand-in), so every call
+// looks the address up with cudaGetSymbolAddress, with the caller's device
+// current.  The lookup is a host-side query once the module is loaded, and
+// doing it per call (rather than caching one address per device index)
+// stays right after a device reset, when the module is loaded again and the
+// array may move.
 namespace {
 
 constexpr size_t kStaticScratchBytes = (size_t)8 << 20;
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_static_mu;
-void* g_static_ptr[kMaxDevices] = {};
-
 hygt_status static_scratch(void** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) return HYGT_ERR_CUDA;
-  if (dev < 0 || dev >= kMaxDevices) return HYGT_ERR_CUDA;
-  std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
-      cudaGetLastError();
-      return HYGT_ERR_CUDA;
-    }
-    g_static_ptr[dev] = p;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+    cudaGetLastError();
+    return HYGT_ERR_CUDA;
   }
-  *out = g_static_ptr[dev];
+  *out = p;
   return HYGT_OK;
 }
 

@@ -46,14 +46,33 @@ def test_static_scratch_forward_matches_workspace_path(gpu, log2n):
 
 
 def test_static_scratch_rejects_oversized_batch(gpu):
+    """The smallest batch whose schedule no longer fits is refused.  Its
+    buffers are allocated in full, so a regression of the size check would
+    give a wrong return code, not an access past the end of a buffer."""
     import torch
     q = inputs.angle_indices(4, 2, 6, seed=1)
     plan = gpu.Plan(6, 2, q)
-    B = 4_000_000  # schedule larger than the 8 MiB array
-    assert gpu.hygt_batch_workspace_bytes(plan.handle, B) > 8 << 20
-    x = torch.zeros((16, 64), dtype=torch.int16, device="cuda")
-    y = torch.zeros((16, 64), dtype=torch.int32, device="cuda")
-    code = gpu.hygt_forward_static(plan.handle, x.data_ptr(), y.data_ptr(), None, B,
-                                   torch.cuda.current_stream().cuda_stream, None)
+    lo, hi = 1, 4_000_000  # the 8 MiB limit lies between these block counts
+    assert gpu.hygt_batch_workspace_bytes(plan.handle, hi) > 8 << 20
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if gpu.hygt_batch_workspace_bytes(plan.handle, mid) > 8 << 20:
+            hi = mid
+        else:
+            lo = mid
+    B = hi
+    x = torch.zeros((B, 64), dtype=torch.int16, device="cuda")
+    y = torch.zeros((B, 64), dtype=torch.int32, device="cuda")
+    s = torch.zeros(B, dtype=torch.int16, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    code = gpu.hygt_forward_static(plan.handle, x.data_ptr(), y.data_ptr(), s.data_ptr(), B,
+                                   stream, st.data_ptr())
     assert code == gpu.HYGT_ERR_TOO_LARGE
     assert "static scratch" in gpu.hygt_status_string(code)
+    # one block fewer fits, and runs
+    code = gpu.hygt_forward_static(plan.handle, x.data_ptr(), y.data_ptr(), s.data_ptr(), lo,
+                                   stream, st.data_ptr())
+    assert code == gpu.HYGT_OK
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
