@@ -577,3 +577,156 @@ int oracle_dense_apply_int(int n, int num_sets, const int32_t *K, int frac_bits,
   }
   return bad_code;
 }
+
+/* ------------------------------------------------------------------ */
+/* General PMPT with explicit index vectors (Sec. III PMPT product,    */
+/* Eq. 5; Sec. IV parallel-Givens matrix over an arbitrary pair cover, */
+/* Eq. 7 and Eq. 8).  Pass k of set s has N/2 pairs (m_j, n_j) and N/2 */
+/* angles; the pairs must cover 0..N-1 (each index in exactly one      */
+/* pair), which makes the rotations of a pass commute.  Layouts:       */
+/* angles [S][P][N/2] (8-bit indices or FP64 radians), m and n         */
+/* [S][P][N/2].  N is any even number up to 256.  The forward applies  */
+/* pass 0 first; the inverse runs the passes in reverse with negated   */
+/* angles (Eq. 9).  Integer rounding, skip and bad-set handling are    */
+/* those of the HyGT paths above.                                      */
+/* ------------------------------------------------------------------ */
+static int pmpt_check(int n, int passes, int num_sets, const uint16_t *m_idx,
+                      const uint16_t *n_idx) {
+  if (n < 2 || n > OR_MAX_N || (n & 1) || passes < 1 || passes > 4096) return OR_ERR_ARG;
+  if (num_sets < 1 || num_sets > 65535 || !m_idx || !n_idx) return OR_ERR_ARG;
+  for (int64_t sp = 0; sp < (int64_t)num_sets * passes; ++sp) {
+    int seen[OR_MAX_N];
+    memset(seen, 0, sizeof(seen));
+    for (int j = 0; j < n / 2; ++j) {
+      int m = m_idx[sp * (n / 2) + j], k = n_idx[sp * (n / 2) + j];
+      if (m >= n || k >= n || m == k || seen[m] || seen[k]) return OR_ERR_ARG;
+      seen[m] = seen[k] = 1;
+    }
+  }
+  return OR_OK;
+}
+
+static int pmpt_int_block(int inverse, int n, int passes, int set, const uint8_t *angle_idx,
+                          const uint16_t *m_idx, const uint16_t *n_idx, const int32_t *ctab,
+                          const int32_t *stab, int frac_bits, int64_t *v) {
+  int64_t half = (int64_t)1 << (frac_bits - 1);
+  for (int kk = 0; kk < passes; ++kk) {
+    int k = inverse ? passes - 1 - kk : kk;
+    int64_t base = ((int64_t)set * passes + k) * (n / 2);
+    for (int j = 0; j < n / 2; ++j) {
+      int m = m_idx[base + j], q = n_idx[base + j];
+      int64_t c = ctab[angle_idx[base + j]];
+      int64_t s = inverse ? -(int64_t)stab[angle_idx[base + j]] : stab[angle_idx[base + j]];
+      int64_t a = v[m], b = v[q];
+      int64_t um = c * a + s * b + half;
+      int64_t un = -s * a + c * b + half;
+      if (!fits_i32(um) || !fits_i32(un)) return OR_ERR_OVERFLOW;
+      v[m] = floor_div_pow2(um, frac_bits);
+      v[q] = floor_div_pow2(un, frac_bits);
+    }
+  }
+  return OR_OK;
+}
+
+static int pmpt_int_run(int inverse, int n, int passes, int num_sets, const uint8_t *angle_idx,
+                        const uint16_t *m_idx, const uint16_t *n_idx, int angle_bits,
+                        int frac_bits, const void *in, const uint16_t *set_idx, int64_t nblocks,
+                        void *out) {
+  int st = pmpt_check(n, passes, num_sets, m_idx, n_idx);
+  if (st) return st;
+  int32_t ctab[256], stab[256];
+  st = oracle_cs_table(angle_bits, frac_bits, ctab, stab);
+  if (st) return st;
+  int64_t first_bad = -1;
+  int bad_code = OR_OK;
+#pragma omp parallel for schedule(static)
+  for (int64_t b = 0; b < nblocks; ++b) {
+    int64_t v[OR_MAX_N];
+    unsigned set = set_idx ? set_idx[b] : 0u;
+    int code = OR_OK;
+    for (int i = 0; i < n; ++i)
+      v[i] = inverse ? ((const int32_t *)in)[b * n + i] : ((const int16_t *)in)[b * n + i];
+    if (set == OR_SKIP) {
+      /* identity */
+    } else if (set >= (unsigned)num_sets) {
+      code = OR_ERR_SET;
+    } else {
+      code = pmpt_int_block(inverse, n, passes, (int)set, angle_idx, m_idx, n_idx, ctab, stab,
+                            frac_bits, v);
+    }
+    if (code != OR_OK) {
+      for (int i = 0; i < n; ++i) v[i] = 0;
+#pragma omp critical
+      {
+        if (first_bad < 0 || b < first_bad) { first_bad = b; bad_code = code; }
+      }
+    }
+    for (int i = 0; i < n; ++i) {
+      if (inverse) ((int16_t *)out)[b * n + i] = saturate_i16(v[i]);
+      else ((int32_t *)out)[b * n + i] = (int32_t)v[i];
+    }
+  }
+  return bad_code;
+}
+
+int oracle_pmpt_fwd_int(int n, int passes, int num_sets, const uint8_t *angle_idx,
+                        const uint16_t *m_idx, const uint16_t *n_idx, int angle_bits,
+                        int frac_bits, const int16_t *x, const uint16_t *set_idx,
+                        int64_t nblocks, int32_t *y) {
+  return pmpt_int_run(0, n, passes, num_sets, angle_idx, m_idx, n_idx, angle_bits, frac_bits, x,
+                      set_idx, nblocks, y);
+}
+
+int oracle_pmpt_inv_int(int n, int passes, int num_sets, const uint8_t *angle_idx,
+                        const uint16_t *m_idx, const uint16_t *n_idx, int angle_bits,
+                        int frac_bits, const int32_t *y, const uint16_t *set_idx,
+                        int64_t nblocks, int16_t *x) {
+  return pmpt_int_run(1, n, passes, num_sets, angle_idx, m_idx, n_idx, angle_bits, frac_bits, y,
+                      set_idx, nblocks, x);
+}
+
+static int pmpt_f64_run(int inverse, int n, int passes, int num_sets, const double *theta,
+                        const uint16_t *m_idx, const uint16_t *n_idx, const double *in,
+                        const uint16_t *set_idx, int64_t nblocks, double *out) {
+  int st = pmpt_check(n, passes, num_sets, m_idx, n_idx);
+  if (st) return st;
+  int bad_code = OR_OK;
+#pragma omp parallel for schedule(static)
+  for (int64_t b = 0; b < nblocks; ++b) {
+    double v[OR_MAX_N];
+    unsigned set = set_idx ? set_idx[b] : 0u;
+    for (int i = 0; i < n; ++i) v[i] = in[b * n + i];
+    if (set != OR_SKIP && set >= (unsigned)num_sets) {
+      for (int i = 0; i < n; ++i) v[i] = 0.0;
+#pragma omp critical
+      bad_code = OR_ERR_SET;
+    } else if (set != OR_SKIP) {
+      for (int kk = 0; kk < passes; ++kk) {
+        int k = inverse ? passes - 1 - kk : kk;
+        int64_t base = ((int64_t)set * passes + k) * (n / 2);
+        for (int j = 0; j < n / 2; ++j) {
+          int m = m_idx[base + j], q = n_idx[base + j];
+          double t = inverse ? -theta[base + j] : theta[base + j];
+          double c = cos(t), s = sin(t);
+          double a = v[m], bb = v[q];
+          v[m] = c * a + s * bb;
+          v[q] = -s * a + c * bb;
+        }
+      }
+    }
+    for (int i = 0; i < n; ++i) out[b * n + i] = v[i];
+  }
+  return bad_code;
+}
+
+int oracle_pmpt_fwd_f64(int n, int passes, int num_sets, const double *theta,
+                        const uint16_t *m_idx, const uint16_t *n_idx, const double *x,
+                        const uint16_t *set_idx, int64_t nblocks, double *y) {
+  return pmpt_f64_run(0, n, passes, num_sets, theta, m_idx, n_idx, x, set_idx, nblocks, y);
+}
+
+int oracle_pmpt_inv_f64(int n, int passes, int num_sets, const double *theta,
+                        const uint16_t *m_idx, const uint16_t *n_idx, const double *y,
+                        const uint16_t *set_idx, int64_t nblocks, double *x) {
+  return pmpt_f64_run(1, n, passes, num_sets, theta, m_idx, n_idx, y, set_idx, nblocks, x);
+}

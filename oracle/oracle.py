@@ -18,7 +18,8 @@ __all__ = [
     "build", "lib", "OK", "ERR_ARG", "ERR_SET", "ERR_OVERFLOW", "SKIP",
     "pair", "cs_table", "fwd_int", "inv_int", "fwd_f64", "inv_f64", "dense_f64",
     "loss_grad_f64", "loss_f64", "dense_apply_f64", "dense_apply_int",
-    "num_threads", "set_num_threads",
+    "num_threads", "set_num_threads", "pmpt_fwd_int", "pmpt_inv_int", "pmpt_fwd_f64",
+    "pmpt_inv_f64",
 ]
 
 OK, ERR_ARG, ERR_SET, ERR_OVERFLOW = 0, 1, 4, 5
@@ -75,6 +76,14 @@ def lib() -> ctypes.CDLL:
         L.oracle_dense_apply_f64.restype = i32
         L.oracle_dense_apply_int.argtypes = [i32, i32, P, i32, P, P, i64, P]
         L.oracle_dense_apply_int.restype = i32
+        for name in ("oracle_pmpt_fwd_int", "oracle_pmpt_inv_int"):
+            f = getattr(L, name)
+            f.argtypes = [i32, i32, i32, P, P, P, i32, i32, P, P, i64, P]
+            f.restype = i32
+        for name in ("oracle_pmpt_fwd_f64", "oracle_pmpt_inv_f64"):
+            f = getattr(L, name)
+            f.argtypes = [i32, i32, i32, P, P, P, P, P, i64, P]
+            f.restype = i32
         _lib = L
     return _lib
 
@@ -245,3 +254,58 @@ def dense_apply_int(x, K_int, frac_bits=8, set_idx=None):
     y = np.zeros((B, n), np.int32)
     st = lib().oracle_dense_apply_int(n, S, _ptr(K), frac_bits, _ptr(x), _ptr(s), B, _ptr(y))
     return y, int(st)
+
+
+def _pmpt_shape(angles, m_idx, n, passes):
+    assert m_idx.size == angles.size and angles.size % (passes * (n // 2)) == 0
+    return angles.size // (passes * (n // 2))
+
+
+def _pmpt_int(fn, inp, in_dtype, out_dtype, angle_idx, m_idx, n_idx, n, passes, set_idx,
+              angle_bits, frac_bits):
+    v = _c(inp, in_dtype)
+    a = _c(angle_idx, np.uint8)
+    mi, ni = _c(m_idx, np.uint16), _c(n_idx, np.uint16)
+    s = _c(set_idx, np.uint16)
+    S = _pmpt_shape(a, mi, n, passes)
+    B = v.size // n
+    out = np.zeros((B, n), out_dtype)
+    st = fn(n, passes, S, _ptr(a), _ptr(mi), _ptr(ni), angle_bits, frac_bits, _ptr(v), _ptr(s),
+            B, _ptr(out))
+    return out, int(st)
+
+
+def pmpt_fwd_int(x, angle_idx, m_idx, n_idx, n, passes, set_idx=None, angle_bits=8,
+                 frac_bits=8):
+    """Integer PMPT with explicit pair covers (Sec. III-IV): int16 x[B][n] ->
+    (int32 y, status); angle_idx, m_idx, n_idx of shape [S][passes][n/2]."""
+    return _pmpt_int(lib().oracle_pmpt_fwd_int, x, np.int16, np.int32, angle_idx, m_idx, n_idx,
+                     n, passes, set_idx, angle_bits, frac_bits)
+
+
+def pmpt_inv_int(y, angle_idx, m_idx, n_idx, n, passes, set_idx=None, angle_bits=8,
+                 frac_bits=8):
+    """Inverse integer PMPT: int32 y -> (int16 x saturated, status)."""
+    return _pmpt_int(lib().oracle_pmpt_inv_int, y, np.int32, np.int16, angle_idx, m_idx, n_idx,
+                     n, passes, set_idx, angle_bits, frac_bits)
+
+
+def _pmpt_f64(fn, inp, theta, m_idx, n_idx, n, passes, set_idx):
+    v = _c(inp, np.float64)
+    t = _c(theta, np.float64)
+    mi, ni = _c(m_idx, np.uint16), _c(n_idx, np.uint16)
+    s = _c(set_idx, np.uint16)
+    S = _pmpt_shape(t, mi, n, passes)
+    B = v.size // n
+    out = np.zeros((B, n), np.float64)
+    st = fn(n, passes, S, _ptr(t), _ptr(mi), _ptr(ni), _ptr(v), _ptr(s), B, _ptr(out))
+    return out, int(st)
+
+
+def pmpt_fwd_f64(x, theta, m_idx, n_idx, n, passes, set_idx=None):
+    """FP64 PMPT with free angles theta[S][passes][n/2] -> (y, status)."""
+    return _pmpt_f64(lib().oracle_pmpt_fwd_f64, x, theta, m_idx, n_idx, n, passes, set_idx)
+
+
+def pmpt_inv_f64(y, theta, m_idx, n_idx, n, passes, set_idx=None):
+    return _pmpt_f64(lib().oracle_pmpt_inv_f64, y, theta, m_idx, n_idx, n, passes, set_idx)
