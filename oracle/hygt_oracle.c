@@ -730,3 +730,135 @@ int oracle_pmpt_inv_f64(int n, int passes, int num_sets, const double *theta,
                         const uint16_t *set_idx, int64_t nblocks, double *x) {
   return pmpt_f64_run(1, n, passes, num_sets, theta, m_idx, n_idx, y, set_idx, nblocks, x);
 }
+
+/* ------------------------------------------------------------------ */
+/* Secondary-transform pipeline (Sec. VI): a separable primary         */
+/* transform of an M x M residual block, then the HyGT on the top-left */
+/* s x s sub-block of its coefficients (s = 4 for 4 x 4 blocks, s = 8  */
+/* for 8 x 8 and larger), the other coefficients passed through.  The  */
+/* paper does not fix the primary; it is read here as the orthonormal  */
+/* 2-D DCT-II, D[k][i] = a_k cos(pi (2i + 1) k / (2M)) with            */
+/* a_0 = sqrt(1/M), a_k = sqrt(2/M), in integer arithmetic with the    */
+/* HyGT's precision: C = round(2^8 D) (half away from zero), each 1-D  */
+/* stage y_k = floor((sum_i C[k][i] x_i + 2^7) / 2^8), rows first then */
+/* columns; the inverse runs the columns first, then the rows, with    */
+/* C transposed and the same rounding, and saturates to int16.  The    */
+/* sub-block is read in raster order (the HyGT's vector order).  Set   */
+/* index 0xFFFF means "no secondary transform" (primary only).         */
+/* ------------------------------------------------------------------ */
+#define OR_PRIMARY_BITS 8
+#define OR_MAX_M 32
+
+/* FP64 DCT-II matrix and its integer form [M][M] (row k = basis k). */
+int oracle_dct_matrix(int log2m, int32_t *C, double *D) {
+  if (log2m < 1 || log2m > 5) return OR_ERR_ARG;
+  int M = 1 << log2m;
+  double scale = ldexp(1.0, OR_PRIMARY_BITS);
+  for (int k = 0; k < M; ++k) {
+    double a = k == 0 ? sqrt(1.0 / M) : sqrt(2.0 / M);
+    for (int i = 0; i < M; ++i) {
+      double d = a * cos(OR_TWO_PI * 0.5 * (2.0 * i + 1.0) * k / (2.0 * M));
+      if (D) D[k * M + i] = d;
+      if (C) C[k * M + i] = (int32_t)lround(scale * d);
+    }
+  }
+  return OR_OK;
+}
+
+/* One separable stage along rows (dim 0) or columns (dim 1) of an M x M
+   block held row-major in v; transpose selects C^T (inverse). */
+static void primary_stage(int M, const int32_t *C, int dim, int transpose, int64_t *v) {
+  int64_t half = (int64_t)1 << (OR_PRIMARY_BITS - 1);
+  int64_t line[OR_MAX_M], out[OR_MAX_M];
+  for (int l = 0; l < M; ++l) {
+    for (int i = 0; i < M; ++i) line[i] = dim == 0 ? v[l * M + i] : v[i * M + l];
+    for (int k = 0; k < M; ++k) {
+      int64_t acc = half;
+      for (int i = 0; i < M; ++i)
+        acc += (int64_t)(transpose ? C[i * M + k] : C[k * M + i]) * line[i];
+      out[k] = floor_div_pow2(acc, OR_PRIMARY_BITS);
+    }
+    for (int k = 0; k < M; ++k) {
+      if (dim == 0) v[l * M + k] = out[k];
+      else v[k * M + l] = out[k];
+    }
+  }
+}
+
+static int secondary_run(int inverse, int log2m, int log2n, int rounds, int num_sets,
+                         const uint8_t *angle_idx, const uint16_t *perms, int angle_bits,
+                         int frac_bits, const void *in, const uint16_t *set_idx, int64_t nblocks,
+                         void *out) {
+  int st = check_shape(log2n, rounds, num_sets);
+  if (st) return st;
+  if (log2m < 2 || log2m > 5 || (log2n != 4 && log2n != 6)) return OR_ERR_ARG;
+  int M = 1 << log2m, s = 1 << (log2n / 2);
+  if ((M == 4 && s != 4) || (M >= 8 && s != 8)) return OR_ERR_ARG;
+  int32_t C[OR_MAX_M * OR_MAX_M];
+  oracle_dct_matrix(log2m, C, NULL);
+  int32_t ctab[256], stab[256];
+  st = oracle_cs_table(angle_bits, frac_bits, ctab, stab);
+  if (st) return st;
+  int64_t first_bad = -1;
+  int bad_code = OR_OK;
+#pragma omp parallel for schedule(static)
+  for (int64_t b = 0; b < nblocks; ++b) {
+    int64_t v[OR_MAX_M * OR_MAX_M], sub[OR_MAX_N];
+    unsigned set = set_idx ? set_idx[b] : 0u;
+    int code = OR_OK;
+    int MM = M * M;
+    for (int i = 0; i < MM; ++i)
+      v[i] = inverse ? ((const int32_t *)in)[b * MM + i] : ((const int16_t *)in)[b * MM + i];
+    if (set != OR_SKIP && set >= (unsigned)num_sets) code = OR_ERR_SET;
+    if (code == OR_OK && !inverse) {
+      primary_stage(M, C, 0, 0, v); /* rows */
+      primary_stage(M, C, 1, 0, v); /* columns */
+    }
+    if (code == OR_OK && set != OR_SKIP) {
+      for (int r = 0; r < s; ++r)
+        for (int c = 0; c < s; ++c) sub[r * s + c] = v[r * M + c];
+      code = inverse ? inv_int_block(log2n, rounds, (int)set, angle_idx, perms, ctab, stab,
+                                     frac_bits, sub)
+                     : fwd_int_block(log2n, rounds, (int)set, angle_idx, perms, ctab, stab,
+                                     frac_bits, sub);
+      for (int r = 0; r < s; ++r)
+        for (int c = 0; c < s; ++c) v[r * M + c] = sub[r * s + c];
+    }
+    if (code == OR_OK && inverse) {
+      primary_stage(M, C, 1, 1, v); /* columns */
+      primary_stage(M, C, 0, 1, v); /* rows */
+    }
+    if (code == OR_OK) {
+      for (int i = 0; i < MM; ++i)
+        if (!fits_i32(v[i])) code = OR_ERR_OVERFLOW;
+    }
+    if (code != OR_OK) {
+      for (int i = 0; i < MM; ++i) v[i] = 0;
+#pragma omp critical
+      {
+        if (first_bad < 0 || b < first_bad) { first_bad = b; bad_code = code; }
+      }
+    }
+    for (int i = 0; i < MM; ++i) {
+      if (inverse) ((int16_t *)out)[b * MM + i] = saturate_i16(v[i]);
+      else ((int32_t *)out)[b * MM + i] = (int32_t)v[i];
+    }
+  }
+  return bad_code;
+}
+
+int oracle_secondary_fwd(int log2m, int log2n, int rounds, int num_sets,
+                         const uint8_t *angle_idx, const uint16_t *perms, int angle_bits,
+                         int frac_bits, const int16_t *x, const uint16_t *set_idx,
+                         int64_t nblocks, int32_t *y) {
+  return secondary_run(0, log2m, log2n, rounds, num_sets, angle_idx, perms, angle_bits,
+                       frac_bits, x, set_idx, nblocks, y);
+}
+
+int oracle_secondary_inv(int log2m, int log2n, int rounds, int num_sets,
+                         const uint8_t *angle_idx, const uint16_t *perms, int angle_bits,
+                         int frac_bits, const int32_t *y, const uint16_t *set_idx,
+                         int64_t nblocks, int16_t *x) {
+  return secondary_run(1, log2m, log2n, rounds, num_sets, angle_idx, perms, angle_bits,
+                       frac_bits, y, set_idx, nblocks, x);
+}

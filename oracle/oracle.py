@@ -19,7 +19,7 @@ __all__ = [
     "pair", "cs_table", "fwd_int", "inv_int", "fwd_f64", "inv_f64", "dense_f64",
     "loss_grad_f64", "loss_f64", "dense_apply_f64", "dense_apply_int",
     "num_threads", "set_num_threads", "pmpt_fwd_int", "pmpt_inv_int", "pmpt_fwd_f64",
-    "pmpt_inv_f64",
+    "pmpt_inv_f64", "dct_matrix", "secondary_fwd", "secondary_inv",
 ]
 
 OK, ERR_ARG, ERR_SET, ERR_OVERFLOW = 0, 1, 4, 5
@@ -83,6 +83,12 @@ def lib() -> ctypes.CDLL:
         for name in ("oracle_pmpt_fwd_f64", "oracle_pmpt_inv_f64"):
             f = getattr(L, name)
             f.argtypes = [i32, i32, i32, P, P, P, P, P, i64, P]
+            f.restype = i32
+        L.oracle_dct_matrix.argtypes = [i32, P, P]
+        L.oracle_dct_matrix.restype = i32
+        for name in ("oracle_secondary_fwd", "oracle_secondary_inv"):
+            f = getattr(L, name)
+            f.argtypes = [i32, i32, i32, i32, P, P, i32, i32, P, P, i64, P]
             f.restype = i32
         _lib = L
     return _lib
@@ -309,3 +315,46 @@ def pmpt_fwd_f64(x, theta, m_idx, n_idx, n, passes, set_idx=None):
 
 def pmpt_inv_f64(y, theta, m_idx, n_idx, n, passes, set_idx=None):
     return _pmpt_f64(lib().oracle_pmpt_inv_f64, y, theta, m_idx, n_idx, n, passes, set_idx)
+
+
+def dct_matrix(log2m):
+    """(integer C = round(256 D), FP64 D) of the M x M orthonormal DCT-II
+    (row k = basis function k), the primary transform of the Sec. VI
+    pipeline."""
+    M = 1 << log2m
+    C = np.zeros((M, M), np.int32)
+    D = np.zeros((M, M), np.float64)
+    if lib().oracle_dct_matrix(log2m, _ptr(C), _ptr(D)):
+        raise ValueError("oracle_dct_matrix: bad arguments")
+    return C, D
+
+
+def _secondary(fn, inp, in_dtype, out_dtype, log2m, angle_idx, log2n, rounds, perms, set_idx,
+               angle_bits, frac_bits):
+    v = _c(inp, in_dtype)
+    a = _c(angle_idx, np.uint8)
+    p = _c(perms, np.uint16)
+    s = _c(set_idx, np.uint16)
+    S = _shape(a, log2n, rounds)
+    MM = 1 << (2 * log2m)
+    B = v.size // MM
+    out = np.zeros((B, MM), out_dtype)
+    st = fn(log2m, log2n, rounds, S, _ptr(a), _ptr(p), angle_bits, frac_bits, _ptr(v), _ptr(s), B,
+            _ptr(out))
+    return out, int(st)
+
+
+def secondary_fwd(x, log2m, angle_idx, log2n, rounds, perms=None, set_idx=None, angle_bits=8,
+                  frac_bits=8):
+    """Integer DCT-II primary of M x M int16 blocks x[B][M*M] (raster), then
+    the integer HyGT on the top-left s x s coefficients -> (int32 y, status)."""
+    return _secondary(lib().oracle_secondary_fwd, x, np.int16, np.int32, log2m, angle_idx, log2n,
+                      rounds, perms, set_idx, angle_bits, frac_bits)
+
+
+def secondary_inv(y, log2m, angle_idx, log2n, rounds, perms=None, set_idx=None, angle_bits=8,
+                  frac_bits=8):
+    """Inverse HyGT on the top-left sub-block, then the inverse DCT-II ->
+    (int16 x saturated, status)."""
+    return _secondary(lib().oracle_secondary_inv, y, np.int32, np.int16, log2m, angle_idx, log2n,
+                      rounds, perms, set_idx, angle_bits, frac_bits)
