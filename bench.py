@@ -49,6 +49,15 @@ def parse_args():
                     help="skip the secondary workloads (mixed block sizes)")
     ap.add_argument("--nblocks", type=int, default=0,
                     help="use only the first N blocks of the workload (profiling cases)")
+    ap.add_argument("--case", choices=sorted(CASES), default=None,
+                    help="run one kernel case instead of the benchmark (for ncu): its "
+                         "kernels twice untimed, then --reps times, and print the mean "
+                         "CUDA-event time of one repetition")
+    ap.add_argument("--reps", type=int, default=1, help="--case: timed repetitions")
+    ap.add_argument("--scale-down", type=int, default=1,
+                    help="--case mixed: divide the frame batch's block counts")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="--case mixed: default CTA split instead of the autotuner's")
     return ap.parse_args()
 
 
@@ -351,6 +360,10 @@ def run_ours(args, rank, world, local):
                 "fwd_ms": f_avg, "inv_ms": i_avg, "schedule_ms": statistics.mean(build_ms),
                 "step_frac": (step_bytes / (total_ms / K / 1000.0) / 1e9) / peak}
 
+    # the same step repeated for about two seconds after the timed region, with
+    # its own clock record (the timed region itself is short)
+    sustained = sustained_leg(batch, d_s, d_x, d_y, d_xr, dev, stream, local, total_ms / K)
+
     # context: the direct (unbucketed) kernels on the same data
     direct = direct_path_ms(plan, d_x, d_s, d_y, d_xr, stream)
     del d_y, d_xr
@@ -370,6 +383,7 @@ def run_ours(args, rank, world, local):
         "roofline": roofline,
         "gpu_launches": 5 * K,
         "clocks": clock_info,
+        "sustained": sustained,
         "direct_path": direct,
     }
 
@@ -382,6 +396,10 @@ def run_ours(args, rank, world, local):
         line["mixed"] = mixed_leg(dev, stream, steps=max(10, K // 2))
         line["backward"] = backward_leg(dev, stream, steps=max(5, K // 4))
         line["small_4x4"] = small_leg(dev, stream, steps=max(20, K))
+        line["coding_gain"] = coding_gain_leg(dev, stream)
+        del d_x, d_s
+        torch.cuda.empty_cache()
+        line["stress_16x16"] = stress_leg(dev, stream)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, data)
@@ -391,6 +409,170 @@ def run_ours(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def sustained_leg(batch, d_s, d_x, d_y, d_xr, dev, stream, local, step_ms, seconds=2.0):
+    import torch
+    steps = max(20, int(seconds * 1000.0 / max(step_ms, 1e-3)))
+    clocks = ClockSampler(gpu_smi_id(dev, local))
+    clocks.start()
+    time.sleep(0.3)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        batch.build(d_s)
+        batch.forward(d_x, out=d_y)
+        batch.inverse(d_y, out=d_xr)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    info = clocks.stop()
+    ms = a.elapsed_time(b) / steps
+    return {"steps": steps, "ms_per_step": ms, "seconds": ms * steps / 1000.0,
+            "value": d_x.shape[0] / (ms / 1000.0), "unit": "blocks/s", "clocks": info}
+
+
+def stress_leg(dev, stream, steps=4, name="hygt16x16_r3_s16", sample=65536):
+    """The large-transform workload (16x16 blocks, N = 256, 3 rounds, 16 sets,
+    16,777,216 blocks): integer forward + inverse through the bucketed path,
+    the FP32 path, and the dense 256 x 256 matrix transform (tcgen05 BF16 and
+    FP8 E4M3), each timed.  Deviations are reported on the first `sample`
+    blocks against the FP32 HyGT output (the parity tests hold that path
+    within 1e-5 of the FP64 oracle and measure every path against it)."""
+    import numpy as np
+    import torch
+    from paper_2505_21728_gb300 import hygt, workloads
+    w = workloads.get(name)
+    d = w.generate()
+    n, N = w.nblocks, w.N
+    plan = hygt.Plan(w.log2n, w.rounds, d["angle_idx"], d["perms"])
+    x = torch.from_numpy(d["x"]).to(dev)
+    s = torch.from_numpy(d["sets"].view(np.int16)).to(dev)
+    del d
+    b = hygt.Batch(plan, n, device=dev)
+    y = torch.empty((n, N), dtype=torch.int32, device=dev)
+    xr = torch.empty_like(x)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def int_step():
+        ev[0].record(stream)
+        b.build(s)
+        ev[1].record(stream)
+        b.forward(x, out=y)
+        ev[2].record(stream)
+        b.inverse(y, out=xr)
+        ev[3].record(stream)
+
+    int_step()
+    torch.cuda.synchronize(dev)
+    tb, tf, ti = [], [], []
+    for _ in range(steps):
+        int_step()
+        torch.cuda.synchronize(dev)
+        tb.append(ev[0].elapsed_time(ev[1]))
+        tf.append(ev[1].elapsed_time(ev[2]))
+        ti.append(ev[2].elapsed_time(ev[3]))
+    f_ms, i_ms, b_ms = statistics.mean(tf), statistics.mean(ti), statistics.mean(tb)
+    peak, kind = measured_peaks()
+    bpl = n * (6 * N + 2)
+    dom_ms = max(f_ms, i_ms)
+    out = {"workload": w.name, "description": w.description, "nblocks": n,
+           "int32": {"fwd_ms": f_ms, "inv_ms": i_ms, "schedule_ms": b_ms,
+                     "value": n / ((f_ms + i_ms + b_ms) / 1000.0), "unit": "blocks/s",
+                     "roofline": {"bound": "hbm", "achieved": bpl / (dom_ms / 1000.0) / 1e9,
+                                  "peak": peak, "unit": "GB/s",
+                                  "frac": bpl / (dom_ms / 1000.0) / 1e9 / peak,
+                                  "peak_source": kind, "bytes_per_launch": bpl,
+                                  "kernel": "hygt_batch_kernel<8,*>"}}}
+    yi_sample = y[:sample].to(torch.float64)
+    del y, xr
+    torch.cuda.empty_cache()
+
+    # FP32 path (float32 in and out, set indices given)
+    xf = x.to(torch.float32)
+    yf = torch.empty_like(xf)
+    xrf = torch.empty_like(xf)
+    plan.forward_f32(xf, s, out=yf)
+    plan.inverse_f32(yf, s, out=xrf)
+    torch.cuda.synchronize(dev)
+    ev[0].record(stream)
+    plan.forward_f32(xf, s, out=yf)
+    ev[1].record(stream)
+    plan.inverse_f32(yf, s, out=xrf)
+    ev[2].record(stream)
+    torch.cuda.synchronize(dev)
+    ff, fi = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    ref = yf[:sample].to(torch.float64)
+    scale = float(ref.abs().max())
+    out["fp32"] = {"fwd_ms": ff, "inv_ms": fi, "value": n / ((ff + fi) / 1000.0),
+                   "unit": "blocks/s",
+                   "roofline": {"bound": "hbm", "achieved": 8 * N * n / (ff / 1000.0) / 1e9,
+                                "peak": peak, "unit": "GB/s",
+                                "frac": 8 * N * n / (ff / 1000.0) / 1e9 / peak,
+                                "peak_source": kind}}
+    out["int32"]["max_abs_dev_vs_fp32_hygt"] = float((yi_sample - ref).abs().max())
+    del xf, yf, xrf
+    torch.cuda.empty_cache()
+
+    # dense 256 x 256 matrix transform of the same blocks (the HyGT's own matrices)
+    dk = hygt.DenseKLT(w.log2n, plan.dense_matrices()).build(s, n)
+    yd = torch.empty((n, N), dtype=torch.float32, device=dev)
+    for nm, kd in (("dense_bf16_tcgen05", hygt.DENSE_KLT_BF16),
+                   ("dense_fp8_e4m3_tcgen05", hygt.DENSE_KLT_FP8)):
+        dk.apply(x, kind=kd, out=yd)
+        torch.cuda.synchronize(dev)
+        ev[0].record(stream)
+        for _ in range(2):
+            dk.apply(x, kind=kd, out=yd)
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        ms = ev[0].elapsed_time(ev[1]) / 2
+        gbs = n * (6 * N + 4) / (ms / 1000.0) / 1e9
+        dev_max = float((yd[:sample].to(torch.float64) - ref).abs().max())
+        out[nm] = {"ms_per_apply": ms, "blocks_per_s_one_direction": n / (ms / 1000.0),
+                   "tflops": 2.0 * N * N * n / (ms / 1000.0) / 1e12,
+                   "max_abs_dev_vs_fp32_hygt": dev_max, "rel_dev": dev_max / scale,
+                   "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                                "frac": gbs / peak, "peak_source": kind}}
+    out["deviation_sample"] = ("first %d blocks, against the FP32 HyGT output (max |y| = %.1f)"
+                               % (sample, scale))
+    dk.close()
+    plan.close()
+    return out
+
+
+def coding_gain_leg(dev, stream, restarts=3, iters=200):
+    """The coding-gain angle fit of Sec. V on the correlated-patch workload:
+    seeded restarts of Adam on J = 1/(2N) sum log2 v_i, every iteration in the
+    library's kernels (forward, objective, diagonal backward, Adam)."""
+    import numpy as np
+    import torch
+    from paper_2505_21728_gb300 import fit, workloads
+    w = workloads.get_fit("hygt8x8_r4_fit")
+    x_np = w.patches()
+    f = fit.CodingGainFit(torch.from_numpy(x_np).to(dev), w.log2n, w.rounds)
+    f.run(w.theta0(), 3)  # warm-up
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    th, J, finals = f.fit(restarts, iters, lr=0.02, seed=0)
+    secs = time.perf_counter() - t0
+    # context: the KLT bound and the separable DCT-II of the same correlation
+    x64 = x_np.astype(np.float64)
+    phi = x64.T @ x64 / x64.shape[0]
+    bound = float(np.sum(np.log2(np.linalg.eigvalsh(phi))) / (2 * w.N))
+    k = np.arange(8)
+    D = np.sqrt(2.0 / 8) * np.cos(np.pi * (2 * k[None, :] + 1) * k[:, None] / 16)
+    D[0] /= np.sqrt(2.0)
+    T = np.kron(D, D)
+    J_dct = float(np.sum(np.log2(np.einsum("ia,ab,ib->i", T, phi, T))) / (2 * w.N))
+    f.close()
+    return {"workload": w.name, "nvec": w.nvec, "rounds": w.rounds,
+            "restarts": restarts, "iterations": iters,
+            "objective": "J = 1/(2N) sum log2 v_i (bits per coefficient, up to constants)",
+            "J_best": J, "J_restarts": finals, "J_klt_bound": bound, "J_dct2": J_dct,
+            "gap_to_klt_bits": J - bound, "gain_over_dct_bits": J_dct - J,
+            "iterations_per_s": restarts * iters / secs,
+            "ms_per_iteration": 1000.0 * secs / (restarts * iters)}
 
 
 def mixed_leg(dev, stream, steps=20, name="mixed_frame_2160p16"):
@@ -651,9 +833,159 @@ def e2e_leg(plan, x_np, s_np, N, dev, stream, world, steps=10):
                                   "chunks of 131,072 blocks on three streams"}
 
 
+# ---------------------------------------------------------------- kernel cases (ncu)
+def _int_case_data(name, nblocks):
+    import numpy as np
+    import torch
+    from paper_2505_21728_gb300 import hygt, workloads
+    w = workloads.get(name)
+    if nblocks:
+        w = workloads.truncated(w, nblocks)
+    d = w.generate()
+    plan = hygt.Plan(w.log2n, w.rounds, d["angle_idx"], d["perms"])
+    x = torch.from_numpy(d["x"]).cuda()
+    s = torch.from_numpy(d["sets"].view(np.int16)).cuda()
+    return w, d, plan, x, s
+
+
+def case_batch(args, name=DEFAULT_WORKLOAD):
+    """bucket + integer forward + integer inverse (8x8 blocks, 105 sets)"""
+    import torch
+    from paper_2505_21728_gb300 import hygt
+    w, d, plan, x, s = _int_case_data(name, args.nblocks)
+    b = hygt.Batch(plan, x.shape[0])
+    y = torch.empty((x.shape[0], w.N), dtype=torch.int32, device="cuda")
+    xr = torch.empty_like(x)
+
+    def run():
+        b.build(s)
+        b.forward(x, out=y)
+        b.inverse(y, out=xr)
+    return run
+
+
+def case_stress(args):
+    """the same on the 16x16 / 3-round / 16-set workload"""
+    return case_batch(args, name="hygt16x16_r3_s16")
+
+
+def case_direct(args):
+    """direct integer forward + inverse (no bucketing), 8x8 workload"""
+    import torch
+    w, d, plan, x, s = _int_case_data(DEFAULT_WORKLOAD, args.nblocks)
+    y = torch.empty((x.shape[0], w.N), dtype=torch.int32, device="cuda")
+    xr = torch.empty_like(x)
+
+    def run():
+        plan.forward(x, s, out=y)
+        plan.inverse(y, s, out=xr)
+    return run
+
+
+def case_mixed(args):
+    """mixed 4x4 / 8x8 / 16x16 frame batch, mixed forward + inverse"""
+    import numpy as np
+    import torch
+    from paper_2505_21728_gb300 import autotune, hygt, workloads
+    w = workloads.get_mixed("mixed_frame_2160p16", scale_down=args.scale_down)
+    classes = []
+    for cw in w.classes():
+        d = cw.generate()
+        plan = hygt.Plan(cw.log2n, cw.rounds, d["angle_idx"], d["perms"])
+        classes.append((plan, torch.from_numpy(d["x"]).cuda(),
+                        torch.from_numpy(d["sets"].view(np.int16)).cuda()))
+    mb = hygt.MixedBatch(classes)
+    mb.build()
+    if not args.no_tune:
+        autotune.tune_split(mb, reps=3, use_cache=False)
+
+    def run():
+        mb.forward()
+        mb.inverse()
+    return run
+
+
+def case_dense(args):
+    """dense matrix transform (tcgen05 BF16, FP8, int32) of the 8x8 blocks"""
+    import torch
+    from paper_2505_21728_gb300 import hygt
+    w, d, plan, x, s = _int_case_data(DEFAULT_WORKLOAD, args.nblocks)
+    dk = hygt.DenseKLT(w.log2n, plan.dense_matrices()).build(s, x.shape[0])
+    y = torch.empty((x.shape[0], w.N), dtype=torch.float32, device="cuda")
+    yi = torch.empty((x.shape[0], w.N), dtype=torch.int32, device="cuda")
+
+    def run():
+        dk.apply(x, kind=hygt.DENSE_KLT_BF16, out=y)
+        dk.apply(x, kind=hygt.DENSE_KLT_FP8, out=y)
+        dk.apply(x, kind=hygt.DENSE_KLT_INT, out=yi)
+    return run
+
+
+def case_grad(args):
+    """FP32 forward + backward, 8x8 patches, 4 rounds (fitting workload)"""
+    import numpy as np
+    import torch
+    from paper_2505_21728_gb300 import hygt, workloads
+    w = workloads.get_fit("hygt8x8_r4_fit")
+    n = args.nblocks or w.nvec
+    x = torch.from_numpy(w.patches(n)).cuda()
+    plan = hygt.Plan.from_theta(w.log2n, w.rounds, w.theta0().astype(np.float32))
+    mask = torch.zeros(w.N, device="cuda")
+    mask[w.keep:] = 2.0 / n
+    y = torch.empty_like(x)
+
+    def run():
+        plan.forward_f32(x, out=y)
+        plan.backward_f32(y, y * mask)
+    return run
+
+
+def case_coding_gain(args):
+    """one iteration of the coding-gain angle fit (forward, objective, diagonal
+    backward, Adam), 8x8 patches, 4 rounds"""
+    import numpy as np
+    import torch
+    from paper_2505_21728_gb300 import fit, workloads
+    w = workloads.get_fit("hygt8x8_r4_fit")
+    n = args.nblocks or w.nvec
+    f = fit.CodingGainFit(torch.from_numpy(w.patches(n)).cuda(), w.log2n, w.rounds)
+    th0 = w.theta0().astype(np.float32)
+
+    def run():
+        f.run(th0, 1)
+    return run
+
+
+CASES = {"batch": case_batch, "stress": case_stress, "direct": case_direct,
+         "mixed": case_mixed, "dense": case_dense, "grad": case_grad,
+         "coding_gain": case_coding_gain}
+
+
+def run_case(args):
+    import torch
+    from paper_2505_21728_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    run = CASES[args.case](args)
+    run()
+    run()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.reps):
+        run()
+    b.record()
+    torch.cuda.synchronize()
+    print("%s: %.4f ms per repetition" % (args.case, a.elapsed_time(b) / max(1, args.reps)))
+
+
 def main():
     args = parse_args()
     rank, world, local = dist_env()
+    if args.case:
+        run_case(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

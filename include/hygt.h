@@ -196,6 +196,101 @@ hygt_status hygt_backward_f32(hygt_plan plan, const float *d_y, const float *d_g
                               int *d_status);
 
 /*
+ * The coding-gain objective of Sec. V and the angle fit it drives.
+ *
+ * Sec. V rates a transform T by the variance vector v = diag(T Phi T^T) of
+ * its outputs (Phi the residuals' correlation matrix, Eq. 1) under the
+ * high-rate model R(D) = 1/2 log2(eps^2 sigma^2 / D) of Sec. V; the paper's
+ * optimiser searches the angles for the highest coding gain, with restarts,
+ * and leaves its details out.  Here Phi is the correlation of a batch of
+ * blocks, so v_i = (1/B) sum_b y_{b,i}^2 for the transformed batch y, and the
+ * objective is the average rate per coefficient up to constants,
+ *     J = 1/(2N) sum_i log2 v_i
+ * (minimising J maximises the coding gain mean(v) / geomean(v); an
+ * orthogonal T cannot go below the KLT's value, Eq. 2).
+ *
+ *   hygt_coding_gain_workspace_bytes  device bytes hygt_coding_gain_f32 needs
+ *        (0 for N = 2, nblocks < 1 or a null plan).
+ *   hygt_coding_gain_f32  from the FP32 outputs d_y (float [nblocks][N], one
+ *        class: every block counts) writes v to d_v (double [N]), J to d_J
+ *        (one double) and the weights w_i = 1 / (N ln 2 B v_i) to d_w
+ *        (float [N]), for which dJ/dy_{b,i} = w_i y_{b,i}.  A coefficient
+ *        with v_i = 0 gets w_i = 0 and makes J = -inf.  The sums are
+ *        deterministic (fixed order; FP32 over runs of 16 values, FP64
+ *        beyond).  Async on stream; the plan gives N only.
+ *   hygt_backward_diag_f32  the backward of any loss whose gradient with
+ *        respect to the outputs is diagonal, dL/dy_{b,i} = d_w[i] y_{b,i}
+ *        (the coding-gain objective with w from hygt_coding_gain_f32; the
+ *        energy-compaction loss (1/B) sum_{i>=K} y_i^2 with w_i = 2/B for
+ *        i >= K): the same kernel as hygt_backward_f32, which forms dL/dy in
+ *        registers instead of reading it.  d_gx (float [nblocks][N]) may be
+ *        null, and then dL/dx is not written: the call reads d_y alone.
+ *        Same workspace as hygt_backward_f32.
+ *   hygt_adam_step  one Adam step (Kingma and Ba) on n FP32 parameters
+ *        d_theta from the FP64 gradient d_grad, with FP32 moment buffers d_m
+ *        and d_v (zero before step 1); step counts from 1.  The paper names
+ *        no optimiser; this is the one the fit uses.
+ */
+size_t hygt_coding_gain_workspace_bytes(hygt_plan plan, int64_t nblocks);
+hygt_status hygt_coding_gain_f32(hygt_plan plan, const float *d_y, int64_t nblocks, double *d_v,
+                                 float *d_w, double *d_J, void *d_work, size_t work_bytes,
+                                 hygt_stream stream);
+hygt_status hygt_backward_diag_f32(hygt_plan plan, const float *d_y, const float *d_w,
+                                   float *d_gx, double *d_gtheta, const uint16_t *d_set,
+                                   int64_t nblocks, void *d_work, size_t work_bytes,
+                                   hygt_stream stream, int *d_status);
+hygt_status hygt_adam_step(float *d_theta, const double *d_grad, float *d_m, float *d_v,
+                           int64_t n, float lr, float beta1, float beta2, float eps, int step,
+                           hygt_stream stream);
+
+/*
+ * General PMPT with explicit index vectors (Sec. III, Eq. 5; Sec. IV,
+ * Eq. 7-9).  Each pass of each set is a parallel-Givens matrix over an
+ * arbitrary cover of 0..N-1 by N/2 disjoint pairs (m_j, n_j) with one angle
+ * per pair -- the construction the HyGT specialises by taking the pairs
+ * from the hypercube, which saves the index storage.  The forward applies
+ * pass 0 first; the inverse runs the passes in reverse with negated angles.
+ * Rotation of a pair: y_m = c a + s b, y_n = -s a + c b; integer plans
+ * round every output half up, floor((. + 2^(f-1)) / 2^f), in int32, and
+ * the inverse saturates to int16.
+ *
+ *   hygt_pmpt_create  n even, 2..256; passes 1..4096; num_sets 1..65535;
+ *        m_idx, n_idx host uint16 [num_sets][passes][n/2], every pass a cover
+ *        of 0..n-1 (each index exactly once), else HYGT_ERR_ARG.  Exactly one
+ *        of angle_idx (host uint8, same layout: theta = 2 pi q / 2^angle_bits,
+ *        integer and FP32 calls) and theta (host float radians: FP32 calls
+ *        only) is non-null.  Synchronous; allocates the plan's device tables
+ *        on the current device.
+ *   hygt_pmpt_forward / hygt_pmpt_inverse  integer (int16 -> int32 /
+ *        int32 -> int16 saturated), d_* device [nblocks][n], 4-byte aligned;
+ *        d_set (uint16 [nblocks] or null: set 0), 0xFFFF = identity, other
+ *        indices >= num_sets zero the block and write HYGT_ERR_SET_INDEX to
+ *        d_status (nullable, first error wins).  Async on stream.
+ *   hygt_pmpt_forward_f32 / hygt_pmpt_inverse_f32  the same in FP32.
+ *   hygt_pmpt_param_bytes  memory of the parameters at one byte per angle
+ *        and one byte per index: 3 bytes per pair (the HyGT needs 1).
+ */
+typedef struct hygt_pmpt_s *hygt_pmpt;
+hygt_status hygt_pmpt_create(hygt_pmpt *out, int n, int passes, int num_sets,
+                             const uint8_t *angle_idx, const float *theta,
+                             const uint16_t *m_idx, const uint16_t *n_idx, int angle_bits,
+                             int frac_bits);
+void hygt_pmpt_destroy(hygt_pmpt pmpt);
+size_t hygt_pmpt_param_bytes(int n, int passes, int num_sets);
+hygt_status hygt_pmpt_forward(hygt_pmpt pmpt, const int16_t *d_x, int32_t *d_y,
+                              const uint16_t *d_set, int64_t nblocks, hygt_stream stream,
+                              int *d_status);
+hygt_status hygt_pmpt_inverse(hygt_pmpt pmpt, const int32_t *d_y, int16_t *d_x,
+                              const uint16_t *d_set, int64_t nblocks, hygt_stream stream,
+                              int *d_status);
+hygt_status hygt_pmpt_forward_f32(hygt_pmpt pmpt, const float *d_x, float *d_y,
+                                  const uint16_t *d_set, int64_t nblocks, hygt_stream stream,
+                                  int *d_status);
+hygt_status hygt_pmpt_inverse_f32(hygt_pmpt pmpt, const float *d_y, float *d_x,
+                                  const uint16_t *d_set, int64_t nblocks, hygt_stream stream,
+                                  int *d_status);
+
+/*
  * Mixed block sizes in one persistent launch.  The paper's codec applies
  * 4x4 (N = 16) and 8x8 (N = 64) secondary transforms (Sec. VI); a frame
  * tiled into 4x4, 8x8 and 16x16 blocks gives one batch per block size, each

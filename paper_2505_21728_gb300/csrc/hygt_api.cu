@@ -16,6 +16,7 @@
 #include "hygt_batch.cuh"
 #include "hygt_dense.cuh"
 #include "hygt_f32u.cuh"
+#include "hygt_fit.cuh"
 #include "hygt_grad.cuh"
 #include "hygt_mixed.cuh"
 #include "hygt_launch.cuh"
@@ -720,13 +721,12 @@ size_t hygt_backward_workspace_bytes(hygt_plan plan, int64_t nblocks) {
   return w.threads == 0 ? 0 : w.total;
 }
 
-hygt_status hygt_backward_f32(hygt_plan plan, const float* d_y, const float* d_gy, float* d_gx,
-                              double* d_gtheta, const uint16_t* d_set, int64_t nblocks,
-                              void* d_work, size_t work_bytes, hygt_stream stream, int* d_status) {
-  if (!plan || nblocks < 0 || nblocks > kBatchMaxBlocks || !d_gtheta) return HYGT_ERR_ARG;
-  hygt_status s = check_io(plan, d_y, d_gx, nblocks);
-  if (s != HYGT_OK) return s;
-  if (nblocks > 0 && (!d_gy || !aligned16(d_gy))) return HYGT_ERR_ARG;
+// The backward of hygt_backward_f32 (d_gy given) and of hygt_backward_diag_f32
+// (d_gy null: dL/dy = w * y, d_gx optional).
+static hygt_status backward_common(hygt_plan plan, const float* d_y, const float* d_gy,
+                                   const float* d_w, float* d_gx, double* d_gtheta,
+                                   const uint16_t* d_set, int64_t nblocks, void* d_work,
+                                   size_t work_bytes, hygt_stream stream, int* d_status) {
   const int angles = plan_angles(plan);
   const GradWork w = grad_work(plan, nblocks);
   if (w.threads == 0) return HYGT_ERR_UNSUPPORTED;
@@ -742,6 +742,7 @@ hygt_status hygt_backward_f32(hygt_plan plan, const float* d_y, const float* d_g
   gl.smem = w.smem;
   gl.p.y = d_y;
   gl.p.gy = d_gy;
+  gl.p.w = d_w;
   gl.p.gx = d_gx;
   gl.p.nblocks = nblocks;
   gl.p.tab = static_cast<const float2*>(plan->d_tab_f32);
@@ -766,6 +767,70 @@ hygt_status hygt_backward_f32(hygt_plan plan, const float* d_y, const float* d_g
     gl.p.tmax = L.tmax;
   }
   return to_status(hygt::launch_grad(gl, d_gtheta, (cudaStream_t)stream));
+}
+
+hygt_status hygt_backward_f32(hygt_plan plan, const float* d_y, const float* d_gy, float* d_gx,
+                              double* d_gtheta, const uint16_t* d_set, int64_t nblocks,
+                              void* d_work, size_t work_bytes, hygt_stream stream, int* d_status) {
+  if (!plan || nblocks < 0 || nblocks > kBatchMaxBlocks || !d_gtheta) return HYGT_ERR_ARG;
+  hygt_status s = check_io(plan, d_y, d_gx, nblocks);
+  if (s != HYGT_OK) return s;
+  if (nblocks > 0 && (!d_gy || !aligned16(d_gy))) return HYGT_ERR_ARG;
+  return backward_common(plan, d_y, d_gy, nullptr, d_gx, d_gtheta, d_set, nblocks, d_work,
+                         work_bytes, stream, d_status);
+}
+
+hygt_status hygt_backward_diag_f32(hygt_plan plan, const float* d_y, const float* d_w,
+                                   float* d_gx, double* d_gtheta, const uint16_t* d_set,
+                                   int64_t nblocks, void* d_work, size_t work_bytes,
+                                   hygt_stream stream, int* d_status) {
+  if (!plan || nblocks < 0 || nblocks > kBatchMaxBlocks || !d_gtheta || !d_w) return HYGT_ERR_ARG;
+  if (nblocks > 0 && (!d_y || !aligned16(d_y))) return HYGT_ERR_ARG;
+  if (d_gx && (!aligned16(d_gx) || d_gx == (float*)d_y)) return HYGT_ERR_ARG;
+  return backward_common(plan, d_y, nullptr, d_w, d_gx, d_gtheta, d_set, nblocks, d_work,
+                         work_bytes, stream, d_status);
+}
+
+size_t hygt_coding_gain_workspace_bytes(hygt_plan plan, int64_t nblocks) {
+  if (!plan || nblocks < 1 || nblocks > kBatchMaxBlocks || plan->log2n < 2) return 0;
+  const long long n4 = (long long)nblocks * (1 << plan->log2n) / 4;
+  return (size_t)hygt::moments_grid(n4) * (size_t)(1 << plan->log2n) * sizeof(double);
+}
+
+hygt_status hygt_coding_gain_f32(hygt_plan plan, const float* d_y, int64_t nblocks, double* d_v,
+                                 float* d_w, double* d_J, void* d_work, size_t work_bytes,
+                                 hygt_stream stream) {
+  if (!plan || nblocks < 1 || nblocks > kBatchMaxBlocks || !d_y || !aligned16(d_y) || !d_v ||
+      !d_w || !d_J)
+    return HYGT_ERR_ARG;
+  if (plan->log2n < 2) return HYGT_ERR_UNSUPPORTED;
+  const size_t need = hygt_coding_gain_workspace_bytes(plan, nblocks);
+  if (!d_work || !aligned16(d_work) || work_bytes < need) return HYGT_ERR_ARG;
+  const int n = 1 << plan->log2n;
+  const long long n4 = (long long)nblocks * n / 4;
+  const int grid = hygt::moments_grid(n4);
+  double* partials = static_cast<double*>(d_work);
+  hygt::hygt_moments_kernel<<<grid, hygt::kMomentThreads, 0, (cudaStream_t)stream>>>(
+      reinterpret_cast<const float4*>(d_y), n4, n, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return to_status(e);
+  hygt::hygt_coding_gain_finish<<<1, n, 0, (cudaStream_t)stream>>>(partials, grid, n, nblocks,
+                                                                   d_v, d_w, d_J);
+  return to_status(cudaGetLastError());
+}
+
+hygt_status hygt_adam_step(float* d_theta, const double* d_grad, float* d_m, float* d_v,
+                           int64_t n, float lr, float beta1, float beta2, float eps, int step,
+                           hygt_stream stream) {
+  if (!d_theta || !d_grad || !d_m || !d_v || n < 1 || step < 1 || !(lr > 0.f) ||
+      !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+    return HYGT_ERR_ARG;
+  const float corr1 = 1.f - (float)std::pow((double)beta1, (double)step);
+  const float corr2 = 1.f - (float)std::pow((double)beta2, (double)step);
+  hygt::hygt_adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+      d_theta, d_grad, d_m, d_v, n, lr, beta1, beta2, eps, corr1 > 0.f ? corr1 : 1.f,
+      corr2 > 0.f ? corr2 : 1.f);
+  return to_status(cudaGetLastError());
 }
 
 struct dense_klt_s {

@@ -40,8 +40,9 @@ constexpr int kGradThreads = 384;
 
 struct GradParams {
   const float* y;       // [B][N] forward output
-  const float* gy;      // [B][N] dL/dy
-  float* gx;            // [B][N] dL/dx
+  const float* gy;      // [B][N] dL/dy, or nullptr: dL/dy = w * y (w below)
+  const float* w;       // [N] per-coefficient weights when gy is nullptr
+  float* gx;            // [B][N] dL/dx, or nullptr: not written
   long long nblocks;
   const float2* tab;    // (cos, sin) per pair, [S][R][k][N/2]
   const uint8_t* perm;  // [S][R][N] or nullptr
@@ -266,6 +267,11 @@ __global__ void __launch_bounds__(kGradThreads, 1) hygt_grad_kernel(GradParams p
   const long long t0 = min(ntasks, ((long long)blockIdx.x * warps + warp) * chunk);
   const long long t1 = min(ntasks, t0 + chunk);
 
+  // diagonal objective: this lane's E weights (dL/dy_e = w_e y_e)
+  float wl[E];
+#pragma unroll
+  for (int i = 0; i < E; ++i) wl[i] = p.gy ? 0.f : __ldg(p.w + lane * E + i);
+
   int bucket = 0, bucket_end = 0;
   for (long long t = t0; t < t1; ++t) {
     const long long slot = t * G;
@@ -283,7 +289,12 @@ __global__ void __launch_bounds__(kGradThreads, 1) hygt_grad_kernel(GradParams p
       valid[k] = b[k] >= 0 && b[k] < p.nblocks;
       if (valid[k]) {
         load_f32<E>(p.y + b[k] * N + lane * E, v[k]);
-        load_f32<E>(p.gy + b[k] * N + lane * E, g[k]);
+        if (p.gy) {
+          load_f32<E>(p.gy + b[k] * N + lane * E, g[k]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < E; ++i) g[k][i] = wl[i] * v[k][i];
+        }
       } else {
 #pragma unroll
         for (int i = 0; i < E; ++i) v[k][i] = g[k][i] = 0.f;
@@ -321,9 +332,11 @@ __global__ void __launch_bounds__(kGradThreads, 1) hygt_grad_kernel(GradParams p
         if (valid[k] && lane == 0 && p.status) atomicCAS(p.status, 0, 4);
       }
     }  // skip bucket (S): identity, dL/dx = dL/dy
+    if (p.gx) {
 #pragma unroll
-    for (int k = 0; k < K; ++k)
-      if (valid[k]) store_f32<E>(p.gx + b[k] * N + lane * E, g[k]);
+      for (int k = 0; k < K; ++k)
+        if (valid[k]) store_f32<E>(p.gx + b[k] * N + lane * E, g[k]);
+    }
   }
   __syncthreads();
   // CTA partial: sum of all (warp, lane group) rows, in FP64, fixed order

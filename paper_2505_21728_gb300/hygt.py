@@ -82,6 +82,26 @@ def _load() -> ctypes.CDLL:
     L.hygt_backward_workspace_bytes.restype = ctypes.c_size_t
     L.hygt_backward_f32.argtypes = [P, P, P, P, P, P, i64, P, ctypes.c_size_t, P, P]
     L.hygt_backward_f32.restype = i32
+    L.hygt_backward_diag_f32.argtypes = [P, P, P, P, P, P, i64, P, ctypes.c_size_t, P, P]
+    L.hygt_backward_diag_f32.restype = i32
+    L.hygt_coding_gain_workspace_bytes.argtypes = [P, i64]
+    L.hygt_coding_gain_workspace_bytes.restype = ctypes.c_size_t
+    L.hygt_coding_gain_f32.argtypes = [P, P, i64, P, P, P, P, ctypes.c_size_t, P]
+    L.hygt_coding_gain_f32.restype = i32
+    f32 = ctypes.c_float
+    L.hygt_adam_step.argtypes = [P, P, P, P, i64, f32, f32, f32, f32, i32, P]
+    L.hygt_adam_step.restype = i32
+    L.hygt_pmpt_create.argtypes = [ctypes.POINTER(P), i32, i32, i32, P, P, P, P, i32, i32]
+    L.hygt_pmpt_create.restype = i32
+    L.hygt_pmpt_destroy.argtypes = [P]
+    L.hygt_pmpt_destroy.restype = None
+    L.hygt_pmpt_param_bytes.argtypes = [i32, i32, i32]
+    L.hygt_pmpt_param_bytes.restype = ctypes.c_size_t
+    for name in ("hygt_pmpt_forward", "hygt_pmpt_inverse", "hygt_pmpt_forward_f32",
+                 "hygt_pmpt_inverse_f32"):
+        f = getattr(L, name)
+        f.argtypes = [P, P, P, P, i64, P, P]
+        f.restype = i32
     L.dense_klt_create.argtypes = [ctypes.POINTER(P), i32, i32, P, i32]
     L.dense_klt_create.restype = i32
     L.dense_klt_destroy.argtypes = [P]
@@ -220,6 +240,62 @@ def hygt_backward_f32(plan, d_y, d_gy, d_gx, d_gtheta, d_set, nblocks, d_work, w
                       stream, d_status):
     return int(_lib.hygt_backward_f32(plan, d_y, d_gy, d_gx, d_gtheta, d_set, nblocks, d_work,
                                       work_bytes, stream, d_status))
+
+
+def hygt_backward_diag_f32(plan, d_y, d_w, d_gx, d_gtheta, d_set, nblocks, d_work, work_bytes,
+                           stream, d_status):
+    return int(_lib.hygt_backward_diag_f32(plan, d_y, d_w, d_gx, d_gtheta, d_set, nblocks,
+                                           d_work, work_bytes, stream, d_status))
+
+
+def hygt_coding_gain_workspace_bytes(plan, nblocks):
+    return int(_lib.hygt_coding_gain_workspace_bytes(plan, nblocks))
+
+
+def hygt_coding_gain_f32(plan, d_y, nblocks, d_v, d_w, d_J, d_work, work_bytes, stream):
+    return int(_lib.hygt_coding_gain_f32(plan, d_y, nblocks, d_v, d_w, d_J, d_work, work_bytes,
+                                         stream))
+
+
+def hygt_adam_step(d_theta, d_grad, d_m, d_v, n, lr, beta1, beta2, eps, step, stream):
+    return int(_lib.hygt_adam_step(d_theta, d_grad, d_m, d_v, n, lr, beta1, beta2, eps, step,
+                                   stream))
+
+
+def hygt_pmpt_create(n, passes, num_sets, angle_idx, theta, m_idx, n_idx, angle_bits=8,
+                     frac_bits=8):
+    a = None if angle_idx is None else np.ascontiguousarray(angle_idx, dtype=np.uint8)
+    t = None if theta is None else np.ascontiguousarray(theta, dtype=np.float32)
+    mi = np.ascontiguousarray(m_idx, dtype=np.uint16)
+    ni = np.ascontiguousarray(n_idx, dtype=np.uint16)
+    h = ctypes.c_void_p()
+    st = _lib.hygt_pmpt_create(ctypes.byref(h), n, passes, num_sets, _np_ptr(a), _np_ptr(t),
+                               _np_ptr(mi), _np_ptr(ni), angle_bits, frac_bits)
+    return int(st), h.value
+
+
+def hygt_pmpt_destroy(pm):
+    _lib.hygt_pmpt_destroy(pm)
+
+
+def hygt_pmpt_param_bytes(n, passes, num_sets):
+    return int(_lib.hygt_pmpt_param_bytes(n, passes, num_sets))
+
+
+def hygt_pmpt_forward(pm, d_x, d_y, d_set, nblocks, stream, d_status):
+    return int(_lib.hygt_pmpt_forward(pm, d_x, d_y, d_set, nblocks, stream, d_status))
+
+
+def hygt_pmpt_inverse(pm, d_y, d_x, d_set, nblocks, stream, d_status):
+    return int(_lib.hygt_pmpt_inverse(pm, d_y, d_x, d_set, nblocks, stream, d_status))
+
+
+def hygt_pmpt_forward_f32(pm, d_x, d_y, d_set, nblocks, stream, d_status):
+    return int(_lib.hygt_pmpt_forward_f32(pm, d_x, d_y, d_set, nblocks, stream, d_status))
+
+
+def hygt_pmpt_inverse_f32(pm, d_y, d_x, d_set, nblocks, stream, d_status):
+    return int(_lib.hygt_pmpt_inverse_f32(pm, d_y, d_x, d_set, nblocks, stream, d_status))
 
 
 def dense_klt_create(log2n, num_sets, K, frac_bits=8):
@@ -431,6 +507,78 @@ class Plan:
             out = torch.empty(y.shape, dtype=torch.float32, device=y.device)
         return self._call(hygt_inverse_f32, "hygt_inverse_f32", y, out, sets, torch.float32,
                           torch.float32, status, stream)
+
+
+class PMPT:
+    """A general PMPT plan (explicit pair covers; hygt_pmpt_create).
+
+    ``PMPT(n, passes, m_idx, n_idx, angle_idx=...)`` builds an integer plan
+    (its FP32 calls use the same angles); ``theta=...`` an FP32-only plan.
+    """
+
+    def __init__(self, n, passes, m_idx, n_idx, angle_idx=None, theta=None, angle_bits=8,
+                 frac_bits=8):
+        self.N, self.passes = int(n), int(passes)
+        ref = angle_idx if angle_idx is not None else theta
+        self.num_sets = int(np.asarray(ref).size // (self.passes * (self.N // 2)))
+        st, h = hygt_pmpt_create(self.N, self.passes, self.num_sets, angle_idx, theta, m_idx,
+                                 n_idx, angle_bits, frac_bits)
+        _check(st, "hygt_pmpt_create")
+        self.handle = h
+
+    def _call(self, fn, name, x, out_dtype, sets, status, stream):
+        import torch
+        nb = x.shape[0]
+        px = _dptr(x, x.dtype, self.N, "input")
+        out = torch.empty((nb, self.N), dtype=out_dtype, device=x.device)
+        ps = None
+        if sets is not None:
+            if sets.numel() != nb:
+                raise ValueError("sets must have one entry per block")
+            ps = _dptr(sets, torch.int16 if sets.dtype == torch.int16 else torch.uint16, None,
+                       "sets")
+        pst = None if status is None else _dptr(status, torch.int32, None, "status")
+        _check(fn(self.handle, px, out.data_ptr(), ps, nb, _stream_handle(stream), pst), name)
+        return out
+
+    def forward(self, x, sets=None, status=None, stream=None):
+        import torch
+        if x.dtype != torch.int16:
+            raise TypeError("x must be int16")
+        return self._call(hygt_pmpt_forward, "hygt_pmpt_forward", x, torch.int32, sets, status,
+                          stream)
+
+    def inverse(self, y, sets=None, status=None, stream=None):
+        import torch
+        if y.dtype != torch.int32:
+            raise TypeError("y must be int32")
+        return self._call(hygt_pmpt_inverse, "hygt_pmpt_inverse", y, torch.int16, sets, status,
+                          stream)
+
+    def forward_f32(self, x, sets=None, status=None, stream=None):
+        import torch
+        if x.dtype != torch.float32:
+            raise TypeError("x must be float32")
+        return self._call(hygt_pmpt_forward_f32, "hygt_pmpt_forward_f32", x, torch.float32,
+                          sets, status, stream)
+
+    def inverse_f32(self, y, sets=None, status=None, stream=None):
+        import torch
+        if y.dtype != torch.float32:
+            raise TypeError("y must be float32")
+        return self._call(hygt_pmpt_inverse_f32, "hygt_pmpt_inverse_f32", y, torch.float32,
+                          sets, status, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            hygt_pmpt_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class HostPipe:

@@ -13,6 +13,7 @@ sets per block size and the int16 residual range the paper implies.
 from __future__ import annotations
 
 import math
+import os
 
 import numpy as np
 
@@ -36,19 +37,36 @@ def laplacian_blocks(nblocks: int, n: int, scale: float, lo: int, hi: int, seed:
     if count is None:
         count = nblocks - first_block
     out = np.empty((count, n), np.int16)
-    b = first_block
     end = first_block + count
+    spans = []  # (chunk, first row in the chunk, rows)
+    b = first_block
     while b < end:
         ch = b // CHUNK
         c0 = ch * CHUNK
-        c1 = min(c0 + CHUNK, nblocks)
+        s0, s1 = b - c0, min(end, min(c0 + CHUNK, nblocks)) - c0
+        spans.append((ch, s0, s1 - s0))
+        b = c0 + s1
+
+    def draw(span):
+        ch, s0, rows = span
+        c0 = ch * CHUNK
         rng = _chunk_rng(seed, ch, 1)
-        v = rng.laplace(0.0, scale, size=(c1 - c0, n))
+        v = rng.laplace(0.0, scale, size=(min(c0 + CHUNK, nblocks) - c0, n))
         v = np.sign(v) * np.floor(np.abs(v) + 0.5)
         np.clip(v, lo, hi, out=v)
-        s0, s1 = b - c0, min(end, c1) - c0
-        out[b - first_block:b - first_block + (s1 - s0)] = v[s0:s1].astype(np.int16)
-        b = c0 + s1
+        o = c0 + s0 - first_block
+        out[o:o + rows] = v[s0:s0 + rows].astype(np.int16)
+
+    # chunks are independent (own generator each): draw them on threads
+    # (numpy releases the GIL while it fills arrays); the result does not
+    # depend on the thread count
+    if len(spans) > 4:
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+            list(ex.map(draw, spans))
+    else:
+        for sp in spans:
+            draw(sp)
     return out
 
 

@@ -146,3 +146,43 @@ def test_dense_bad_set_and_empty(gpu, orc):
         st = torch.zeros(1, dtype=torch.int32, device="cuda")
         y = d.apply(_t(x), kind=kind, status=st).cpu().numpy()
         assert int(st.item()) == 4 and np.all(y[10] == 0)
+
+
+def test_stress_workload_paths_error_vs_fp64(gpu, orc, capsys):
+    """The large-transform workload (16x16 blocks, N = 256, 3 rounds, 16 sets):
+    every path's error against the FP64 oracle on its first 65,536 blocks --
+    the exact integer HyGT (rounding per pass, within the integer-vs-float
+    bound), the FP32 HyGT (<= 1e-5 of max |y|), and the dense 256 x 256
+    matrix transform with BF16 and FP8 E4M3 tensor cores (within the
+    precision of their operands).  The errors are printed."""
+    import torch
+    from paper_2505_21728_gb300 import workloads
+    w = workloads.truncated(workloads.get("hygt16x16_r3_s16"), 65536)
+    d = w.generate()
+    N, n = w.N, w.nblocks
+    theta = inputs.theta_from_indices(d["angle_idx"])
+    ye, st = orc.fwd_f64(d["x"].astype(np.float64), theta, w.log2n, w.rounds, d["perms"],
+                         d["sets"])
+    assert st == 0
+    scale = np.max(np.abs(ye))
+    plan = gpu.Plan(w.log2n, w.rounds, d["angle_idx"], d["perms"])
+    x, s = _t(d["x"]), _t(d["sets"])
+    y_int = gpu.Batch(plan, n).build(s).forward(x).cpu().numpy().astype(np.float64)
+    y_f32 = plan.forward_f32(x.float(), s).cpu().numpy().astype(np.float64)
+    dk = gpu.DenseKLT(w.log2n, plan.dense_matrices()).build(s, n)
+    y_bf16 = dk.apply(x, kind=gpu.DENSE_KLT_BF16).cpu().numpy().astype(np.float64)
+    y_fp8 = dk.apply(x, kind=gpu.DENSE_KLT_FP8).cpu().numpy().astype(np.float64)
+    torch.cuda.synchronize()
+    errs = {k: float(np.max(np.abs(v - ye))) for k, v in
+            (("int32", y_int), ("fp32", y_f32), ("bf16", y_bf16), ("fp8_e4m3", y_fp8))}
+    with capsys.disabled():
+        print("\nstress 16x16 max|y|=%.1f; max abs error vs FP64: %s" % (
+            scale, ", ".join("%s %.4g (%.2e rel)" % (k, e, e / scale) for k, e in errs.items())))
+    # integer: table quantisation (|c - 256 cos| <= 1/2) and 1/2 per pass, 24 passes
+    assert errs["int32"] <= 24 * 0.5 + 24 * scale / 256.0
+    assert errs["fp32"] <= 1e-5 * scale
+    assert errs["bf16"] <= 2.0 ** -7 * 4 * scale      # BF16 operands (8-bit mantissa)
+    assert errs["fp8_e4m3"] <= 2.0 ** -3 * 4 * scale  # E4M3 operands (3-bit mantissa)
+    assert errs["fp8_e4m3"] > errs["bf16"] > errs["fp32"]
+    dk.close()
+    plan.close()
