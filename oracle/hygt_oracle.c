@@ -766,8 +766,10 @@ int oracle_dct_matrix(int log2m, int32_t *C, double *D) {
 }
 
 /* One separable stage along rows (dim 0) or columns (dim 1) of an M x M
-   block held row-major in v; transpose selects C^T (inverse). */
-static void primary_stage(int M, const int32_t *C, int dim, int transpose, int64_t *v) {
+   block held row-major in v; transpose selects C^T (inverse).  Returns
+   OR_ERR_OVERFLOW when a sum leaves int32 (the range the integer
+   arithmetic is specified for, as for the HyGT butterflies). */
+static int primary_stage(int M, const int32_t *C, int dim, int transpose, int64_t *v) {
   int64_t half = (int64_t)1 << (OR_PRIMARY_BITS - 1);
   int64_t line[OR_MAX_M], out[OR_MAX_M];
   for (int l = 0; l < M; ++l) {
@@ -776,6 +778,7 @@ static void primary_stage(int M, const int32_t *C, int dim, int transpose, int64
       int64_t acc = half;
       for (int i = 0; i < M; ++i)
         acc += (int64_t)(transpose ? C[i * M + k] : C[k * M + i]) * line[i];
+      if (!fits_i32(acc)) return OR_ERR_OVERFLOW;
       out[k] = floor_div_pow2(acc, OR_PRIMARY_BITS);
     }
     for (int k = 0; k < M; ++k) {
@@ -783,6 +786,7 @@ static void primary_stage(int M, const int32_t *C, int dim, int transpose, int64
       else v[k * M + l] = out[k];
     }
   }
+  return OR_OK;
 }
 
 static int secondary_run(int inverse, int log2m, int log2n, int rounds, int num_sets,
@@ -811,8 +815,8 @@ static int secondary_run(int inverse, int log2m, int log2n, int rounds, int num_
       v[i] = inverse ? ((const int32_t *)in)[b * MM + i] : ((const int16_t *)in)[b * MM + i];
     if (set != OR_SKIP && set >= (unsigned)num_sets) code = OR_ERR_SET;
     if (code == OR_OK && !inverse) {
-      primary_stage(M, C, 0, 0, v); /* rows */
-      primary_stage(M, C, 1, 0, v); /* columns */
+      code = primary_stage(M, C, 0, 0, v);             /* rows */
+      if (code == OR_OK) code = primary_stage(M, C, 1, 0, v); /* columns */
     }
     if (code == OR_OK && set != OR_SKIP) {
       for (int r = 0; r < s; ++r)
@@ -825,8 +829,8 @@ static int secondary_run(int inverse, int log2m, int log2n, int rounds, int num_
         for (int c = 0; c < s; ++c) v[r * M + c] = sub[r * s + c];
     }
     if (code == OR_OK && inverse) {
-      primary_stage(M, C, 1, 1, v); /* columns */
-      primary_stage(M, C, 0, 1, v); /* rows */
+      code = primary_stage(M, C, 1, 1, v);             /* columns */
+      if (code == OR_OK) code = primary_stage(M, C, 0, 1, v); /* rows */
     }
     if (code == OR_OK) {
       for (int i = 0; i < MM; ++i)
