@@ -244,6 +244,39 @@ hygt_status hygt_adam_step(float *d_theta, const double *d_grad, float *d_m, flo
                            hygt_stream stream);
 
 /*
+ * Secondary-transform pipeline (Sec. VI): the HyGT used as a secondary
+ * transform on the low-frequency coefficients of a separable primary
+ * transform -- a 4x4 HyGT (N = 16) for 4x4 blocks, an 8x8 HyGT (N = 64) on
+ * the top-left 8x8 coefficients of 8x8, 16x16 and 32x32 blocks -- fused
+ * with the primary in one kernel.  The paper does not fix the primary; it
+ * is the orthonormal 2-D DCT-II in integer arithmetic with the HyGT's
+ * precision: C = round(256 D), D[k][i] = a_k cos(pi (2i + 1) k / (2M)),
+ * a_0 = sqrt(1/M), a_k = sqrt(2/M); each 1-D stage rounds half up,
+ * floor((sum_i C[k][i] x_i + 128) / 256), rows then columns (the inverse:
+ * C^T, columns then rows, then int16 saturation).  The sub-block is the
+ * HyGT's vector in raster order (row-major); the other coefficients pass
+ * through.
+ *
+ *   hygt_secondary_forward  int16 residual blocks d_x [nblocks][M*M]
+ *        (raster, M = 2^log2m, log2m 2..5) -> int32 coefficients d_y
+ *        [nblocks][M*M].  plan: an integer plan with log2n = 4 for
+ *        log2m = 2 and log2n = 6 otherwise (else HYGT_ERR_ARG).  d_set as
+ *        for hygt_forward: 0xFFFF = no secondary transform (primary only);
+ *        other indices >= num_sets zero the block and write
+ *        HYGT_ERR_SET_INDEX to d_status.  Pointers 16-byte aligned; async
+ *        on stream.  Exact in int32 for every int16 input.
+ *   hygt_secondary_inverse  int32 coefficients -> int16 blocks (inverse HyGT
+ *        on the sub-block, then the inverse DCT-II); coefficients as the
+ *        forward produces them keep every sum within int32.
+ */
+hygt_status hygt_secondary_forward(hygt_plan plan, int log2m, const int16_t *d_x, int32_t *d_y,
+                                   const uint16_t *d_set, int64_t nblocks, hygt_stream stream,
+                                   int *d_status);
+hygt_status hygt_secondary_inverse(hygt_plan plan, int log2m, const int32_t *d_y, int16_t *d_x,
+                                   const uint16_t *d_set, int64_t nblocks, hygt_stream stream,
+                                   int *d_status);
+
+/*
  * General PMPT with explicit index vectors (Sec. III, Eq. 5; Sec. IV,
  * Eq. 7-9).  Each pass of each set is a parallel-Givens matrix over an
  * arbitrary cover of 0..N-1 by N/2 disjoint pairs (m_j, n_j) with one angle

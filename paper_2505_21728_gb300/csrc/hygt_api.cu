@@ -17,6 +17,7 @@
 #include "hygt_dense.cuh"
 #include "hygt_f32u.cuh"
 #include "hygt_fit.cuh"
+#include "hygt_secondary.cuh"
 #include "hygt_grad.cuh"
 #include "hygt_mixed.cuh"
 #include "hygt_launch.cuh"
@@ -789,6 +790,58 @@ hygt_status hygt_backward_diag_f32(hygt_plan plan, const float* d_y, const float
   if (d_gx && (!aligned16(d_gx) || d_gx == (float*)d_y)) return HYGT_ERR_ARG;
   return backward_common(plan, d_y, nullptr, d_w, d_gx, d_gtheta, d_set, nblocks, d_work,
                          work_bytes, stream, d_status);
+}
+
+// The secondary-transform pipeline (hygt_secondary.cuh): checks, the
+// primary matrix C = round(256 D) of the orthonormal DCT-II, the launch.
+static hygt_status secondary_run(int inverse, hygt_plan plan, int log2m, const void* in,
+                                 void* out, const uint16_t* d_set, int64_t nblocks,
+                                 hygt_stream stream, int* d_status) {
+  if (!plan || nblocks < 0 || nblocks > kBatchMaxBlocks) return HYGT_ERR_ARG;
+  if (plan->is_float) return HYGT_ERR_UNSUPPORTED;
+  if (log2m < 2 || log2m > 5) return HYGT_ERR_ARG;
+  // 4x4 blocks take a 4x4 secondary (N = 16), larger blocks an 8x8 one (N = 64)
+  if (plan->log2n != (log2m == 2 ? 4 : 6)) return HYGT_ERR_ARG;
+  if (nblocks == 0) return HYGT_OK;
+  if (!in || !out || !aligned16(in) || !aligned16(out)) return HYGT_ERR_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HYGT_ERR_CUDA;
+  if (dev != plan->device) return HYGT_ERR_ARG;
+  hygt::SecondaryParams p{};
+  const int M = 1 << log2m;
+  for (int k = 0; k < M; ++k) {
+    const double a = k == 0 ? std::sqrt(1.0 / M) : std::sqrt(2.0 / M);
+    for (int i = 0; i < M; ++i)
+      p.C[k * M + i] = (int16_t)std::lround(256.0 * a * std::cos(kTwoPi * (2.0 * i + 1.0) * k /
+                                                                 (4.0 * M)));
+  }
+  p.in = in;
+  p.out = out;
+  p.set = d_set;
+  p.nblocks = nblocks;
+  p.log2m = log2m;
+  p.log2n = plan->log2n;
+  p.rounds = plan->rounds;
+  p.num_sets = plan->num_sets;
+  p.frac_bits = plan->frac_bits;
+  p.perm_mask = plan->perm_mask;
+  p.tab = static_cast<const uint32_t*>(plan->d_tab_int);
+  p.perm = plan->d_perm;
+  p.group = M * M >= 512 ? 1 : 512 / (M * M);
+  p.status = d_status;
+  return to_status(hygt::launch_secondary(inverse, p, (cudaStream_t)stream));
+}
+
+hygt_status hygt_secondary_forward(hygt_plan plan, int log2m, const int16_t* d_x, int32_t* d_y,
+                                   const uint16_t* d_set, int64_t nblocks, hygt_stream stream,
+                                   int* d_status) {
+  return secondary_run(0, plan, log2m, d_x, d_y, d_set, nblocks, stream, d_status);
+}
+
+hygt_status hygt_secondary_inverse(hygt_plan plan, int log2m, const int32_t* d_y, int16_t* d_x,
+                                   const uint16_t* d_set, int64_t nblocks, hygt_stream stream,
+                                   int* d_status) {
+  return secondary_run(1, plan, log2m, d_y, d_x, d_set, nblocks, stream, d_status);
 }
 
 size_t hygt_coding_gain_workspace_bytes(hygt_plan plan, int64_t nblocks) {

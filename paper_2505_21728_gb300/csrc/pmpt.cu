@@ -90,9 +90,9 @@ __global__ void __launch_bounds__(kPmptThreads) hygt_pmpt_kernel(PmptParams p) {
       else
         reg[blk * RS + i] = __ldcs(static_cast<const int16_t*>(p.in) + g);
     }
-    if (lane < nb) {
-      const int s = p.set ? (int)__ldg(p.set + b0 + lane) : 0;
-      bset[lane] = s;
+    for (int k = lane; k < nb; k += 32) {  // a task may hold more than 32 blocks
+      const int s = p.set ? (int)__ldg(p.set + b0 + k) : 0;
+      bset[k] = s;
       if (s != 0xFFFF && s >= p.num_sets && p.status) atomicCAS(p.status, 0, HYGT_ERR_SET_INDEX);
     }
     __syncwarp();

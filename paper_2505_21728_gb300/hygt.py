@@ -91,6 +91,10 @@ def _load() -> ctypes.CDLL:
     f32 = ctypes.c_float
     L.hygt_adam_step.argtypes = [P, P, P, P, i64, f32, f32, f32, f32, i32, P]
     L.hygt_adam_step.restype = i32
+    for name in ("hygt_secondary_forward", "hygt_secondary_inverse"):
+        f = getattr(L, name)
+        f.argtypes = [P, i32, P, P, P, i64, P, P]
+        f.restype = i32
     L.hygt_pmpt_create.argtypes = [ctypes.POINTER(P), i32, i32, i32, P, P, P, P, i32, i32]
     L.hygt_pmpt_create.restype = i32
     L.hygt_pmpt_destroy.argtypes = [P]
@@ -260,6 +264,16 @@ def hygt_coding_gain_f32(plan, d_y, nblocks, d_v, d_w, d_J, d_work, work_bytes, 
 def hygt_adam_step(d_theta, d_grad, d_m, d_v, n, lr, beta1, beta2, eps, step, stream):
     return int(_lib.hygt_adam_step(d_theta, d_grad, d_m, d_v, n, lr, beta1, beta2, eps, step,
                                    stream))
+
+
+def hygt_secondary_forward(plan, log2m, d_x, d_y, d_set, nblocks, stream, d_status):
+    return int(_lib.hygt_secondary_forward(plan, log2m, d_x, d_y, d_set, nblocks, stream,
+                                           d_status))
+
+
+def hygt_secondary_inverse(plan, log2m, d_y, d_x, d_set, nblocks, stream, d_status):
+    return int(_lib.hygt_secondary_inverse(plan, log2m, d_y, d_x, d_set, nblocks, stream,
+                                           d_status))
 
 
 def hygt_pmpt_create(n, passes, num_sets, angle_idx, theta, m_idx, n_idx, angle_bits=8,
@@ -483,6 +497,42 @@ class Plan:
                                  gth.data_ptr(), ps, nb, work.data_ptr(), wb,
                                  _stream_handle(stream), pst), "hygt_backward_f32")
         return gx, gth
+
+    def secondary_forward(self, x, log2m, sets=None, out=None, status=None, stream=None):
+        """Integer DCT-II primary of int16 M x M blocks x [B, M*M] (raster),
+        then this plan's HyGT on the top-left coefficients -> int32 [B, M*M]."""
+        import torch
+        M2 = 1 << (2 * int(log2m))
+        if out is None:
+            out = torch.empty((x.shape[0], M2), dtype=torch.int32, device=x.device)
+        return self._call_sec(hygt_secondary_forward, "hygt_secondary_forward", log2m, x, out,
+                              sets, torch.int16, torch.int32, status, stream)
+
+    def secondary_inverse(self, y, log2m, sets=None, out=None, status=None, stream=None):
+        import torch
+        M2 = 1 << (2 * int(log2m))
+        if out is None:
+            out = torch.empty((y.shape[0], M2), dtype=torch.int16, device=y.device)
+        return self._call_sec(hygt_secondary_inverse, "hygt_secondary_inverse", log2m, y, out,
+                              sets, torch.int32, torch.int16, status, stream)
+
+    def _call_sec(self, fn, name, log2m, x, out, sets, in_dtype, out_dtype, status, stream):
+        import torch
+        M2 = 1 << (2 * int(log2m))
+        nb = x.shape[0]
+        px = _dptr(x, in_dtype, M2, "input")
+        po = _dptr(out, out_dtype, M2, "output")
+        if out.shape[0] != nb:
+            raise ValueError("output has %d blocks, input %d" % (out.shape[0], nb))
+        ps = None
+        if sets is not None:
+            if sets.numel() != nb:
+                raise ValueError("sets must have one entry per block")
+            ps = _dptr(sets, torch.int16 if sets.dtype == torch.int16 else torch.uint16, None,
+                       "sets")
+        pst = None if status is None else _dptr(status, torch.int32, None, "status")
+        _check(fn(self.handle, int(log2m), px, po, ps, nb, _stream_handle(stream), pst), name)
+        return out
 
     def dense_matrices(self):
         """The N x N matrix of every set (float32 [S, N, N], y = T x), from
