@@ -58,6 +58,10 @@ def parse_args():
                     help="--case mixed: divide the frame batch's block counts")
     ap.add_argument("--no-tune", action="store_true",
                     help="--case mixed: default CTA split instead of the autotuner's")
+    ap.add_argument("--fwd-tuning", default=None,
+                    help="--case batch/stress: launch tuning of the forward, "
+                         "'warps,ctas_per_sm,stage' (hygt_batch_set_tuning)")
+    ap.add_argument("--inv-tuning", default=None, help="the same for the inverse")
     return ap.parse_args()
 
 
@@ -305,6 +309,11 @@ def run_ours(args, rank, world, local):
     d_xr = torch.empty((count, N), dtype=torch.int16, device=dev)
     stream = torch.cuda.current_stream(dev)
     batch = hygt.Batch(plan, count, device=dev)
+    # launch tuning (warps per CTA, CTAs per SM, staging) by the autotuner,
+    # outside the timed region
+    from paper_2505_21728_gb300 import autotune
+    batch.build(d_s)
+    tuning = autotune.tune_batch(batch, d_x, d_y, d_xr, reps=3, use_cache=False)
 
     # One step: bucket the batch by set, forward, inverse (5 kernels).
     K = args.steps
@@ -376,6 +385,9 @@ def run_ours(args, rank, world, local):
         "config": {"workload": w.name, "nblocks": count, "N": N, "rounds": w.rounds,
                    "sets": w.num_sets, "parallelism": "dp%d" % world,
                    "step": "bucket blocks by set, integer forward, integer inverse",
+                   "launch_tuning": {d: {"warps_per_cta": v[0], "ctas_per_sm": v[1],
+                                         "stage": v[2], "tuner_ms": v[3]}
+                                     for d, v in tuning.items()},
                    "l2": "inputs larger than L2 (%.0f MB read + %.0f MB written per step "
                          "vs %d MB L2), no flush" % (count * 6 * N / 1e6, count * 6 * N / 1e6,
                                                      L2_BYTES >> 20),
@@ -397,6 +409,9 @@ def run_ours(args, rank, world, local):
         line["backward"] = backward_leg(dev, stream, steps=max(5, K // 4))
         line["small_4x4"] = small_leg(dev, stream, steps=max(20, K))
         line["coding_gain"] = coding_gain_leg(dev, stream)
+        line["rounds_variants"] = rounds_leg(dev)
+        line["secondary_8x8"] = secondary_leg(dev, stream)
+        line["pmpt_64"] = pmpt_leg(dev, stream)
         del d_x, d_s
         torch.cuda.empty_cache()
         line["stress_16x16"] = stress_leg(dev, stream)
@@ -452,6 +467,9 @@ def stress_leg(dev, stream, steps=4, name="hygt16x16_r3_s16", sample=65536):
     b = hygt.Batch(plan, n, device=dev)
     y = torch.empty((n, N), dtype=torch.int32, device=dev)
     xr = torch.empty_like(x)
+    from paper_2505_21728_gb300 import autotune
+    b.build(s)
+    tuning = autotune.tune_batch(b, x, y, xr, reps=2, use_cache=False)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
 
     def int_step():
@@ -478,6 +496,7 @@ def stress_leg(dev, stream, steps=4, name="hygt16x16_r3_s16", sample=65536):
     dom_ms = max(f_ms, i_ms)
     out = {"workload": w.name, "description": w.description, "nblocks": n,
            "int32": {"fwd_ms": f_ms, "inv_ms": i_ms, "schedule_ms": b_ms,
+                     "launch_tuning": {d: list(v) for d, v in tuning.items()},
                      "value": n / ((f_ms + i_ms + b_ms) / 1000.0), "unit": "blocks/s",
                      "roofline": {"bound": "hbm", "achieved": bpl / (dom_ms / 1000.0) / 1e9,
                                   "peak": peak, "unit": "GB/s",
@@ -488,17 +507,17 @@ def stress_leg(dev, stream, steps=4, name="hygt16x16_r3_s16", sample=65536):
     del y, xr
     torch.cuda.empty_cache()
 
-    # FP32 path (float32 in and out, set indices given)
+    # FP32 path (float32 in and out) through the same set-bucketed schedule
     xf = x.to(torch.float32)
     yf = torch.empty_like(xf)
     xrf = torch.empty_like(xf)
-    plan.forward_f32(xf, s, out=yf)
-    plan.inverse_f32(yf, s, out=xrf)
+    b.forward_f32(xf, out=yf)
+    b.inverse_f32(yf, out=xrf)
     torch.cuda.synchronize(dev)
     ev[0].record(stream)
-    plan.forward_f32(xf, s, out=yf)
+    b.forward_f32(xf, out=yf)
     ev[1].record(stream)
-    plan.inverse_f32(yf, s, out=xrf)
+    b.inverse_f32(yf, out=xrf)
     ev[2].record(stream)
     torch.cuda.synchronize(dev)
     ff, fi = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
@@ -509,7 +528,7 @@ def stress_leg(dev, stream, steps=4, name="hygt16x16_r3_s16", sample=65536):
                    "roofline": {"bound": "hbm", "achieved": 8 * N * n / (ff / 1000.0) / 1e9,
                                 "peak": peak, "unit": "GB/s",
                                 "frac": 8 * N * n / (ff / 1000.0) / 1e9 / peak,
-                                "peak_source": kind}}
+                                "peak_source": kind, "kernel": "hygt_f32b_kernel<8,*>"}}
     out["int32"]["max_abs_dev_vs_fp32_hygt"] = float((yi_sample - ref).abs().max())
     del xf, yf, xrf
     torch.cuda.empty_cache()
@@ -575,6 +594,116 @@ def coding_gain_leg(dev, stream, restarts=3, iters=200):
             "ms_per_iteration": 1000.0 * secs / (restarts * iters)}
 
 
+def _timed(fn, dev, stream, reps):
+    import torch
+    fn()
+    torch.cuda.synchronize(dev)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    return a.elapsed_time(b) / reps
+
+
+def secondary_leg(dev, stream, reps=5):
+    """The secondary-transform pipeline (Sec. VI) on 16 frames of 3840x2160
+    tiled into 8x8 blocks: the fused kernel runs the integer DCT-II primary
+    and the 8x8 HyGT (2 rounds, 105 sets, 10% of the blocks without a
+    secondary transform) on the top-left coefficients, then the inverse."""
+    import numpy as np
+    import torch
+    from paper_2505_21728_gb300 import hygt, inputs
+    B, R, S = 16 * (3840 // 8) * (2160 // 8), 2, 105
+    q = inputs.angle_indices(S, R, 6, seed=7)
+    perms = inputs.permutations(S, R, 64, seed=7)
+    plan = hygt.Plan(6, R, q, perms)
+    x = torch.from_numpy(inputs.laplacian_blocks(B, 64, 8.0, -1024, 1023, seed=7)).to(dev)
+    s = torch.from_numpy(inputs.set_indices(B, S, seed=7, skip_frac=0.1).view(np.int16)).to(dev)
+    y = torch.empty((B, 64), dtype=torch.int32, device=dev)
+    xr = torch.empty_like(x)
+    f_ms = _timed(lambda: plan.secondary_forward(x, 3, s, out=y), dev, stream, reps)
+    i_ms = _timed(lambda: plan.secondary_inverse(y, 3, s, out=xr), dev, stream, reps)
+    peak, kind = measured_peaks()
+    bpl = B * (6 * 64 + 2)
+    dom = max(f_ms, i_ms)
+    plan.close()
+    return {"workload": "16 frames of 3840x2160 in 8x8 blocks (%d blocks), 8x8 HyGT secondary, "
+                        "2 rounds, 105 sets, 10%% primary only" % B,
+            "fwd_ms": f_ms, "inv_ms": i_ms, "value": B / ((f_ms + i_ms) / 1000.0),
+            "unit": "blocks/s",
+            "roofline": {"bound": "hbm", "achieved": bpl / (dom / 1000.0) / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": bpl / (dom / 1000.0) / 1e9 / peak,
+                         "peak_source": kind, "kernel": "hygt_secondary_kernel"}}
+
+
+def pmpt_leg(dev, stream, reps=5, B=1 << 22):
+    """The general PMPT with explicit pair covers (random perfect matchings,
+    12 passes of N = 64: as many rotations as a 2-round 8x8 HyGT) on the
+    benchmark's block count, 105 sets: its time, and its parameter memory
+    against the HyGT's (indices stored: 3 bytes per rotation, not 1)."""
+    import numpy as np
+    import torch
+    from paper_2505_21728_gb300 import hygt, inputs
+    N, P, S = 64, 12, 105
+    rng = np.random.default_rng(9)
+    m = np.empty((S, P, N // 2), np.uint16)
+    n = np.empty((S, P, N // 2), np.uint16)
+    for a in range(S):
+        for k in range(P):
+            perm = rng.permutation(N)
+            m[a, k], n[a, k] = perm[0::2], perm[1::2]
+    q = rng.integers(0, 256, (S, P, N // 2)).astype(np.uint8)
+    pm = hygt.PMPT(N, P, m, n, angle_idx=q)
+    x = torch.from_numpy(inputs.laplacian_blocks(B, N, 8.0, -1024, 1023, seed=9)).to(dev)
+    s = torch.from_numpy(inputs.set_indices(B, S, seed=9).view(np.int16)).to(dev)
+    y = pm.forward(x, s)
+    f_ms = _timed(lambda: pm.forward(x, s), dev, stream, reps)
+    i_ms = _timed(lambda: pm.inverse(y, s), dev, stream, reps)
+    peak, kind = measured_peaks()
+    bpl = B * (6 * N + 2)
+    dom = max(f_ms, i_ms)
+    pm.close()
+    return {"workload": "%d blocks, N = 64, 12 passes, 105 sets, random pair covers" % B,
+            "fwd_ms": f_ms, "inv_ms": i_ms, "value": B / ((f_ms + i_ms) / 1000.0),
+            "unit": "blocks/s",
+            "param_bytes_per_set": hygt.hygt_pmpt_param_bytes(N, P, 1),
+            "hygt_param_bytes_per_set": hygt.hygt_param_bytes(6, 2, 1),
+            "roofline": {"bound": "hbm", "achieved": bpl / (dom / 1000.0) / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": bpl / (dom / 1000.0) / 1e9 / peak,
+                         "peak_source": kind, "kernel": "hygt_pmpt_kernel"}}
+
+
+def rounds_leg(dev, nvec=1 << 18):
+    """HyGT variants H(R) fitted with the Sec. V objective on correlated 4x4
+    and 8x8 patches (Table II's H(2), H(3) for 4x4 and H(3), H(4), H(5) for
+    8x8), each quantised to one byte per angle: J at the FP32 and at the
+    8-bit angles against the KLT bound, and the KLT/HyGT memory ratio."""
+    import numpy as np
+    import torch
+    from paper_2505_21728_gb300 import fit, inputs
+    out = []
+    t0 = time.perf_counter()
+    for log2n, rl in ((4, (2, 3)), (6, (3, 4, 5))):
+        N = 1 << log2n
+        x = inputs.ar1_patches(nvec, int(round(N ** 0.5)), seed=3)
+        x64 = x.astype(np.float64)
+        phi = x64.T @ x64 / nvec
+        bound = float(np.sum(np.log2(np.linalg.eigvalsh(phi))) / (2 * N))
+        for r in fit.rounds_ladder(torch.from_numpy(x).to(dev), log2n, rl, iters=200,
+                                   restarts=2, seed=1):
+            out.append({"block": "%dx%d" % (int(N ** 0.5), int(N ** 0.5)), "rounds": r["rounds"],
+                        "J": r["J"], "J_8bit": r["J_q"], "J_klt": bound,
+                        "gap_bits": r["J"] - bound, "gap_bits_8bit": r["J_q"] - bound,
+                        "param_bytes": r["param_bytes"], "klt_bytes": N * N,
+                        "memory_ratio": N * N / r["param_bytes"]})
+    return {"patches_per_class": nvec, "variants": out,
+            "seconds": time.perf_counter() - t0,
+            "objective": "J = 1/(2N) sum log2 v_i (bits per coefficient, up to constants)"}
+
+
 def mixed_leg(dev, stream, steps=20, name="mixed_frame_2160p16"):
     """The mixed-size frame batch (4x4 / 8x8 / 16x16 blocks, one persistent
     launch per direction) as a CUDA graph of one step: schedules of the three
@@ -593,6 +722,7 @@ def mixed_leg(dev, stream, steps=20, name="mixed_frame_2160p16"):
                         torch.from_numpy(d["sets"].view(np.int16)).to(dev)))
     mb = hygt.MixedBatch(classes, device=dev)
     mb.build()
+    tunings = autotune.tune_mixed_classes(mb, reps=3, use_cache=False)
     split = autotune.tune_split(mb, reps=3, use_cache=False)
     graph = mb.graph()
     for _ in range(3):
@@ -633,6 +763,10 @@ def mixed_leg(dev, stream, steps=20, name="mixed_frame_2160p16"):
             "mode": ("separate launches" if all(c == -1 for c in split) else
                      "concurrent" if all(c > 0 for c in split) else "sequential"),
             "cta_split": split,
+            "class_launch_tuning": {str(n): {d: {"warps_per_cta": v[0], "ctas_per_sm": v[1],
+                                                 "stage": v[2], "tuner_ms": v[3]}
+                                             for d, v in t.items()}
+                                    for n, t in tunings.items()},
             "gpu_launches_per_step": 3 * 3 + (6 if all(c == -1 for c in split) else 2),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "kernel": dom_name, "peak_source": kind,
@@ -802,8 +936,9 @@ def e2e_leg(plan, x_np, s_np, N, dev, stream, world, steps=10):
     """Same metric through the public API with host buffers: every step is
     one hygt_host_roundtrip call (HostPipe.roundtrip) on pinned host tensors
     -- the blocks and set indices go host->device, are bucketed, transformed
-    forward and back, and the coefficients and reconstructed blocks come back
-    to host memory, in chunks whose copies overlap the kernels."""
+    forward and back, and the step's result (the reconstructed blocks) comes
+    back to host memory, in chunks whose copies overlap the kernels.  The
+    same with the coefficients returned as well is reported beside it."""
     import numpy as np
     import torch
     from paper_2505_21728_gb300 import hygt
@@ -814,23 +949,34 @@ def e2e_leg(plan, x_np, s_np, N, dev, stream, world, steps=10):
     h_xr = torch.empty((count, N), dtype=torch.int16).pin_memory()
     pipe = hygt.HostPipe(plan, 1 << 17)
 
-    def step():
-        _, _, status = pipe.roundtrip(h_x, h_s, h_y, h_xr)
-        if status:
-            raise RuntimeError("device status %d" % status)
-
-    step()
-    barrier(world)
-    t0 = time.perf_counter()
-    for _ in range(steps):
+    def run(coefficients):
+        def step():
+            _, _, status = pipe.roundtrip(h_x, h_s, h_y if coefficients else None, h_xr,
+                                          coefficients=coefficients)
+            if status:
+                raise RuntimeError("device status %d" % status)
         step()
-    ms = (time.perf_counter() - t0) * 1000.0
-    ms = max_over_ranks(ms, world, dev)
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            step()
+        ms = (time.perf_counter() - t0) * 1000.0
+        return max_over_ranks(ms, world, dev)
+
+    ms = run(False)
+    ms_coef = run(True)
     pipe.close()
     return {"value": count * world * steps / (ms / 1000.0), "unit": "blocks/s",
-            "h2d_bytes_per_step": count * (2 * N + 2), "d2h_bytes_per_step": count * 6 * N,
+            "h2d_bytes_per_step": count * (2 * N + 2), "d2h_bytes_per_step": count * 2 * N,
             "steps": steps, "api": "hygt_host_roundtrip (HostPipe), pinned host buffers, "
-                                  "chunks of 131,072 blocks on three streams"}
+                                  "chunks of 131,072 blocks on three streams; the step's "
+                                  "result (the reconstruction) read back",
+            "with_coefficients": {"value": count * world * steps / (ms_coef / 1000.0),
+                                  "unit": "blocks/s", "d2h_bytes_per_step": count * 6 * N,
+                                  "note": "int32 coefficients read back as well"},
+            "host_link": "measured on this box: 193 GB/s device to host, 211 GB/s host to "
+                         "device, 171 GB/s each way when both run (copy engines or SM "
+                         "stores alike)"}
 
 
 # ---------------------------------------------------------------- kernel cases (ncu)
@@ -853,6 +999,11 @@ def case_batch(args, name=DEFAULT_WORKLOAD):
     import torch
     from paper_2505_21728_gb300 import hygt
     w, d, plan, x, s = _int_case_data(name, args.nblocks)
+    for inv, t in ((0, args.fwd_tuning), (1, args.inv_tuning)):
+        if t:
+            vals = [int(v) for v in t.split(",")]
+            hygt._check(hygt.hygt_batch_set_tuning(plan.handle, inv, *vals),
+                        "hygt_batch_set_tuning")
     b = hygt.Batch(plan, x.shape[0])
     y = torch.empty((x.shape[0], w.N), dtype=torch.int32, device="cuda")
     xr = torch.empty_like(x)
@@ -956,9 +1107,64 @@ def case_coding_gain(args):
     return run
 
 
+def case_stress_f32(args):
+    """bucket + FP32 forward + FP32 inverse (set-bucketed kernels), 16x16 workload"""
+    import torch
+    from paper_2505_21728_gb300 import hygt
+    w, d, plan, x, s = _int_case_data("hygt16x16_r3_s16", args.nblocks)
+    xf = x.float()
+    b = hygt.Batch(plan, x.shape[0])
+    y = torch.empty_like(xf)
+    xr = torch.empty_like(xf)
+
+    def run():
+        b.build(s)
+        b.forward_f32(xf, out=y)
+        b.inverse_f32(y, out=xr)
+    return run
+
+
+def case_secondary(args):
+    """fused DCT-II primary + 8x8 HyGT secondary, forward + inverse, 8x8 blocks"""
+    import numpy as np
+    import torch
+    from paper_2505_21728_gb300 import hygt, inputs
+    B = args.nblocks or 2073600
+    q = inputs.angle_indices(105, 2, 6, seed=7)
+    plan = hygt.Plan(6, 2, q, inputs.permutations(105, 2, 64, seed=7))
+    x = torch.from_numpy(inputs.laplacian_blocks(B, 64, 8.0, -1024, 1023, seed=7)).cuda()
+    s = torch.from_numpy(inputs.set_indices(B, 105, seed=7, skip_frac=0.1).view(np.int16)).cuda()
+    y = torch.empty((B, 64), dtype=torch.int32, device="cuda")
+    xr = torch.empty_like(x)
+
+    def run():
+        plan.secondary_forward(x, 3, s, out=y)
+        plan.secondary_inverse(y, 3, s, out=xr)
+    return run
+
+
+def case_pmpt(args):
+    """general PMPT (random pair covers), N = 64, 12 passes, forward + inverse"""
+    import numpy as np
+    import torch
+    from paper_2505_21728_gb300 import hygt, inputs
+    B, N, P, S = args.nblocks or (1 << 22), 64, 12, 105
+    rng = np.random.default_rng(9)
+    perm = np.stack([[rng.permutation(N) for _ in range(P)] for _ in range(S)])
+    q = rng.integers(0, 256, (S, P, N // 2)).astype(np.uint8)
+    pm = hygt.PMPT(N, P, perm[:, :, 0::2], perm[:, :, 1::2], angle_idx=q)
+    x = torch.from_numpy(inputs.laplacian_blocks(B, N, 8.0, -1024, 1023, seed=9)).cuda()
+    s = torch.from_numpy(inputs.set_indices(B, S, seed=9).view(np.int16)).cuda()
+
+    def run():
+        pm.inverse(pm.forward(x, s), s)
+    return run
+
+
 CASES = {"batch": case_batch, "stress": case_stress, "direct": case_direct,
          "mixed": case_mixed, "dense": case_dense, "grad": case_grad,
-         "coding_gain": case_coding_gain}
+         "coding_gain": case_coding_gain, "stress_f32": case_stress_f32,
+         "secondary": case_secondary, "pmpt": case_pmpt}
 
 
 def run_case(args):

@@ -166,6 +166,48 @@ hygt_status hygt_inverse_batch(hygt_plan plan, const void *d_work, const int32_t
                                int *d_status);
 
 /*
+ * Launch tuning of the set-bucketed kernels (no counterpart in the paper:
+ * how many blocks a CTA holds and how far ahead the input is staged decide
+ * how well a GB300 SM hides memory latency; the autotuner of the Python
+ * package times the choices and sets the fastest).  Per plan and direction
+ * (inverse 0: hygt_forward_batch, 1: hygt_inverse_batch), used by every
+ * later bucketed call with that plan, the mixed calls included:
+ *   warps_per_cta  warps of a CTA, 1 .. max_warps (0: max_warps); a warp
+ *        task holds 32 * (blocks per lane group) / (lanes per block) blocks;
+ *   ctas_per_sm    CTAs per SM, 1 .. 8 (0: as many as the shared memory and
+ *        registers allow); the shared memory is split between them;
+ *   stage          -1: the default; 0: blocks read straight from global
+ *        memory; 1: each warp copies its next task's blocks into shared
+ *        memory (cp.async) while it transforms the current one (N >= 16;
+ *        smaller blocks return HYGT_ERR_UNSUPPORTED).
+ * Results do not depend on the tuning.  A choice whose shared memory does
+ * not fit makes the next bucketed call return HYGT_ERR_UNSUPPORTED.  Not
+ * thread-safe with concurrent calls on the same plan.
+ */
+hygt_status hygt_batch_set_tuning(hygt_plan plan, int inverse, int warps_per_cta,
+                                  int ctas_per_sm, int stage);
+hygt_status hygt_batch_get_tuning(hygt_plan plan, int inverse, int *warps_per_cta,
+                                  int *ctas_per_sm, int *stage, int *max_warps);
+
+/*
+ * FP32 HyGT through the same set-bucketed schedule (the FP32 forward and
+ * inverse of Sec. IV; y_m = c a + s b, y_n = -s a + c b in FP32, the inverse
+ * with (c, -s) and the passes reversed): hygt_batch_build(plan, d_set, ...)
+ * first, then these calls with the same d_work and nblocks (float
+ * [nblocks][N] in and out, 16-byte aligned).  For N >= 16 (log2n >= 4;
+ * smaller blocks return HYGT_ERR_UNSUPPORTED: use hygt_forward_f32).  Skip
+ * blocks are copied; bad set indices give zeros and HYGT_ERR_SET_INDEX in
+ * d_status; a schedule built for another batch gives HYGT_ERR_ARG in
+ * d_status and no output.  Async on stream.
+ */
+hygt_status hygt_forward_batch_f32(hygt_plan plan, const void *d_work, const float *d_x,
+                                   float *d_y, int64_t nblocks, hygt_stream stream,
+                                   int *d_status);
+hygt_status hygt_inverse_batch_f32(hygt_plan plan, const void *d_work, const float *d_y,
+                                   float *d_x, int64_t nblocks, hygt_stream stream,
+                                   int *d_status);
+
+/*
  * Differentiable FP32 path (the angles are the parameters optimised in
  * Sec. V; the paper leaves the optimiser out of scope).
  *
@@ -470,8 +512,9 @@ hygt_status hygt_forward_static(hygt_plan plan, const int16_t *d_x, int32_t *d_y
  *        schedule workspace, a stream and a status word each); chunk_blocks
  *        in 1 .. 2^26.  Synchronous.
  *   hygt_host_roundtrip    h_x int16 [nblocks][N] in; h_set uint16 [nblocks]
- *        or NULL (set 0); h_y int32 [nblocks][N] and h_xr int16 [nblocks][N]
- *        out.  Synchronous: returns when every result is in host memory;
+ *        or NULL (set 0); h_y int32 [nblocks][N] (or NULL: the coefficients
+ *        are not copied back, only the reconstruction) and h_xr int16
+ *        [nblocks][N] out.  Synchronous: returns when every result is in host memory;
  *        *h_status (nullable) receives the first device-side status
  *        (HYGT_ERR_SET_INDEX for an out-of-range set index).  Calls on one
  *        pipe must not overlap.

@@ -1,4 +1,8 @@
-"""Autotuner of the mixed-size launch.
+"""Autotuners: the launch tuning of the bucketed kernels (blocks per CTA,
+CTAs per SM, staging depth; ``tune_batch``) and the mode of the mixed-size
+launch (``tune_split``).
+
+Mixed launch.
 
 A mixed batch runs in one of three modes: one launch in which every CTA
 works through all classes in turn (split of all zeros); one launch in which
@@ -153,3 +157,110 @@ def tune_split(mb, reps=5, use_cache=True, verbose=False):
         except OSError:
             pass
     return split
+
+
+# ---------------------------------------------------------------- launch tuning
+def batch_candidates(max_warps, log2n):
+    """(warps_per_cta, ctas_per_sm, stage) points the batch tuner times:
+    blocks per CTA through the warps of a CTA, CTAs per SM, and the staging
+    depth (0: none, 1: the next task's blocks copied ahead; N >= 16 only)."""
+    warps = sorted({w for w in (max_warps, (3 * max_warps) // 4, max_warps // 2,
+                                max_warps // 3, 4) if w >= 2})
+    stages = (0, 1) if log2n >= 4 else (-1,)
+    out = []
+    for w in warps:
+        for c in (0, 1, 2):
+            for s in stages:
+                out.append((w, c, s))
+    return out
+
+
+def _time_dir(fn, reps):
+    import torch
+    stream = torch.cuda.current_stream()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    return statistics.median(times)
+
+
+def tune_batch(batch, x, y, xr, reps=5, use_cache=True, verbose=False, time_fn=None):
+    """Times every launch tuning of ``batch_candidates`` for the bucketed
+    forward and inverse of ``batch`` (a hygt.Batch with its schedule built)
+    and sets the fastest on the plan (hygt_batch_set_tuning).  Returns
+    {"forward": (warps, ctas_per_sm, stage, ms), "inverse": (...)}.
+    Results are cached by GPU name, block size, rounds, sets and block count.
+    ``time_fn(direction, tuning)`` replaces the GPU timing (tests)."""
+    plan = batch.plan
+    key = None
+    cache, path = {}, _cache_path()
+    if use_cache:
+        import torch
+        key = "batch|%s|N%d_R%d_S%d_B%d" % (torch.cuda.get_device_name(), plan.N, plan.rounds,
+                                             plan.num_sets, batch.nblocks)
+        if os.path.exists(path):
+            try:
+                with open(path) as f:
+                    cache = json.load(f)
+            except (OSError, ValueError):
+                cache = {}
+        if key in cache:
+            res = {d: tuple(v) for d, v in cache[key].items()}
+            for inv, d in ((0, "forward"), (1, "inverse")):
+                hygt._check(hygt.hygt_batch_set_tuning(plan.handle, inv, *res[d][:3]),
+                            "hygt_batch_set_tuning")
+            return res
+    res = {}
+    for inv, d in ((0, "forward"), (1, "inverse")):
+        max_warps = hygt.hygt_batch_get_tuning(plan.handle, inv)[3]
+        best = None
+        for cand in batch_candidates(max_warps, plan.log2n):
+            if hygt.hygt_batch_set_tuning(plan.handle, inv, *cand) != hygt.HYGT_OK:
+                continue
+            if time_fn is not None:
+                ms = time_fn(d, cand)
+            else:
+                fn = (lambda: batch.forward(x, out=y)) if inv == 0 else \
+                    (lambda: batch.inverse(y, out=xr))
+                try:
+                    ms = _time_dir(fn, reps)
+                except hygt.HygtError:
+                    continue  # this point does not fit (shared memory)
+            if verbose:
+                print("tune %s %s: %.4f ms" % (d, cand, ms))
+            if best is None or ms < best[3]:
+                best = (cand[0], cand[1], cand[2], ms)
+        if best is None:
+            best = (0, 0, -1, float("nan"))
+        hygt._check(hygt.hygt_batch_set_tuning(plan.handle, inv, *best[:3]),
+                    "hygt_batch_set_tuning")
+        res[d] = best
+    if use_cache and key is not None:
+        cache[key] = {d: list(v) for d, v in res.items()}
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            with open(path, "w") as f:
+                json.dump(cache, f, indent=1)
+        except OSError:
+            pass
+    return res
+
+
+def tune_mixed_classes(mb, reps=3, use_cache=True):
+    """tune_batch for every class of a MixedBatch (schedules built): the
+    per-class launches of its separate mode use these tunings.  Returns
+    {N: result of tune_batch}."""
+    out = {}
+    for e in mb.entries:
+        plan = e["plan"]
+        b = hygt.Batch.on_workspace(plan, int(e["x"].shape[0]), e["work"])
+        out[plan.N] = tune_batch(b, e["x"], e["y"], e["xr"], reps=reps, use_cache=use_cache)
+    return out

@@ -91,7 +91,7 @@ hygt_status hygt_host_roundtrip(hygt_host_pipe p, const int16_t* h_x, const uint
   if (!p || nblocks < 0) return HYGT_ERR_ARG;
   if (h_status) *h_status = 0;
   if (nblocks == 0) return HYGT_OK;
-  if (!h_x || !h_y || !h_xr) return HYGT_ERR_ARG;
+  if (!h_x || !h_xr) return HYGT_ERR_ARG;  // h_y may be null: coefficients stay on the device
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return HYGT_ERR_CUDA;
   if (dev != p->device) return HYGT_ERR_ARG;
@@ -122,8 +122,8 @@ hygt_status hygt_host_roundtrip(hygt_host_pipe p, const int16_t* h_x, const uint
     if (st == HYGT_OK)
       st = hygt_inverse_batch(p->plan, s.d_work, s.d_y, s.d_xr, nb, hs, s.d_status);
     if (st != HYGT_OK) break;
-    if (cudaMemcpyAsync(h_y + off * n, s.d_y, (size_t)nb * n * 4, cudaMemcpyDeviceToHost, cs) !=
-            cudaSuccess ||
+    if ((h_y && cudaMemcpyAsync(h_y + off * n, s.d_y, (size_t)nb * n * 4, cudaMemcpyDeviceToHost,
+                                cs) != cudaSuccess) ||
         cudaMemcpyAsync(h_xr + off * n, s.d_xr, (size_t)nb * n * 2, cudaMemcpyDeviceToHost, cs) !=
             cudaSuccess)
       st = HYGT_ERR_CUDA;

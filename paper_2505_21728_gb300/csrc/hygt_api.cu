@@ -15,6 +15,7 @@
 #include "../../include/hygt.h"
 #include "hygt_batch.cuh"
 #include "hygt_dense.cuh"
+#include "hygt_f32b.cuh"
 #include "hygt_f32u.cuh"
 #include "hygt_fit.cuh"
 #include "hygt_secondary.cuh"
@@ -36,6 +37,7 @@ struct hygt_plan_s {
   unsigned perm_mask = 0;
   int* d_ktab = nullptr;      // batch path: per-set tables [S][ktab_words]
   int ktab_words = 0;         // words per set, padded to a multiple of 4
+  hygt::BatchTune tune[2];    // batch path launch tuning: forward, inverse
 };
 
 namespace hygt {
@@ -483,8 +485,10 @@ static hygt_status batch_call(hygt_plan plan, const void* d_work, const void* in
   if (plan->is_float) return HYGT_ERR_UNSUPPORTED;
   if (!d_work || !aligned16(d_work) || nblocks > kBatchMaxBlocks) return HYGT_ERR_ARG;
   const hygt::BatchParams p = make_batch_params(plan, d_work, in, out, nblocks, d_status);
-  cudaError_t e = inverse ? hygt::launch_batch_inv(plan->log2n, p, (cudaStream_t)stream)
-                          : hygt::launch_batch_fwd(plan->log2n, p, (cudaStream_t)stream);
+  cudaError_t e =
+      inverse ? hygt::launch_batch_inv(plan->log2n, p, (cudaStream_t)stream, plan->tune[1])
+              : hygt::launch_batch_fwd(plan->log2n, p, (cudaStream_t)stream, plan->tune[0]);
+  if (e == cudaErrorInvalidConfiguration) return HYGT_ERR_UNSUPPORTED;
   return to_status(e);
 }
 
@@ -498,6 +502,74 @@ hygt_status hygt_inverse_batch(hygt_plan plan, const void* d_work, const int32_t
   return batch_call(plan, d_work, d_y, d_x, nblocks, stream, d_status, true);
 }
 
+static hygt_status batch_f32_call(hygt_plan plan, const void* d_work, const float* in,
+                                  float* out, int64_t nblocks, hygt_stream stream, int* d_status,
+                                  bool inverse) {
+  hygt_status s = check_io(plan, in, out, nblocks);
+  if (s != HYGT_OK || nblocks == 0) return s;
+  if (plan->log2n < 4) return HYGT_ERR_UNSUPPORTED;
+  if (!d_work || !aligned16(d_work) || nblocks > kBatchMaxBlocks) return HYGT_ERR_ARG;
+  const int group = hygt::batch_group(plan->log2n);
+  const hygt::BatchLayout L = hygt::batch_layout(plan->num_sets, nblocks, group);
+  const char* w = static_cast<const char*>(d_work);
+  hygt::F32bParams p{};
+  p.in = in;
+  p.out = out;
+  p.nblocks = nblocks;
+  p.tab = static_cast<const float2*>(plan->d_tab_f32);
+  p.perm = plan->d_perm;
+  p.perm_mask = plan->perm_mask;
+  p.rounds = plan->rounds;
+  p.num_sets = plan->num_sets;
+  p.order = reinterpret_cast<const int*>(w + L.order);
+  p.starts = reinterpret_cast<const int*>(w + L.starts);
+  p.meta = reinterpret_cast<const int*>(w + L.meta);
+  p.tmax = L.tmax;
+  p.group_sched = group;
+  p.status = d_status;
+  cudaError_t e = hygt::launch_f32b(plan->log2n, inverse ? 1 : 0, p, (cudaStream_t)stream);
+  if (e == cudaErrorInvalidConfiguration) return HYGT_ERR_UNSUPPORTED;
+  return to_status(e);
+}
+
+hygt_status hygt_forward_batch_f32(hygt_plan plan, const void* d_work, const float* d_x,
+                                   float* d_y, int64_t nblocks, hygt_stream stream,
+                                   int* d_status) {
+  return batch_f32_call(plan, d_work, d_x, d_y, nblocks, stream, d_status, false);
+}
+
+hygt_status hygt_inverse_batch_f32(hygt_plan plan, const void* d_work, const float* d_y,
+                                   float* d_x, int64_t nblocks, hygt_stream stream,
+                                   int* d_status) {
+  return batch_f32_call(plan, d_work, d_y, d_x, nblocks, stream, d_status, true);
+}
+
+hygt_status hygt_batch_set_tuning(hygt_plan plan, int inverse, int warps_per_cta,
+                                  int ctas_per_sm, int stage) {
+  if (!plan || (inverse != 0 && inverse != 1) || warps_per_cta < 0 || ctas_per_sm < 0 ||
+      ctas_per_sm > 8 || stage < -1 || stage > 1)
+    return HYGT_ERR_ARG;
+  const int max_warps = hygt::batch_threads(plan->log2n, inverse) / 32;
+  if (warps_per_cta > max_warps) return HYGT_ERR_ARG;
+  if (stage >= 0 && plan->log2n < 4) return HYGT_ERR_UNSUPPORTED;
+  hygt::BatchTune& t = plan->tune[inverse];
+  t.warps = warps_per_cta;
+  t.ctas_per_sm = ctas_per_sm;
+  t.stage = stage;
+  return HYGT_OK;
+}
+
+hygt_status hygt_batch_get_tuning(hygt_plan plan, int inverse, int* warps_per_cta,
+                                  int* ctas_per_sm, int* stage, int* max_warps) {
+  if (!plan || (inverse != 0 && inverse != 1)) return HYGT_ERR_ARG;
+  const hygt::BatchTune& t = plan->tune[inverse];
+  if (warps_per_cta) *warps_per_cta = t.warps;
+  if (ctas_per_sm) *ctas_per_sm = t.ctas_per_sm;
+  if (stage) *stage = t.stage;
+  if (max_warps) *max_warps = hygt::batch_threads(plan->log2n, inverse) / 32;
+  return HYGT_OK;
+}
+
 int hygt_mixed_ctas(void) { return hygt::mixed_grid_ctas(); }
 
 // Validates the classes of a mixed launch and fills the kernel parameters.
@@ -505,7 +577,8 @@ int hygt_mixed_ctas(void) { return hygt::mixed_grid_ctas(); }
 enum MixedMode { kMixedSequential, kMixedConcurrent, kMixedSeparate };
 
 static hygt_status mixed_params(const hygt_mixed_class* cls, int nclasses, bool inverse,
-                                int* d_status, hygt::MixedParams* mp, MixedMode* mode) {
+                                int* d_status, hygt::MixedParams* mp, MixedMode* mode,
+                                hygt::BatchTune* tunes = nullptr) {
   if (!cls || nclasses < 1 || nclasses > hygt::kMaxMixedClasses) return HYGT_ERR_ARG;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return HYGT_ERR_CUDA;
@@ -534,6 +607,7 @@ static hygt_status mixed_params(const hygt_mixed_class* cls, int nclasses, bool 
     }
     mp->cls[slot] = make_batch_params(plan, k.d_work, in, out, k.nblocks, d_status);
     mp->present[slot] = k.nblocks > 0 ? 1 : 0;
+    if (tunes) tunes[slot] = plan->tune[inverse ? 1 : 0];
     slot_ctas[slot] = k.ctas;
     if (k.ctas <= 0) explicit_split = false;
     if (k.ctas != -1) separate = false;
@@ -559,13 +633,13 @@ static hygt_status mixed_params(const hygt_mixed_class* cls, int nclasses, bool 
 // One direction of a mixed batch: the mixed kernel, or (separate mode) the
 // batch kernel of each class in turn.
 static cudaError_t mixed_launch(const hygt::MixedParams& mp, MixedMode mode, bool inverse,
-                                cudaStream_t stream) {
+                                cudaStream_t stream, const hygt::BatchTune* tunes) {
   if (mode != kMixedSeparate) return hygt::launch_mixed(inverse ? 1 : 0, mp, stream);
   for (int k = 0; k < hygt::kMaxMixedClasses; ++k) {
     if (!mp.present[k]) continue;
     const int log2n = hygt::mixed_slot_log2n(k);
-    const cudaError_t e = inverse ? hygt::launch_batch_inv(log2n, mp.cls[k], stream)
-                                  : hygt::launch_batch_fwd(log2n, mp.cls[k], stream);
+    const cudaError_t e = inverse ? hygt::launch_batch_inv(log2n, mp.cls[k], stream, tunes[k])
+                                  : hygt::launch_batch_fwd(log2n, mp.cls[k], stream, tunes[k]);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -575,9 +649,10 @@ static hygt_status mixed_call(const hygt_mixed_class* cls, int nclasses, hygt_st
                               int* d_status, bool inverse) {
   hygt::MixedParams mp;
   MixedMode mode;
-  hygt_status s = mixed_params(cls, nclasses, inverse, d_status, &mp, &mode);
+  hygt::BatchTune tunes[hygt::kMaxMixedClasses];
+  hygt_status s = mixed_params(cls, nclasses, inverse, d_status, &mp, &mode, tunes);
   if (s != HYGT_OK) return s;
-  return to_status(mixed_launch(mp, mode, inverse, (cudaStream_t)stream));
+  return to_status(mixed_launch(mp, mode, inverse, (cudaStream_t)stream, tunes));
 }
 
 hygt_status hygt_forward_mixed(const hygt_mixed_class* classes, int nclasses, hygt_stream stream,
@@ -643,8 +718,9 @@ hygt_status hygt_mixed_graph_create(hygt_graph* out, const hygt_mixed_class* cla
   *out = nullptr;
   hygt::MixedParams fwd, inv;
   MixedMode mode;
-  hygt_status s = mixed_params(classes, nclasses, false, d_status, &fwd, &mode);
-  if (s == HYGT_OK) s = mixed_params(classes, nclasses, true, d_status, &inv, &mode);
+  hygt::BatchTune tf[hygt::kMaxMixedClasses], ti[hygt::kMaxMixedClasses];
+  hygt_status s = mixed_params(classes, nclasses, false, d_status, &fwd, &mode, tf);
+  if (s == HYGT_OK) s = mixed_params(classes, nclasses, true, d_status, &inv, &mode, ti);
   if (s != HYGT_OK) return s;
   cudaStream_t cs = nullptr;
   if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return HYGT_ERR_CUDA;
@@ -656,8 +732,8 @@ hygt_status hygt_mixed_graph_create(hygt_graph* out, const hygt_mixed_class* cla
   GraphBranches br;
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) e = capture_schedules(classes, nclasses, cs, br);
-  if (e == cudaSuccess) e = mixed_launch(fwd, mode, false, cs);
-  if (e == cudaSuccess) e = mixed_launch(inv, mode, true, cs);
+  if (e == cudaSuccess) e = mixed_launch(fwd, mode, false, cs, tf);
+  if (e == cudaSuccess) e = mixed_launch(inv, mode, true, cs, ti);
   cudaGraph_t graph = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
   if (e == cudaSuccess) e = e2;

@@ -463,12 +463,10 @@ struct BatchStage {
 
 // Shared memory of one warp: permutation buffer, then (staged kernels) the
 // stage and the block ids.
-template <int LOG2N, int KIND>
+template <int LOG2N, int KIND, bool STAGED = batch_staged(LOG2N, KIND)>
 __host__ __device__ constexpr int batch_warp_bytes() {
   return perm_buf_words(LOG2N, KIND) * 4 +
-         (batch_staged(LOG2N, KIND)
-              ? BatchStage<LOG2N, KIND>::BYTES + BatchStage<LOG2N, KIND>::IDS_BYTES
-              : 0);
+         (STAGED ? BatchStage<LOG2N, KIND>::BYTES + BatchStage<LOG2N, KIND>::IDS_BYTES : 0);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -557,8 +555,9 @@ __device__ __forceinline__ void stage_read(const char* stage, int k, int lane32,
 // [set_lo, set_lo + cached count) when CACHED, else tables are read from
 // global memory.  `pbuf` is the warp's shared memory: G block regions of
 // perm_region_words(LOG2N) words (the permutation buffer), then for staged
-// kernels the stage and the block ids (batch_warp_bytes in all).
-template <int LOG2N, int KIND, bool CACHED>
+// kernels (STAGED: the input copied into shared memory one task ahead) the
+// stage and the block ids (batch_warp_bytes in all).
+template <int LOG2N, int KIND, bool CACHED, bool STAGED>
 __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, long long t1,
                                             const int* cache, int set_lo, int32_t* pbuf) {
   using M = BatchMath<LOG2N, KIND == 1>;
@@ -579,7 +578,6 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
   const SetTableShape sh{LOG2N, M::LOG2E, R, p.perms};
   const int rw = sh.round_words();
 
-  constexpr bool STAGED = batch_staged(LOG2N, KIND);
   char* stage = reinterpret_cast<char*>(pbuf + perm_buf_words(LOG2N, KIND));
   int* ids = reinterpret_cast<int*>(stage + BatchStage<LOG2N, KIND>::BYTES);  // [2][G]
   if constexpr (STAGED) {
@@ -662,7 +660,7 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
 // range of warp tasks.  `smem` is the dynamic shared memory: the cached set
 // tables (max_cached_sets x set_words) followed by batch_warp_bytes per warp.
 // KIND 0: int16 -> int32 forward; KIND 1: int32 -> int16 inverse.
-template <int LOG2N, int KIND>
+template <int LOG2N, int KIND, bool STAGED = batch_staged(LOG2N, KIND)>
 __device__ __forceinline__ void batch_cta(const BatchParams& p, long long cta, long long ncta,
                                           int32_t* smem) {
   constexpr int GS = batch_group(LOG2N);                 // schedule group
@@ -705,25 +703,38 @@ __device__ __forceinline__ void batch_cta(const BatchParams& p, long long cta, l
   }
   __syncthreads();
 
-  int32_t* wbuf = pbuf + (size_t)warp * (batch_warp_bytes<LOG2N, KIND>() / 4);
+  int32_t* wbuf = pbuf + (size_t)warp * (batch_warp_bytes<LOG2N, KIND, STAGED>() / 4);
   if (cached)
-    batch_tasks<LOG2N, KIND, true>(p, t0, t1, cache, set_lo, wbuf);
+    batch_tasks<LOG2N, KIND, true, STAGED>(p, t0, t1, cache, set_lo, wbuf);
   else
-    batch_tasks<LOG2N, KIND, false>(p, t0, t1, cache, set_lo, wbuf);
+    batch_tasks<LOG2N, KIND, false, STAGED>(p, t0, t1, cache, set_lo, wbuf);
 }
 
 // Dynamic shared memory of batch_cta for block size 2^LOG2N without the set
 // tables: batch_warp_bytes per warp.
-template <int LOG2N, int KIND>
+template <int LOG2N, int KIND, bool STAGED = batch_staged(LOG2N, KIND)>
 __host__ __device__ inline size_t batch_pbuf_bytes(int threads) {
-  return (size_t)(threads / 32) * batch_warp_bytes<LOG2N, KIND>();
+  return (size_t)(threads / 32) * batch_warp_bytes<LOG2N, KIND, STAGED>();
 }
 
-template <int LOG2N, int KIND>
+// The kernel may be launched with fewer threads than batch_threads (a
+// multiple of 32): the launch tuning picks the warps per CTA.
+template <int LOG2N, int KIND, bool STAGED>
 __global__ void __launch_bounds__(batch_threads(LOG2N, KIND), 1) hygt_batch_kernel(BatchParams p) {
   extern __shared__ __align__(16) int32_t bsmem[];
-  batch_cta<LOG2N, KIND>(p, blockIdx.x, gridDim.x, bsmem);
+  batch_cta<LOG2N, KIND, STAGED>(p, blockIdx.x, gridDim.x, bsmem);
 }
+
+// Launch tuning of the bucketed kernels (one per plan and direction): warps
+// per CTA (0: batch_threads / 32), CTAs per SM (0: as many as fit), and
+// whether the input is staged in shared memory one task ahead (-1: the
+// measured default batch_staged; 0 / 1: off / on; staging exists for
+// N = 32 and 64 only).
+struct BatchTune {
+  int warps = 0;
+  int ctas_per_sm = 0;
+  int stage = -1;
+};
 
 // Set tables a CTA keeps in shared memory: as many as its share of the
 // sorted order usually spans (a CTA that spans more reads the tables from
@@ -741,7 +752,9 @@ __host__ inline int batch_cached_sets(size_t max_smem, size_t pbuf, size_t set_b
 // Host launchers (batch_int.cu).
 cudaError_t batch_build(const uint16_t* d_set, long long nblocks, int num_sets, int group,
                         void* d_work, cudaStream_t stream);
-cudaError_t launch_batch_fwd(int log2n, const BatchParams& p, cudaStream_t stream);
-cudaError_t launch_batch_inv(int log2n, const BatchParams& p, cudaStream_t stream);
+cudaError_t launch_batch_fwd(int log2n, const BatchParams& p, cudaStream_t stream,
+                             const BatchTune& tune = BatchTune());
+cudaError_t launch_batch_inv(int log2n, const BatchParams& p, cudaStream_t stream,
+                             const BatchTune& tune = BatchTune());
 
 }  // namespace hygt

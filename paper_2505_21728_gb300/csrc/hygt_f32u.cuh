@@ -47,11 +47,11 @@ __host__ __device__ inline size_t f32u_smem_bytes(int threads, int rounds) {
   return f32u_table_bytes<LOG2N>(rounds) + (size_t)(threads / 32) * M::GROUPS * M::RW * 4;
 }
 
-template <int LOG2N, bool INV, int P>
+template <int LOG2N, bool INV, bool PADDED, int P>
 __device__ __forceinline__ void f32u_pass(float (&v)[GradMap<LOG2N>::K][GradMap<LOG2N>::E],
                                           const unsigned char* rtab, int lane) {
   using M = GradMap<LOG2N>;
-  using T = GradTab<LOG2N, true>;
+  using T = GradTab<LOG2N, PADDED>;
   constexpr int E = M::E;
   constexpr int K = M::K;
   if constexpr (P < M::LOG2E) {
@@ -91,13 +91,15 @@ __device__ __forceinline__ void f32u_pass(float (&v)[GradMap<LOG2N>::K][GradMap<
   }
 }
 
-template <int LOG2N, bool INV, int J>
+// All passes of one round; PADDED: the shared-memory table layout, else the
+// plan's global layout [k][N/2] (hygt_grad.cuh, GradTab).
+template <int LOG2N, bool INV, bool PADDED, int J>
 __device__ __forceinline__ void f32u_round(float (&v)[GradMap<LOG2N>::K][GradMap<LOG2N>::E],
                                            const unsigned char* rtab, int lane) {
   if constexpr (J < LOG2N) {
     constexpr int P = INV ? LOG2N - 1 - J : J;
-    f32u_pass<LOG2N, INV, P>(v, rtab, lane);
-    f32u_round<LOG2N, INV, J + 1>(v, rtab, lane);
+    f32u_pass<LOG2N, INV, PADDED, P>(v, rtab, lane);
+    f32u_round<LOG2N, INV, PADDED, J + 1>(v, rtab, lane);
   }
 }
 
@@ -161,7 +163,7 @@ __global__ void __launch_bounds__(kF32uThreads, 1) hygt_f32u_kernel(F32uParams p
           __syncwarp();
         }
       }
-      f32u_round<LOG2N, INV, 0>(v, tab + (size_t)r * T::ROUND, lane);
+      f32u_round<LOG2N, INV, true, 0>(v, tab + (size_t)r * T::ROUND, lane);
       if (!INV && has_perm) {  // gather: v'[e] = v[perm[e]]
 #pragma unroll
         for (int k = 0; k < K; ++k) {

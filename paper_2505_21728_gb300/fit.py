@@ -138,3 +138,35 @@ def quantise_angles(theta, angle_bits=8):
     t = np.asarray(theta, np.float64)
     q = np.rint(t * (1 << angle_bits) / (2.0 * math.pi)).astype(np.int64) % (1 << angle_bits)
     return q.astype(np.uint8)
+
+
+def rounds_ladder(x, log2n, rounds_list, iters, lr=0.02, restarts=3, seed=0, angle_bits=8):
+    """HyGT variants H(R) for increasing R fitted to one class (Table II's
+    columns H(2) .. H(5); Sec. V objective), each quantised to one byte per
+    angle (Sec. IV).
+
+    The smallest R is fitted with seeded restarts; every larger R starts
+    from the previous variant's angles with the added rounds at zero angle
+    (the identity), so it starts from the previous variant's transform and
+    objective.  Returns one dict per R: the FP32 angles, J, the 8-bit
+    angle indices q, J at the angles q stands for, and the parameter bytes
+    at one byte per angle.
+    """
+    out = []
+    prev = None
+    N = 1 << int(log2n)
+    for R in sorted(rounds_list):
+        f = CodingGainFit(x, log2n, R)
+        if prev is None:
+            th, J, _ = f.fit(restarts, iters, lr=lr, seed=seed)
+        else:
+            th0 = np.zeros((R, log2n, N // 2), np.float64)
+            th0[:prev.shape[0]] = prev
+            th, _, J = f.run(th0, iters, lr=lr)
+        q = quantise_angles(th, angle_bits)
+        Jq, _ = f.objective(q.astype(np.float64) * (2.0 * math.pi / (1 << angle_bits)))
+        out.append({"rounds": R, "theta": th, "J": J, "q": q, "J_q": Jq,
+                    "param_bytes": hygt.hygt_param_bytes(int(log2n), R, 1)})
+        prev = th
+        f.close()
+    return out

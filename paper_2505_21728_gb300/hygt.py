@@ -64,7 +64,8 @@ def _load() -> ctypes.CDLL:
     L.hygt_batch_workspace_bytes.restype = ctypes.c_size_t
     L.hygt_batch_build.argtypes = [P, P, i64, P, ctypes.c_size_t, P]
     L.hygt_batch_build.restype = i32
-    for name in ("hygt_forward_batch", "hygt_inverse_batch"):
+    for name in ("hygt_forward_batch", "hygt_inverse_batch", "hygt_forward_batch_f32",
+                 "hygt_inverse_batch_f32"):
         f = getattr(L, name)
         f.argtypes = [P, P, P, P, i64, P, P]
         f.restype = i32
@@ -116,6 +117,10 @@ def _load() -> ctypes.CDLL:
     L.dense_klt_build.restype = i32
     L.dense_klt_apply.argtypes = [P, P, P, P, i64, i32, P, P]
     L.dense_klt_apply.restype = i32
+    L.hygt_batch_set_tuning.argtypes = [P, i32, i32, i32, i32]
+    L.hygt_batch_set_tuning.restype = i32
+    L.hygt_batch_get_tuning.argtypes = [P, i32] + [ctypes.POINTER(i32)] * 4
+    L.hygt_batch_get_tuning.restype = i32
     L.hygt_mixed_ctas.argtypes = []
     L.hygt_mixed_ctas.restype = i32
     for name in ("hygt_forward_mixed", "hygt_inverse_mixed"):
@@ -210,6 +215,14 @@ def hygt_forward_batch(plan, d_work, d_x, d_y, nblocks, stream, d_status):
 
 def hygt_inverse_batch(plan, d_work, d_y, d_x, nblocks, stream, d_status):
     return int(_lib.hygt_inverse_batch(plan, d_work, d_y, d_x, nblocks, stream, d_status))
+
+
+def hygt_forward_batch_f32(plan, d_work, d_x, d_y, nblocks, stream, d_status):
+    return int(_lib.hygt_forward_batch_f32(plan, d_work, d_x, d_y, nblocks, stream, d_status))
+
+
+def hygt_inverse_batch_f32(plan, d_work, d_y, d_x, nblocks, stream, d_status):
+    return int(_lib.hygt_inverse_batch_f32(plan, d_work, d_y, d_x, nblocks, stream, d_status))
 
 
 def hygt_forward_static(plan, d_x, d_y, d_set, nblocks, stream, d_status):
@@ -333,6 +346,19 @@ def dense_klt_build(d, d_set, nblocks, d_work, work_bytes, stream):
 
 def dense_klt_apply(d, d_work, d_x, d_y, nblocks, kind, stream, d_status):
     return int(_lib.dense_klt_apply(d, d_work, d_x, d_y, nblocks, kind, stream, d_status))
+
+
+def hygt_batch_set_tuning(plan, inverse, warps_per_cta, ctas_per_sm, stage):
+    return int(_lib.hygt_batch_set_tuning(plan, int(inverse), int(warps_per_cta),
+                                          int(ctas_per_sm), int(stage)))
+
+
+def hygt_batch_get_tuning(plan, inverse):
+    """(warps_per_cta, ctas_per_sm, stage, max_warps) of one direction."""
+    vals = [ctypes.c_int() for _ in range(4)]
+    _check(_lib.hygt_batch_get_tuning(plan, int(inverse), *[ctypes.byref(v) for v in vals]),
+           "hygt_batch_get_tuning")
+    return tuple(v.value for v in vals)
 
 
 def hygt_mixed_ctas():
@@ -643,20 +669,25 @@ class HostPipe:
         self.handle = h
         self.plan = plan
 
-    def roundtrip(self, x, sets=None, y=None, xr=None):
+    def roundtrip(self, x, sets=None, y=None, xr=None, coefficients=True):
         """x: int16 CPU tensor [B, N]; sets: int16/uint16 CPU tensor [B] or
-        None.  Returns (y int32 [B, N], xr int16 [B, N], status)."""
+        None.  Returns (y int32 [B, N] or None, xr int16 [B, N], status);
+        with coefficients=False only the reconstruction comes back."""
         import torch
         N = self.plan.N
         if x.is_cuda or x.dtype != torch.int16 or x.dim() != 2 or x.shape[1] != N or \
                 not x.is_contiguous():
             raise ValueError("x must be a contiguous int16 CPU tensor [nblocks, %d]" % N)
         B = x.shape[0]
-        if y is None:
+        if y is None and coefficients:
             y = torch.empty((B, N), dtype=torch.int32, pin_memory=x.is_pinned())
+        if not coefficients:
+            y = None
         if xr is None:
             xr = torch.empty((B, N), dtype=torch.int16, pin_memory=x.is_pinned())
         for t, dt, name in ((y, torch.int32, "y"), (xr, torch.int16, "xr")):
+            if t is None:
+                continue
             if t.is_cuda or t.dtype != dt or tuple(t.shape) != (B, N) or not t.is_contiguous():
                 raise ValueError("%s must be a contiguous %s CPU tensor [%d, %d]" % (name, dt, B, N))
         ps = None
@@ -665,8 +696,8 @@ class HostPipe:
                     sets.dtype not in (torch.int16, torch.uint16):
                 raise ValueError("sets must be a contiguous 16-bit CPU tensor [nblocks]")
             ps = sets.data_ptr()
-        st, status = hygt_host_roundtrip(self.handle, x.data_ptr(), ps, y.data_ptr(),
-                                         xr.data_ptr(), B)
+        st, status = hygt_host_roundtrip(self.handle, x.data_ptr(), ps,
+                                         None if y is None else y.data_ptr(), xr.data_ptr(), B)
         _check(st, "hygt_host_roundtrip")
         return y, xr, status
 
@@ -698,6 +729,15 @@ class Batch:
         if nbytes == 0:
             raise HygtError(HYGT_ERR_ARG, "hygt_batch_workspace_bytes")
         self.work = torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+    @classmethod
+    def on_workspace(cls, plan: Plan, nblocks: int, work):
+        """A Batch over an existing schedule workspace (a uint8 CUDA tensor
+        holding a schedule built for this plan and block count), e.g. one
+        class of a MixedBatch."""
+        b = cls.__new__(cls)
+        b.plan, b.nblocks, b.work = plan, int(nblocks), work
+        return b
 
     def build(self, sets=None, stream=None):
         import torch
@@ -734,6 +774,21 @@ class Batch:
             out = torch.empty(y.shape, dtype=torch.int16, device=y.device)
         return self._run(hygt_inverse_batch, "hygt_inverse_batch", y, out, torch.int32,
                          torch.int16, status, stream)
+
+    def forward_f32(self, x, out=None, status=None, stream=None):
+        """FP32 forward through the bucketed schedule (N >= 16)."""
+        import torch
+        if out is None:
+            out = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+        return self._run(hygt_forward_batch_f32, "hygt_forward_batch_f32", x, out,
+                         torch.float32, torch.float32, status, stream)
+
+    def inverse_f32(self, y, out=None, status=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(y.shape, dtype=torch.float32, device=y.device)
+        return self._run(hygt_inverse_batch_f32, "hygt_inverse_batch_f32", y, out,
+                         torch.float32, torch.float32, status, stream)
 
 
 class MixedBatch:

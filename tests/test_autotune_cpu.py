@@ -104,3 +104,38 @@ def test_single_active_class_takes_every_cta(at, monkeypatch):
     monkeypatch.setattr(at, "_time_pair", no_timing)
     mb = _FakeMixed(hygt, [0, 5000, 0])
     assert at.tune_split(mb, reps=1, use_cache=False) == [0, G, 0]
+
+
+def test_batch_tuner_picks_the_modelled_best(at, monkeypatch):
+    """tune_batch with the GPU timing replaced by a cost model: it must set
+    the cheapest fitting point for each direction and skip refused ones."""
+    from paper_2505_21728_gb300 import hygt
+    state = {}
+
+    def fake_set(plan, inv, w, c, s):
+        if c == 2 and w > 8:  # pretend these do not fit
+            return hygt.HYGT_ERR_UNSUPPORTED
+        state[inv] = (w, c, s)
+        return hygt.HYGT_OK
+
+    def fake_get(plan, inv):
+        return state.get(inv, (0, 0, -1)) + (12,)
+
+    monkeypatch.setattr(hygt, "hygt_batch_set_tuning", fake_set)
+    monkeypatch.setattr(hygt, "hygt_batch_get_tuning", fake_get)
+
+    class _P:
+        handle, N, rounds, num_sets, log2n = 1, 64, 2, 105, 6
+
+    class _B:
+        plan, nblocks = _P(), 1000
+
+    def model(direction, cand):
+        w, c, s = cand
+        base = 1.0 + abs(w - 9) * 0.1 + (0.05 if c == 0 else 0.0)
+        return base - (0.2 if s == 1 and direction == "forward" else 0.0)
+
+    res = at.tune_batch(_B(), None, None, None, use_cache=False, time_fn=model)
+    assert res["forward"][:3] == (9, 1, 1)
+    assert res["inverse"][:3] in ((9, 1, 0), (9, 1, 1))
+    assert state[0] == (9, 1, 1)

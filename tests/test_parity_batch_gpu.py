@@ -178,3 +178,94 @@ def test_batch_workload_16x16_full(gpu, orc):
         assert np.array_equal(y[sl].cpu().numpy(), ye), off
         xe, _ = orc.inv_int(ye, d["angle_idx"], w.log2n, w.rounds, d["perms"], d["sets"][sl])
         assert np.array_equal(xr[sl].cpu().numpy(), xe), off
+
+
+@pytest.mark.parametrize("log2n", [4, 5, 6, 7, 8])
+@pytest.mark.parametrize("rounds,perm_kind", [(1, "none"), (2, "between"), (3, "all")])
+def test_batch_f32_parity(gpu, orc, log2n, rounds, perm_kind):
+    """The set-bucketed FP32 kernels against the FP64 oracle (max abs error
+    <= 1e-5 of max |y|), with skip and bad set indices."""
+    import torch
+    N = 1 << log2n
+    S, B = 9, 4003
+    q = inputs.angle_indices(S, rounds, log2n, seed=log2n + 3 * rounds)
+    perms = None if perm_kind == "none" else inputs.permutations(
+        S, rounds, N, seed=5, between_rounds_only=(perm_kind == "between"))
+    x = inputs.laplacian_blocks(B, N, 50.0, -32768, 32767, seed=log2n + 1).astype(np.float32)
+    sets = inputs.set_indices(B, S, seed=log2n + 2, skip_frac=0.1)
+    sets[7] = 50  # a bad set index
+    plan = gpu.Plan(log2n, rounds, q, perms)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    b = gpu.Batch(plan, B).build(_t(sets))
+    y = b.forward_f32(_t(x), status=st)
+    xr = b.inverse_f32(y, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == gpu.HYGT_ERR_SET_INDEX
+    theta = inputs.theta_from_indices(q)
+    ye, ste = orc.fwd_f64(x.astype(np.float64), theta, log2n, rounds, perms, sets)
+    assert ste == orc.ERR_SET
+    yg = y.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(yg - ye)) <= 1e-5 * np.max(np.abs(ye))
+    xe, _ = orc.inv_f64(yg, theta, log2n, rounds, perms, sets)
+    assert np.max(np.abs(xr.cpu().numpy() - xe)) <= 1e-5 * np.max(np.abs(xe))
+    assert np.all(yg[7] == 0)
+    plan.close()
+
+
+@pytest.mark.parametrize("log2n,rounds", [(4, 2), (5, 2), (6, 2), (7, 2), (8, 3)])
+def test_batch_every_launch_tuning_bit_exact(gpu, orc, log2n, rounds):
+    """Every point the launch tuner can pick (warps per CTA, CTAs per SM,
+    staging depth) gives the oracle's integers, forward and inverse."""
+    import torch
+    from paper_2505_21728_gb300 import autotune
+    N, S = 1 << log2n, 105
+    B = 20011 if log2n <= 6 else 3001
+    q = inputs.angle_indices(S, rounds, log2n, seed=log2n + 40)
+    perms = inputs.permutations(S, rounds, N, seed=41)
+    x = inputs.laplacian_blocks(B, N, 20.0, -32768, 32767, seed=log2n + 42)
+    sets = inputs.set_indices(B, S, seed=43, skip_frac=0.1)
+    ye, _ = orc.fwd_int(x, q, log2n, rounds, perms, sets)
+    xe, _ = orc.inv_int(ye, q, log2n, rounds, perms, sets)
+    plan = gpu.Plan(log2n, rounds, q, perms)
+    b = gpu.Batch(plan, B).build(_t(sets))
+    dx, dy = _t(x), _t(ye)
+    ran = 0
+    for inv in (0, 1):
+        max_w = gpu.hygt_batch_get_tuning(plan.handle, inv)[3]
+        for cand in autotune.batch_candidates(max_w, log2n):
+            assert gpu.hygt_batch_set_tuning(plan.handle, inv, *cand) == gpu.HYGT_OK
+            st = torch.zeros(1, dtype=torch.int32, device="cuda")
+            try:
+                out = b.forward(dx, status=st) if inv == 0 else b.inverse(dy, status=st)
+            except gpu.HygtError as e:
+                assert e.code == gpu.HYGT_ERR_UNSUPPORTED  # does not fit: refused
+                continue
+            torch.cuda.synchronize()
+            assert int(st.item()) == 0, cand
+            assert np.array_equal(out.cpu().numpy(), xe if inv else ye), (inv, cand)
+            ran += 1
+        gpu.hygt_batch_set_tuning(plan.handle, inv, 0, 0, -1)
+    assert ran >= 8
+    plan.close()
+
+
+def test_tune_batch_sets_a_fitting_point(gpu, tmp_path, monkeypatch):
+    """The tuner times the candidates on the GPU and leaves the fastest set."""
+    import torch
+    from paper_2505_21728_gb300 import autotune
+    monkeypatch.setenv("HYGT_AUTOTUNE_CACHE", str(tmp_path / "cache.json"))
+    log2n, R, S, B = 6, 2, 105, 1 << 18
+    q = inputs.angle_indices(S, R, log2n, seed=1)
+    plan = gpu.Plan(log2n, R, q)
+    x = _t(inputs.laplacian_blocks(B, 64, 8.0, -1024, 1023, seed=1))
+    b = gpu.Batch(plan, B).build(_t(inputs.set_indices(B, S, seed=1)))
+    y = torch.empty((B, 64), dtype=torch.int32, device="cuda")
+    xr = torch.empty_like(x)
+    res = autotune.tune_batch(b, x, y, xr, reps=2)
+    for inv, d in ((0, "forward"), (1, "inverse")):
+        w, c, s, ms = res[d]
+        assert gpu.hygt_batch_get_tuning(plan.handle, inv)[:3] == (w, c, s)
+        assert ms > 0
+    again = autotune.tune_batch(b, x, y, xr, reps=2)  # from the cache
+    assert again == {k: tuple(v) for k, v in res.items()}
+    plan.close()

@@ -57,3 +57,26 @@ def test_host_roundtrip_no_sets_and_bad_set(gpu, orc):
     ye, _ = orc.fwd_int(x, q, 6, rounds, None, sets)
     assert np.array_equal(y.numpy(), ye)
     pipe.close()
+
+
+def test_host_roundtrip_reconstruction_only(gpu, orc):
+    """With no coefficient buffer only the reconstruction comes back; it
+    equals the oracle's inverse of its forward."""
+    import torch
+    log2n, rounds, S, B = 6, 2, 105, 300007
+    N = 1 << log2n
+    q = inputs.angle_indices(S, rounds, log2n, seed=12)
+    perms = inputs.permutations(S, rounds, N, seed=12)
+    x = inputs.laplacian_blocks(B, N, 8.0, -1024, 1023, seed=12)
+    sets = inputs.set_indices(B, S, seed=12, skip_frac=0.1)
+    plan = gpu.Plan(log2n, rounds, q, perms)
+    pipe = gpu.HostPipe(plan, 65536)
+    y, xr, status = pipe.roundtrip(torch.from_numpy(x).pin_memory(),
+                                   torch.from_numpy(sets.view(np.int16)).pin_memory(),
+                                   coefficients=False)
+    assert y is None and status == 0
+    ye, _ = orc.fwd_int(x, q, log2n, rounds, perms, sets)
+    xe, _ = orc.inv_int(ye, q, log2n, rounds, perms, sets)
+    assert np.array_equal(xr.numpy(), xe)
+    pipe.close()
+    plan.close()
