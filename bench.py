@@ -58,6 +58,9 @@ def parse_args():
                     help="--case mixed: divide the frame batch's block counts")
     ap.add_argument("--no-tune", action="store_true",
                     help="--case mixed: default CTA split instead of the autotuner's")
+    ap.add_argument("--autotune-cache", action="store_true",
+                    help="reuse the launch tuning cached by an earlier run (profiling runs "
+                         "then launch no tuning kernels)")
     ap.add_argument("--fwd-tuning", default=None,
                     help="--case batch/stress: launch tuning of the forward, "
                          "'warps,ctas_per_sm,stage' (hygt_batch_set_tuning)")
@@ -187,20 +190,28 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_sha() -> str:
+# the sources of the set-bucketed integer kernels (the benchmark's dominant kernels)
+BATCH_SOURCES = ("hygt_batch.cuh", "hygt_batch_launch.cuh", "hygt_device.cuh", "hygt_primary.cuh",
+                 "hygt_launch.cuh", "batch_int.cu", "batch_fwd.cu", "batch_inv.cu")
+
+
+def kernel_source_sha(files=BATCH_SOURCES) -> str:
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2505_21728_gb300", "csrc", "*"))):
+    for name in sorted(files):
+        p = os.path.join(ROOT, "paper_2505_21728_gb300", "csrc", name)
         with open(p, "rb") as f:
-            h.update(os.path.basename(p).encode())
+            h.update(name.encode())
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str, workload: str):
+def ncu_traffic(kernel: str, workload: str, tuning=None):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel sources (a line 'bench-traffic: kernel=... workload=...
-    sha=... bytes_per_launch=...' in profiles/*.md); else None."""
+    the current kernel sources and (when given) the same launch tuning (a line
+    'bench-traffic: kernel=... workload=... sha=... tuning=w,c,s
+    bytes_per_launch=...' in profiles/*.md); else None."""
     sha = kernel_source_sha()
+    want = None if tuning is None else ",".join(str(int(v)) for v in tuning[:3])
     for p in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
         with open(p) as f:
             for line in f:
@@ -208,7 +219,7 @@ def ncu_traffic(kernel: str, workload: str):
                     continue
                 kv = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
                 if kv.get("kernel") == kernel and kv.get("workload") == workload \
-                        and kv.get("sha") == sha:
+                        and kv.get("sha") == sha and (want is None or kv.get("tuning") == want):
                     return int(float(kv["bytes_per_launch"]))
     return None
 
@@ -313,7 +324,7 @@ def run_ours(args, rank, world, local):
     # outside the timed region
     from paper_2505_21728_gb300 import autotune
     batch.build(d_s)
-    tuning = autotune.tune_batch(batch, d_x, d_y, d_xr, reps=3, use_cache=False)
+    tuning = autotune.tune_batch(batch, d_x, d_y, d_xr, reps=3, use_cache=args.autotune_cache)
 
     # One step: bucket the batch by set, forward, inverse (5 kernels).
     K = args.steps
@@ -362,8 +373,9 @@ def run_ours(args, rank, world, local):
     peak, peak_kind = measured_peaks()
     achieved = bytes_per_launch / (dom_ms / 1000.0) / 1e9
     step_bytes = 2 * bytes_per_launch
+    dom_tuning = tuning["forward" if dom_name == "hygt_batch_forward" else "inverse"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": ncu_traffic(dom_name, w.name),
+                "frac": achieved / peak, "traffic": ncu_traffic(dom_name, w.name, dom_tuning),
                 "kernel": dom_name, "peak_source": peak_kind,
                 "bytes_per_launch": bytes_per_launch,
                 "fwd_ms": f_avg, "inv_ms": i_avg, "schedule_ms": statistics.mean(build_ms),
@@ -624,19 +636,35 @@ def secondary_leg(dev, stream, reps=5):
     s = torch.from_numpy(inputs.set_indices(B, S, seed=7, skip_frac=0.1).view(np.int16)).to(dev)
     y = torch.empty((B, 64), dtype=torch.int32, device=dev)
     xr = torch.empty_like(x)
-    f_ms = _timed(lambda: plan.secondary_forward(x, 3, s, out=y), dev, stream, reps)
-    i_ms = _timed(lambda: plan.secondary_inverse(y, 3, s, out=xr), dev, stream, reps)
+    # the bucketed kernels with the primary fused (one step: schedule,
+    # forward, inverse), the launch tuning's staging choice timed
+    b = hygt.Batch(plan, B, device=dev)
+    b_ms = _timed(lambda: b.build(s), dev, stream, reps)
+    best = None
+    for stage in (0, 1):
+        for inv in (0, 1):
+            hygt._check(hygt.hygt_batch_set_tuning(plan.handle, inv, 0, 0, stage), "tuning")
+        f = _timed(lambda: b.secondary_forward(x, 3, out=y), dev, stream, reps)
+        i = _timed(lambda: b.secondary_inverse(y, 3, out=xr), dev, stream, reps)
+        if best is None or f + i < best[0] + best[1]:
+            best = (f, i, stage)
+    f_ms, i_ms, stage = best
+    # context: the generic kernel (any block size, no schedule)
+    gf_ms = _timed(lambda: plan.secondary_forward(x, 3, s, out=y), dev, stream, reps)
+    gi_ms = _timed(lambda: plan.secondary_inverse(y, 3, s, out=xr), dev, stream, reps)
     peak, kind = measured_peaks()
     bpl = B * (6 * 64 + 2)
     dom = max(f_ms, i_ms)
     plan.close()
     return {"workload": "16 frames of 3840x2160 in 8x8 blocks (%d blocks), 8x8 HyGT secondary, "
                         "2 rounds, 105 sets, 10%% primary only" % B,
-            "fwd_ms": f_ms, "inv_ms": i_ms, "value": B / ((f_ms + i_ms) / 1000.0),
-            "unit": "blocks/s",
+            "fwd_ms": f_ms, "inv_ms": i_ms, "schedule_ms": b_ms, "stage": stage,
+            "value": B / ((f_ms + i_ms + b_ms) / 1000.0), "unit": "blocks/s",
+            "generic_kernel": {"fwd_ms": gf_ms, "inv_ms": gi_ms},
             "roofline": {"bound": "hbm", "achieved": bpl / (dom / 1000.0) / 1e9, "peak": peak,
                          "unit": "GB/s", "frac": bpl / (dom / 1000.0) / 1e9 / peak,
-                         "peak_source": kind, "kernel": "hygt_secondary_kernel"}}
+                         "peak_source": kind,
+                         "kernel": "hygt_batch_kernel<6, *, *, true> (DCT-II primary fused)"}}
 
 
 def pmpt_leg(dev, stream, reps=5, B=1 << 22):
@@ -1124,6 +1152,28 @@ def case_stress_f32(args):
     return run
 
 
+def case_secondary_batch(args):
+    """secondary pipeline of 8x8 blocks through the bucketed kernels with the
+    primary fused: schedule, forward, inverse"""
+    import numpy as np
+    import torch
+    from paper_2505_21728_gb300 import hygt, inputs
+    B = args.nblocks or 2073600
+    q = inputs.angle_indices(105, 2, 6, seed=7)
+    plan = hygt.Plan(6, 2, q, inputs.permutations(105, 2, 64, seed=7))
+    x = torch.from_numpy(inputs.laplacian_blocks(B, 64, 8.0, -1024, 1023, seed=7)).cuda()
+    s = torch.from_numpy(inputs.set_indices(B, 105, seed=7, skip_frac=0.1).view(np.int16)).cuda()
+    b = hygt.Batch(plan, B)
+    y = torch.empty((B, 64), dtype=torch.int32, device="cuda")
+    xr = torch.empty_like(x)
+
+    def run():
+        b.build(s)
+        b.secondary_forward(x, 3, out=y)
+        b.secondary_inverse(y, 3, out=xr)
+    return run
+
+
 def case_secondary(args):
     """fused DCT-II primary + 8x8 HyGT secondary, forward + inverse, 8x8 blocks"""
     import numpy as np
@@ -1164,7 +1214,8 @@ def case_pmpt(args):
 CASES = {"batch": case_batch, "stress": case_stress, "direct": case_direct,
          "mixed": case_mixed, "dense": case_dense, "grad": case_grad,
          "coding_gain": case_coding_gain, "stress_f32": case_stress_f32,
-         "secondary": case_secondary, "pmpt": case_pmpt}
+         "secondary": case_secondary, "secondary_batch": case_secondary_batch,
+         "pmpt": case_pmpt}
 
 
 def run_case(args):

@@ -178,8 +178,9 @@ hygt_status hygt_inverse_batch(hygt_plan plan, const void *d_work, const int32_t
  *        registers allow); the shared memory is split between them;
  *   stage          -1: the default; 0: blocks read straight from global
  *        memory; 1: each warp copies its next task's blocks into shared
- *        memory (cp.async) while it transforms the current one (N >= 16;
- *        smaller blocks return HYGT_ERR_UNSUPPORTED).
+ *        memory (cp.async) while it transforms the current one; 2: each
+ *        warp prefetches its next task's blocks into L2 (N >= 16 for 1 and
+ *        2; smaller blocks return HYGT_ERR_UNSUPPORTED).
  * Results do not depend on the tuning.  A choice whose shared memory does
  * not fit makes the next bucketed call return HYGT_ERR_UNSUPPORTED.  Not
  * thread-safe with concurrent calls on the same plan.
@@ -258,7 +259,7 @@ hygt_status hygt_backward_f32(hygt_plan plan, const float *d_y, const float *d_g
  *        (one double) and the weights w_i = 1 / (N ln 2 B v_i) to d_w
  *        (float [N]), for which dJ/dy_{b,i} = w_i y_{b,i}.  A coefficient
  *        with v_i = 0 gets w_i = 0 and makes J = -inf.  The sums are
- *        deterministic (fixed order; FP32 over runs of 16 values, FP64
+ *        deterministic (fixed order; FP32 over runs of 8 values, FP64
  *        beyond).  Async on stream; the plan gives N only.
  *   hygt_backward_diag_f32  the backward of any loss whose gradient with
  *        respect to the outputs is diagonal, dL/dy_{b,i} = d_w[i] y_{b,i}
@@ -317,6 +318,21 @@ hygt_status hygt_secondary_forward(hygt_plan plan, int log2m, const int16_t *d_x
 hygt_status hygt_secondary_inverse(hygt_plan plan, int log2m, const int32_t *d_y, int16_t *d_x,
                                    const uint16_t *d_set, int64_t nblocks, hygt_stream stream,
                                    int *d_status);
+/*
+ *   hygt_secondary_forward_batch / hygt_secondary_inverse_batch  the same
+ *        pipeline for 4x4 (log2m = 2) and 8x8 (log2m = 3) blocks, where the
+ *        secondary covers every coefficient, through the set-bucketed
+ *        kernels with the primary fused: hygt_batch_build(plan, d_set, ...)
+ *        first, then these calls with its d_work and nblocks (same results,
+ *        bit for bit; other log2m: HYGT_ERR_UNSUPPORTED).  The launch tuning
+ *        of hygt_batch_set_tuning applies.
+ */
+hygt_status hygt_secondary_forward_batch(hygt_plan plan, const void *d_work, int log2m,
+                                         const int16_t *d_x, int32_t *d_y, int64_t nblocks,
+                                         hygt_stream stream, int *d_status);
+hygt_status hygt_secondary_inverse_batch(hygt_plan plan, const void *d_work, int log2m,
+                                         const int32_t *d_y, int16_t *d_x, int64_t nblocks,
+                                         hygt_stream stream, int *d_status);
 
 /*
  * General PMPT with explicit index vectors (Sec. III, Eq. 5; Sec. IV,

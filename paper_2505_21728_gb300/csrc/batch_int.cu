@@ -1,4 +1,6 @@
-// batch_int.cu -- launchers of the set-bucketed integer HyGT (see hygt_batch.cuh).
+// batch_int.cu -- the bucketing kernels of the set-bucketed integer HyGT (counting sort of
+// the block ids by transform set; see hygt_batch.cuh).  The transform launchers are in
+// batch_fwd.cu and batch_inv.cu.
 #include "hygt_batch.cuh"
 #include "hygt_launch.cuh"
 
@@ -153,86 +155,6 @@ cudaError_t batch_build(const uint16_t* d_set, long long nblocks, int num_sets, 
   batch_scatter<<<(unsigned)g3, kBucketThreads, local ? 8 * L.nb : 0, stream>>>(
       d_set, nblocks, num_sets, cursor, order);
   return cudaGetLastError();
-}
-
-template <int LOG2N, int KIND, bool STAGED>
-static cudaError_t launch_variant(BatchParams p, cudaStream_t stream, const BatchTune& tune) {
-  auto kern = hygt_batch_kernel<LOG2N, KIND, STAGED>;
-  int dev = 0;
-  cudaError_t err = cudaGetDevice(&dev);
-  if (err != cudaSuccess) return err;
-  const DeviceInfo info = device_info(dev);
-  constexpr int G = batch_task_group(LOG2N, KIND == 1);
-  constexpr int kMaxWarps = batch_threads(LOG2N, KIND) / 32;
-  const int warps = tune.warps > 0 && tune.warps < kMaxWarps ? tune.warps : kMaxWarps;
-  const int threads = warps * 32;
-  const size_t pbuf = batch_pbuf_bytes<LOG2N, KIND, STAGED>(threads);
-  const size_t set_bytes = (size_t)p.set_words * 4;
-  // with several CTAs per SM each gets its share of the shared memory
-  const int want = tune.ctas_per_sm > 0 ? tune.ctas_per_sm : 1;
-  const size_t budget = (size_t)info.max_smem_optin / want - (want > 1 ? 1024 : 0);
-  const int fit = batch_cached_sets(budget, pbuf, set_bytes, p.num_sets, info.sms * want);
-  if (fit < 0 || pbuf > budget) return cudaErrorInvalidConfiguration;
-  p.max_cached_sets = fit;
-  const size_t smem = pbuf + (size_t)fit * set_bytes;
-  static std::atomic<int> attr_set{0};
-  if ((int)smem > attr_set.load()) {
-    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    attr_set.store((int)smem);
-  }
-  int occ = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
-  if (err != cudaSuccess) return err;
-  if (occ < 1) occ = 1;
-  if (tune.ctas_per_sm > 0 && tune.ctas_per_sm < occ) occ = tune.ctas_per_sm;
-  const long long per_cta = (long long)warps * G;
-  long long need = (p.nblocks + per_cta - 1) / per_cta + 1;
-  long long grid = (long long)occ * info.sms;
-  if (need < grid) grid = need;
-  kern<<<(unsigned)grid, threads, smem, stream>>>(p);
-  return cudaGetLastError();
-}
-
-// Staging exists as a tuning choice for N >= 16; smaller blocks keep the
-// measured default (no stage).
-template <int LOG2N, int KIND>
-static cudaError_t launch_batch_sized(const BatchParams& p, cudaStream_t stream,
-                                      const BatchTune& tune) {
-  constexpr bool kDefault = batch_staged(LOG2N, KIND);
-  if constexpr (LOG2N >= 4) {
-    const bool staged = tune.stage < 0 ? kDefault : tune.stage != 0;
-    return staged ? launch_variant<LOG2N, KIND, true>(p, stream, tune)
-                  : launch_variant<LOG2N, KIND, false>(p, stream, tune);
-  } else {
-    return launch_variant<LOG2N, KIND, kDefault>(p, stream, tune);
-  }
-}
-
-template <int KIND>
-static cudaError_t launch_batch(int log2n, const BatchParams& p, cudaStream_t stream,
-                                const BatchTune& tune) {
-  switch (log2n) {
-    case 1: return launch_batch_sized<1, KIND>(p, stream, tune);
-    case 2: return launch_batch_sized<2, KIND>(p, stream, tune);
-    case 3: return launch_batch_sized<3, KIND>(p, stream, tune);
-    case 4: return launch_batch_sized<4, KIND>(p, stream, tune);
-    case 5: return launch_batch_sized<5, KIND>(p, stream, tune);
-    case 6: return launch_batch_sized<6, KIND>(p, stream, tune);
-    case 7: return launch_batch_sized<7, KIND>(p, stream, tune);
-    case 8: return launch_batch_sized<8, KIND>(p, stream, tune);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-cudaError_t launch_batch_fwd(int log2n, const BatchParams& p, cudaStream_t stream,
-                             const BatchTune& tune) {
-  return launch_batch<0>(log2n, p, stream, tune);
-}
-
-cudaError_t launch_batch_inv(int log2n, const BatchParams& p, cudaStream_t stream,
-                             const BatchTune& tune) {
-  return launch_batch<1>(log2n, p, stream, tune);
 }
 
 }  // namespace hygt

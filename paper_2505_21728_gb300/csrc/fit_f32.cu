@@ -11,8 +11,9 @@ int moments_grid(long long n4) {
   int dev = 0;
   cudaGetDevice(&dev);
   const DeviceInfo info = device_info(dev);
-  long long g = (long long)info.sms * 4;
-  const long long need = (n4 + kMomentThreads - 1) / kMomentThreads;
+  long long g = (long long)info.sms * 8;
+  const long long need = (n4 + (long long)kMomentThreads * kMomentUnroll - 1) /
+                         ((long long)kMomentThreads * kMomentUnroll);
   if (need < g) g = need;
   return (int)(g < 1 ? 1 : g);
 }
@@ -22,34 +23,40 @@ __global__ void __launch_bounds__(kMomentThreads) hygt_moments_kernel(
   __shared__ double red[kMomentThreads][4];
   // every float4 this thread reads covers coefficients q .. q + 3 with
   // q = (4 * tid) mod n, because the stride (4 * threads of the grid) is a
-  // multiple of n
+  // multiple of n; kMomentUnroll independent loads are in flight per thread
   const long long stride = (long long)gridDim.x * blockDim.x;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  float run[4] = {0.f, 0.f, 0.f, 0.f};
-  int cnt = 0;
-  for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < n4; f += stride) {
-    const float4 a = __ldcs(y + f);
-    run[0] = fmaf(a.x, a.x, run[0]);
-    run[1] = fmaf(a.y, a.y, run[1]);
-    run[2] = fmaf(a.z, a.z, run[2]);
-    run[3] = fmaf(a.w, a.w, run[3]);
-    if (++cnt == 16) {
+  long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; f + (kMomentUnroll - 1) * stride < n4; f += kMomentUnroll * stride) {
+    float4 a[kMomentUnroll];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        acc[j] += (double)run[j];
-        run[j] = 0.f;
-      }
-      cnt = 0;
+    for (int u = 0; u < kMomentUnroll; ++u) a[u] = __ldcs(y + f + u * stride);
+    float run[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int u = 0; u < kMomentUnroll; ++u) {
+      run[0] = fmaf(a[u].x, a[u].x, run[0]);
+      run[1] = fmaf(a[u].y, a[u].y, run[1]);
+      run[2] = fmaf(a[u].z, a[u].z, run[2]);
+      run[3] = fmaf(a[u].w, a[u].w, run[3]);
     }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[j] += (double)run[j];
+  }
+  for (; f < n4; f += stride) {  // the tail, one float4 at a time
+    const float4 a = __ldcs(y + f);
+    acc[0] += (double)(a.x * a.x);
+    acc[1] += (double)(a.y * a.y);
+    acc[2] += (double)(a.z * a.z);
+    acc[3] += (double)(a.w * a.w);
   }
 #pragma unroll
-  for (int j = 0; j < 4; ++j) red[threadIdx.x][j] = acc[j] + (double)run[j];
+  for (int j = 0; j < 4; ++j) red[threadIdx.x][j] = acc[j];
   __syncthreads();
   // coefficient i is held by the threads t with (4 t) mod n = i - i mod 4
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double s = 0.0;
-    for (int t = i / 4; t < (int)blockDim.x; t += n / 4) s += red[t][i & 3];
-    partials[(size_t)blockIdx.x * n + i] = s;
+    double sm = 0.0;
+    for (int t = i / 4; t < (int)blockDim.x; t += n / 4) sm += red[t][i & 3];
+    partials[(size_t)blockIdx.x * n + i] = sm;
   }
 }
 

@@ -547,7 +547,7 @@ hygt_status hygt_inverse_batch_f32(hygt_plan plan, const void* d_work, const flo
 hygt_status hygt_batch_set_tuning(hygt_plan plan, int inverse, int warps_per_cta,
                                   int ctas_per_sm, int stage) {
   if (!plan || (inverse != 0 && inverse != 1) || warps_per_cta < 0 || ctas_per_sm < 0 ||
-      ctas_per_sm > 8 || stage < -1 || stage > 1)
+      ctas_per_sm > 8 || stage < -1 || stage > 2)
     return HYGT_ERR_ARG;
   const int max_warps = hygt::batch_threads(plan->log2n, inverse) / 32;
   if (warps_per_cta > max_warps) return HYGT_ERR_ARG;
@@ -906,6 +906,36 @@ static hygt_status secondary_run(int inverse, hygt_plan plan, int log2m, const v
   p.group = M * M >= 512 ? 1 : 512 / (M * M);
   p.status = d_status;
   return to_status(hygt::launch_secondary(inverse, p, (cudaStream_t)stream));
+}
+
+// The secondary pipeline of 4x4 / 8x8 blocks through the set-bucketed
+// kernels with the primary fused (schedule from hygt_batch_build).
+static hygt_status secondary_batch_run(int inverse, hygt_plan plan, const void* d_work,
+                                       int log2m, const void* in, void* out, int64_t nblocks,
+                                       hygt_stream stream, int* d_status) {
+  hygt_status s = check_io(plan, in, out, nblocks);
+  if (s != HYGT_OK || nblocks == 0) return s;
+  if (plan->is_float) return HYGT_ERR_UNSUPPORTED;
+  if (log2m != 2 && log2m != 3) return HYGT_ERR_UNSUPPORTED;
+  if (plan->log2n != 2 * log2m) return HYGT_ERR_ARG;
+  if (!d_work || !aligned16(d_work) || nblocks > kBatchMaxBlocks) return HYGT_ERR_ARG;
+  const hygt::BatchParams p = make_batch_params(plan, d_work, in, out, nblocks, d_status);
+  cudaError_t e = hygt::launch_batch_primary(plan->log2n, inverse, p, (cudaStream_t)stream,
+                                             plan->tune[inverse]);
+  if (e == cudaErrorInvalidConfiguration) return HYGT_ERR_UNSUPPORTED;
+  return to_status(e);
+}
+
+hygt_status hygt_secondary_forward_batch(hygt_plan plan, const void* d_work, int log2m,
+                                         const int16_t* d_x, int32_t* d_y, int64_t nblocks,
+                                         hygt_stream stream, int* d_status) {
+  return secondary_batch_run(0, plan, d_work, log2m, d_x, d_y, nblocks, stream, d_status);
+}
+
+hygt_status hygt_secondary_inverse_batch(hygt_plan plan, const void* d_work, int log2m,
+                                         const int32_t* d_y, int16_t* d_x, int64_t nblocks,
+                                         hygt_stream stream, int* d_status) {
+  return secondary_batch_run(1, plan, d_work, log2m, d_y, d_x, nblocks, stream, d_status);
 }
 
 hygt_status hygt_secondary_forward(hygt_plan plan, int log2m, const int16_t* d_x, int32_t* d_y,

@@ -35,6 +35,7 @@
 #include <stdint.h>
 
 #include "hygt_device.cuh"
+#include "hygt_primary.cuh"
 
 namespace hygt {
 
@@ -551,13 +552,99 @@ __device__ __forceinline__ void stage_read(const char* stage, int k, int lane32,
   }
 }
 
+// ---------------------------------------------------------------- primary
+// The integer DCT-II primary of the secondary-transform pipeline (Sec. VI)
+// for 4x4 (N = 16) and 8x8 (N = 64) blocks, whose secondary HyGT covers every
+// coefficient.  In the lane-group layout a lane holds RPL = E / M whole rows
+// of its block (row l RPL + q in registers q M .. q M + M - 1); the row
+// stage runs in registers, the column stage after a transpose through the
+// block's region of the permutation buffer (word of (row r, column c):
+// r S + c; S = 9 for 8x8 spreads a warp's accesses over the 32 banks), after
+// which a lane holds RPL whole columns.
+template <int LOG2N>
+struct PrimaryShape {
+  static constexpr int M = LOG2N == 4 ? 4 : 8;
+  static constexpr int E = 1 << batch_log2e(LOG2N);
+  static constexpr int RPL = E / M;
+  static constexpr int S = M == 8 ? 9 : 4;
+  static_assert(LOG2N == 4 || LOG2N == 6, "primary for 4x4 and 8x8 blocks");
+  static_assert(S * (M - 1) + M <= perm_region_words(LOG2N), "region too small");
+};
+
+template <int LOG2N>
+__device__ __forceinline__ void prim_rows_to_cols(const int32_t* src, int32_t* dst,
+                                                  int32_t* region, int l) {
+  using P = PrimaryShape<LOG2N>;
+#pragma unroll
+  for (int q = 0; q < P::RPL; ++q)
+#pragma unroll
+    for (int c = 0; c < P::M; ++c) region[(l * P::RPL + q) * P::S + c] = src[q * P::M + c];
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < P::RPL; ++q)
+#pragma unroll
+    for (int r = 0; r < P::M; ++r) dst[q * P::M + r] = region[r * P::S + l * P::RPL + q];
+  __syncwarp();
+}
+
+template <int LOG2N>
+__device__ __forceinline__ void prim_cols_to_rows(const int32_t* src, int32_t* dst,
+                                                  int32_t* region, int l) {
+  using P = PrimaryShape<LOG2N>;
+#pragma unroll
+  for (int q = 0; q < P::RPL; ++q)
+#pragma unroll
+    for (int r = 0; r < P::M; ++r) region[r * P::S + l * P::RPL + q] = src[q * P::M + r];
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < P::RPL; ++q)
+#pragma unroll
+    for (int c = 0; c < P::M; ++c) dst[q * P::M + c] = region[(l * P::RPL + q) * P::S + c];
+  __syncwarp();
+}
+
+// Forward primary of the K blocks of a lane group: rows, then columns.
+// Inverse: columns, then rows, with C transposed.  `pbuf` is the warp's
+// permutation buffer (one region per block of the lane group).
+template <int LOG2N, int KIND>
+__device__ __forceinline__ void batch_primary(
+    int32_t (&v)[BatchMath<LOG2N, KIND == 1>::K][BatchMath<LOG2N, KIND == 1>::E], int32_t* pbuf,
+    int grp, int lane) {
+  using P = PrimaryShape<LOG2N>;
+  using Mth = BatchMath<LOG2N, KIND == 1>;
+  constexpr int E = Mth::E, K = Mth::K, GROUPS = 32 / Mth::L;
+  constexpr int RW = perm_region_words(LOG2N);
+  constexpr bool INV = KIND == 1;
+  static_assert(batch_perm_k(LOG2N, KIND) == K, "one buffer region per block");
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    int32_t* region = pbuf + (k * GROUPS + grp) * RW;
+    int32_t t[E], u[E];
+    if (!INV) {
+#pragma unroll
+      for (int q = 0; q < P::RPL; ++q) dct_stage<P::M, false>(v[k] + q * P::M, t + q * P::M);
+      prim_rows_to_cols<LOG2N>(t, u, region, lane);
+#pragma unroll
+      for (int q = 0; q < P::RPL; ++q) dct_stage<P::M, false>(u + q * P::M, t + q * P::M);
+      prim_cols_to_rows<LOG2N>(t, v[k], region, lane);
+    } else {
+      prim_rows_to_cols<LOG2N>(v[k], u, region, lane);
+#pragma unroll
+      for (int q = 0; q < P::RPL; ++q) dct_stage<P::M, true>(u + q * P::M, t + q * P::M);
+      prim_cols_to_rows<LOG2N>(t, u, region, lane);
+#pragma unroll
+      for (int q = 0; q < P::RPL; ++q) dct_stage<P::M, true>(u + q * P::M, v[k] + q * P::M);
+    }
+  }
+}
+
 // The tasks [t0, t1) of one warp.  `cache` holds the tables of sets
 // [set_lo, set_lo + cached count) when CACHED, else tables are read from
 // global memory.  `pbuf` is the warp's shared memory: G block regions of
 // perm_region_words(LOG2N) words (the permutation buffer), then for staged
 // kernels (STAGED: the input copied into shared memory one task ahead) the
 // stage and the block ids (batch_warp_bytes in all).
-template <int LOG2N, int KIND, bool CACHED, bool STAGED>
+template <int LOG2N, int KIND, bool CACHED, bool STAGED, bool PRIM = false, bool PF = false>
 __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, long long t1,
                                             const int* cache, int set_lo, int32_t* pbuf) {
   using M = BatchMath<LOG2N, KIND == 1>;
@@ -617,6 +704,21 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
       }
       cp_async_commit();
     } else {
+      if constexpr (PF) {
+        // pull the next task's blocks into L2 while this one computes: each
+        // lane asks for its own E values of each block
+        if (t + 1 < t1) {
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            const int nbk = __ldg(p.order + slot + G + k * GROUPS + grp);
+            if (nbk >= 0 && nbk < p.nblocks) {
+              const char* a = static_cast<const char*>(p.in) +
+                              ((long long)nbk * (1 << LOG2N) + lane * E) * (KIND == 0 ? 2 : 4);
+              asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a));
+            }
+          }
+        }
+      }
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         b[k] = __ldg(p.order + slot + k * GROUPS + grp);
@@ -628,6 +730,9 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
           for (int i = 0; i < E; ++i) v[k][i] = 0;
         }
       }
+    }
+    if constexpr (PRIM && !INV) {  // primary first (also for the skip bucket)
+      if (bucket != S + 1) batch_primary<LOG2N, KIND>(v, pbuf, grp, lane);
     }
     if (bucket < S) {
       const int* stab = CACHED ? cache + (size_t)(bucket - set_lo) * p.set_words
@@ -649,6 +754,9 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
         if (active[k] && lane == 0 && p.status) atomicCAS(p.status, 0, 4);
       }
     }
+    if constexpr (PRIM && INV) {  // inverse primary last
+      if (bucket != S + 1) batch_primary<LOG2N, KIND>(v, pbuf, grp, lane);
+    }
 #pragma unroll
     for (int k = 0; k < K; ++k)
       if (active[k]) batch_store<LOG2N, KIND>(p, b[k], lane, v[k]);
@@ -660,7 +768,8 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
 // range of warp tasks.  `smem` is the dynamic shared memory: the cached set
 // tables (max_cached_sets x set_words) followed by batch_warp_bytes per warp.
 // KIND 0: int16 -> int32 forward; KIND 1: int32 -> int16 inverse.
-template <int LOG2N, int KIND, bool STAGED = batch_staged(LOG2N, KIND)>
+template <int LOG2N, int KIND, bool STAGED = batch_staged(LOG2N, KIND), bool PRIM = false,
+          bool PF = false>
 __device__ __forceinline__ void batch_cta(const BatchParams& p, long long cta, long long ncta,
                                           int32_t* smem) {
   constexpr int GS = batch_group(LOG2N);                 // schedule group
@@ -705,9 +814,9 @@ __device__ __forceinline__ void batch_cta(const BatchParams& p, long long cta, l
 
   int32_t* wbuf = pbuf + (size_t)warp * (batch_warp_bytes<LOG2N, KIND, STAGED>() / 4);
   if (cached)
-    batch_tasks<LOG2N, KIND, true, STAGED>(p, t0, t1, cache, set_lo, wbuf);
+    batch_tasks<LOG2N, KIND, true, STAGED, PRIM, PF>(p, t0, t1, cache, set_lo, wbuf);
   else
-    batch_tasks<LOG2N, KIND, false, STAGED>(p, t0, t1, cache, set_lo, wbuf);
+    batch_tasks<LOG2N, KIND, false, STAGED, PRIM, PF>(p, t0, t1, cache, set_lo, wbuf);
 }
 
 // Dynamic shared memory of batch_cta for block size 2^LOG2N without the set
@@ -719,17 +828,17 @@ __host__ __device__ inline size_t batch_pbuf_bytes(int threads) {
 
 // The kernel may be launched with fewer threads than batch_threads (a
 // multiple of 32): the launch tuning picks the warps per CTA.
-template <int LOG2N, int KIND, bool STAGED>
+template <int LOG2N, int KIND, bool STAGED, bool PRIM = false, bool PF = false>
 __global__ void __launch_bounds__(batch_threads(LOG2N, KIND), 1) hygt_batch_kernel(BatchParams p) {
   extern __shared__ __align__(16) int32_t bsmem[];
-  batch_cta<LOG2N, KIND, STAGED>(p, blockIdx.x, gridDim.x, bsmem);
+  batch_cta<LOG2N, KIND, STAGED, PRIM, PF>(p, blockIdx.x, gridDim.x, bsmem);
 }
 
 // Launch tuning of the bucketed kernels (one per plan and direction): warps
 // per CTA (0: batch_threads / 32), CTAs per SM (0: as many as fit), and
-// whether the input is staged in shared memory one task ahead (-1: the
-// measured default batch_staged; 0 / 1: off / on; staging exists for
-// N = 32 and 64 only).
+// how the next task's input is fetched ahead (-1: the measured default
+// batch_staged; 0: not at all; 1: copied into shared memory one task ahead;
+// 2: prefetched into L2 one task ahead; 1 and 2 for N >= 16).
 struct BatchTune {
   int warps = 0;
   int ctas_per_sm = 0;
@@ -756,5 +865,13 @@ cudaError_t launch_batch_fwd(int log2n, const BatchParams& p, cudaStream_t strea
                              const BatchTune& tune = BatchTune());
 cudaError_t launch_batch_inv(int log2n, const BatchParams& p, cudaStream_t stream,
                              const BatchTune& tune = BatchTune());
+// The same kernels with the DCT-II primary of the secondary-transform
+// pipeline fused (log2n 4 or 6: 4x4 or 8x8 blocks).
+cudaError_t launch_batch_primary(int log2n, int inverse, const BatchParams& p,
+                                 cudaStream_t stream, const BatchTune& tune = BatchTune());
+cudaError_t launch_batch_primary_fwd(int log2n, const BatchParams& p, cudaStream_t stream,
+                                     const BatchTune& tune);
+cudaError_t launch_batch_primary_inv(int log2n, const BatchParams& p, cudaStream_t stream,
+                                     const BatchTune& tune);
 
 }  // namespace hygt

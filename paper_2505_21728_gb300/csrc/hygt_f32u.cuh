@@ -136,6 +136,16 @@ __global__ void __launch_bounds__(kF32uThreads, 1) hygt_f32u_kernel(F32uParams p
   const long long t1 = min(ntasks, t0 + chunk);
 
   for (long long t = t0; t < t1; ++t) {
+    if (lane32 == 0 && t + 1 < t1) {
+      // the next task's blocks are contiguous: pull them into L2 while this
+      // task computes (the size stays inside the buffer)
+      const long long nb = min((long long)G, p.nblocks - (t + 1) * G);
+      const uint32_t bytes = (uint32_t)(nb * N * 4);
+      if (nb > 0 && (bytes & 15u) == 0)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p.in + (t + 1) * G * N),
+                     "r"(bytes)
+                     : "memory");
+    }
     long long b[K];
     float v[K][E];
 #pragma unroll

@@ -19,9 +19,10 @@
 namespace hygt {
 
 constexpr int kMomentThreads = 256;
+constexpr int kMomentUnroll = 8;   // 16-byte loads in flight per thread
 
 // Per-CTA second moments: partials[cta][i] = sum of y_{b,i}^2 over the
-// float4s that CTA reads (FP32 within runs of 16 values, FP64 across them;
+// float4s that CTA reads (FP32 within runs of 8 values, FP64 across them;
 // fixed order).  n4 = B N / 4 float4s; N divides 4 * kMomentThreads.
 __global__ void hygt_moments_kernel(const float4* __restrict__ y, long long n4, int n,
                                     double* __restrict__ partials);

@@ -275,6 +275,21 @@ __global__ void __launch_bounds__(kGradThreads, 1) hygt_grad_kernel(GradParams p
   int bucket = 0, bucket_end = 0;
   for (long long t = t0; t < t1; ++t) {
     const long long slot = t * G;
+    if (!p.order && lane32 == 0 && t + 1 < t1) {
+      // blocks in order: the next task's rows are contiguous; pull them into
+      // L2 while this task computes (the sizes stay inside the buffers)
+      const long long nb = min((long long)G, p.nblocks - (t + 1) * G);
+      const uint32_t bytes = (uint32_t)(nb * N * 4);
+      if (nb > 0 && (bytes & 15u) == 0) {
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p.y + (t + 1) * G * N),
+                     "r"(bytes)
+                     : "memory");
+        if (p.gy)
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p.gy + (t + 1) * G * N),
+                       "r"(bytes)
+                       : "memory");
+      }
+    }
     if (p.order && slot >= bucket_end) {  // warp-uniform
       bucket = bucket_of_slot(p.starts, S, (int)slot);
       bucket_end = __ldg(p.starts + bucket + 1);

@@ -12,10 +12,11 @@
 //
 // Mapping.  A warp task is G = max(1, 256 / N) consecutive blocks: the warp
 // copies them (coalesced) into a shared-memory region per block of N + 1
-// words, and every pass spreads its G N/2 rotations over the 32 lanes (item
-// w: block w / (N/2), pair w mod (N/2)); each item reads its pair's packed
-// multipliers and indices (8 bytes, L1-cached), gathers the two values from
-// the block's region, rotates them and writes them back; __syncwarp()
+// words, and every pass spreads its G N/2 <= 128 rotations over the 32
+// lanes (item w: block w / (N/2), pair w mod (N/2); at most four per lane,
+// fixed for the task); each item reads its pair's packed indices and
+// multipliers (one 8-byte load, L1-cached), gathers the two values from the
+// block's region, rotates them and writes them back; __syncwarp()
 // separates the passes.  Integer rotations round half up,
 // floor((c a + s b + 2^(f-1)) / 2^f) (Sec. IV, Fig. 5 conversion), with
 // int32 intermediates; the inverse output saturates to int16.  Set index
@@ -37,9 +38,9 @@ struct hygt_pmpt_s {
   int angle_bits = 0, frac_bits = 0;
   int is_float = 0;
   int device = 0;
-  uint32_t* d_mn = nullptr;   // m | n << 16 per pair, [S][P][N/2]
-  uint32_t* d_cs = nullptr;   // int16 c | int16 s << 16 per pair (integer plans)
+  uint2* d_mncs = nullptr;    // (m | n << 16, int16 c | int16 s << 16) per pair, [S][P][N/2]
   float2* d_csf = nullptr;    // (cos, sin) per pair
+  uint32_t* d_mn = nullptr;   // m | n << 16 per pair (FP32 calls)
 };
 
 namespace hygt {
@@ -53,11 +54,16 @@ struct PmptParams {
   long long nblocks;
   int n, passes, num_sets, frac_bits;
   int group;  // blocks per warp task
+  const uint2* mncs;
   const uint32_t* mn;
-  const uint32_t* cs;
   const float2* csf;
   int* status;
 };
+
+// Items of a lane in a task: item it = lane + 32 u (u < kPmptItems) is
+// rotation j = it mod (N/2) of block it / (N/2); a task holds at most 128
+// rotations per pass (G N/2 <= 128), so 4 items per lane cover it.
+constexpr int kPmptItems = 4;
 
 // KIND: 0 integer forward, 1 integer inverse, 2 FP32 forward, 3 FP32 inverse.
 template <int KIND>
@@ -74,21 +80,29 @@ __global__ void __launch_bounds__(kPmptThreads) hygt_pmpt_kernel(PmptParams p) {
   const long long ntasks = (p.nblocks + G - 1) / G;
   const uint32_t rnd = 1u << (p.frac_bits - 1);
   const int f = p.frac_bits;
+  const size_t pass_stride = (size_t)half;
 
   for (long long t = (long long)blockIdx.x * wpc + warp; t < ntasks;
        t += (long long)gridDim.x * wpc) {
     const long long b0 = t * G;
     const int nb = (int)min((long long)G, p.nblocks - b0);
-    // blocks in (coalesced), set index per block
-    for (int e = lane; e < nb * N; e += 32) {
-      const int blk = e / N, i = e - blk * N;
-      const long long g = b0 * N + e;
-      if constexpr (F32)
-        regf[blk * RS + i] = __ldcs(static_cast<const float*>(p.in) + g);
-      else if constexpr (INV)
-        reg[blk * RS + i] = __ldcs(static_cast<const int32_t*>(p.in) + g);
-      else
-        reg[blk * RS + i] = __ldcs(static_cast<const int16_t*>(p.in) + g);
+    // blocks in (coalesced): element e = lane + 32 x of the task, block and
+    // index advanced without division
+    {
+      int blk = lane / N, i = lane - blk * N;
+      const int step_blk = 32 / N, step_i = 32 - step_blk * N;
+      for (int e = lane; e < nb * N; e += 32) {
+        const long long g = b0 * N + e;
+        if constexpr (F32)
+          regf[blk * RS + i] = __ldcs(static_cast<const float*>(p.in) + g);
+        else if constexpr (INV)
+          reg[blk * RS + i] = __ldcs(static_cast<const int32_t*>(p.in) + g);
+        else
+          reg[blk * RS + i] = __ldcs(static_cast<const int16_t*>(p.in) + g);
+        blk += step_blk;
+        i += step_i;
+        if (i >= N) { i -= N; ++blk; }
+      }
     }
     for (int k = lane; k < nb; k += 32) {  // a task may hold more than 32 blocks
       const int s = p.set ? (int)__ldg(p.set + b0 + k) : 0;
@@ -96,46 +110,76 @@ __global__ void __launch_bounds__(kPmptThreads) hygt_pmpt_kernel(PmptParams p) {
       if (s != 0xFFFF && s >= p.num_sets && p.status) atomicCAS(p.status, 0, HYGT_ERR_SET_INDEX);
     }
     __syncwarp();
+    // this lane's rotations: region offset and table offset of pass 0
+    int rbase[kPmptItems];
+    long long tbase[kPmptItems];
+#pragma unroll
+    for (int u = 0; u < kPmptItems; ++u) {
+      const int it = lane + 32 * u;
+      const int blk = it / half, j = it - blk * half;
+      rbase[u] = blk * RS;
+      tbase[u] = -1;
+      if (it < nb * half) {
+        const int s = bset[blk];
+        if (s < p.num_sets) tbase[u] = (long long)s * p.passes * half + j;
+      }
+    }
     for (int kk = 0; kk < p.passes; ++kk) {
       const int k = INV ? p.passes - 1 - kk : kk;
-      for (int w = lane; w < nb * half; w += 32) {
-        const int blk = w / half, j = w - blk * half;
-        const int s = bset[blk];
-        if (s >= p.num_sets) continue;  // skip sentinel or bad index
-        const size_t e = ((size_t)s * p.passes + k) * half + j;
-        const uint32_t mn = __ldg(p.mn + e);
-        const int m = (int)(mn & 0xFFFFu), q = (int)(mn >> 16);
+      uint2 ent[kPmptItems];
+      float2 entf[kPmptItems];
+      uint32_t mnf[kPmptItems];
+#pragma unroll
+      for (int u = 0; u < kPmptItems; ++u) {  // the loads first: independent
+        if (tbase[u] < 0) continue;
+        const size_t e = (size_t)tbase[u] + (size_t)k * pass_stride;
         if constexpr (F32) {
-          const float2 cs = __ldg(p.csf + e);
-          const float c = cs.x, sn = INV ? -cs.y : cs.y;
-          const float a = regf[blk * RS + m], bb = regf[blk * RS + q];
-          regf[blk * RS + m] = fmaf(c, a, sn * bb);
-          regf[blk * RS + q] = fmaf(c, bb, -sn * a);
+          entf[u] = __ldg(p.csf + e);
+          mnf[u] = __ldg(p.mn + e);
         } else {
-          const uint32_t cs = __ldg(p.cs + e);
-          const int32_t c = (int32_t)(int16_t)(cs & 0xFFFFu);
-          const int32_t s0 = (int32_t)cs >> 16;
+          ent[u] = __ldg(p.mncs + e);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kPmptItems; ++u) {
+        if (tbase[u] < 0) continue;
+        if constexpr (F32) {
+          const int m = (int)(mnf[u] & 0xFFFFu), q = (int)(mnf[u] >> 16);
+          const float c = entf[u].x, sn = INV ? -entf[u].y : entf[u].y;
+          const float a = regf[rbase[u] + m], bb = regf[rbase[u] + q];
+          regf[rbase[u] + m] = fmaf(c, a, sn * bb);
+          regf[rbase[u] + q] = fmaf(c, bb, -sn * a);
+        } else {
+          const int m = (int)(ent[u].x & 0xFFFFu), q = (int)(ent[u].x >> 16);
+          const int32_t c = (int32_t)(int16_t)(ent[u].y & 0xFFFFu);
+          const int32_t s0 = (int32_t)ent[u].y >> 16;
           const int32_t sn = INV ? -s0 : s0;
-          const uint32_t a = (uint32_t)reg[blk * RS + m], bb = (uint32_t)reg[blk * RS + q];
-          reg[blk * RS + m] = (int32_t)((uint32_t)c * a + (uint32_t)sn * bb + rnd) >> f;
-          reg[blk * RS + q] = (int32_t)((uint32_t)c * bb - (uint32_t)sn * a + rnd) >> f;
+          const uint32_t a = (uint32_t)reg[rbase[u] + m], bb = (uint32_t)reg[rbase[u] + q];
+          reg[rbase[u] + m] = (int32_t)((uint32_t)c * a + (uint32_t)sn * bb + rnd) >> f;
+          reg[rbase[u] + q] = (int32_t)((uint32_t)c * bb - (uint32_t)sn * a + rnd) >> f;
         }
       }
       __syncwarp();
     }
     // blocks out (coalesced); bad set index: zeros
-    for (int e = lane; e < nb * N; e += 32) {
-      const int blk = e / N, i = e - blk * N;
-      const long long g = b0 * N + e;
-      const int s = bset[blk];
-      const bool bad = s != 0xFFFF && s >= p.num_sets;
-      if constexpr (F32) {
-        __stcs(static_cast<float*>(p.out) + g, bad ? 0.f : regf[blk * RS + i]);
-      } else if constexpr (INV) {
-        const int32_t v = bad ? 0 : reg[blk * RS + i];
-        __stcs(static_cast<int16_t*>(p.out) + g, (int16_t)max(-32768, min(32767, v)));
-      } else {
-        __stcs(static_cast<int32_t*>(p.out) + g, bad ? 0 : reg[blk * RS + i]);
+    {
+      int blk = lane / N, i = lane - blk * N;
+      const int step_blk = 32 / N, step_i = 32 - step_blk * N;
+      for (int e = lane; e < nb * N; e += 32) {
+        const long long g = b0 * N + e;
+        const int s = bset[blk];
+        const bool bad = s != 0xFFFF && s >= p.num_sets;
+        if constexpr (F32) {
+          __stcs(static_cast<float*>(p.out) + g, bad ? 0.f : regf[blk * RS + i]);
+        } else if constexpr (INV) {
+          const int32_t v = bad ? 0 : reg[blk * RS + i];
+          __stcs(static_cast<int16_t*>(p.out) + g, (int16_t)max(-32768, min(32767, v)));
+        } else {
+          __stcs(static_cast<int32_t*>(p.out) + g, bad ? 0 : reg[blk * RS + i]);
+        }
+        blk += step_blk;
+        i += step_i;
+        if (i >= N) { i -= N; ++blk; }
       }
     }
     __syncwarp();
@@ -168,7 +212,7 @@ namespace {
 void free_pmpt(hygt_pmpt p) {
   if (!p) return;
   if (p->d_mn) cudaFree(p->d_mn);
-  if (p->d_cs) cudaFree(p->d_cs);
+  if (p->d_mncs) cudaFree(p->d_mncs);
   if (p->d_csf) cudaFree(p->d_csf);
   delete p;
 }
@@ -212,8 +256,8 @@ hygt_status pmpt_run(int kind, hygt_pmpt pm, const void* in, void* out, const ui
   p.num_sets = pm->num_sets;
   p.frac_bits = pm->frac_bits > 0 ? pm->frac_bits : 8;
   p.group = pm->n >= 256 ? 1 : 256 / pm->n;
+  p.mncs = pm->d_mncs;
   p.mn = pm->d_mn;
-  p.cs = pm->d_cs;
   p.csf = pm->d_csf;
   p.status = d_status;
   return pmpt_status(hygt::launch_pmpt(kind, p, (cudaStream_t)stream));
@@ -280,7 +324,11 @@ hygt_status hygt_pmpt_create(hygt_pmpt* out, int n, int passes, int num_sets,
   }
   hygt_status s = upload_vec(&p->d_mn, mn);
   if (s == HYGT_OK) s = upload_vec(&p->d_csf, csf);
-  if (s == HYGT_OK && !cs.empty()) s = upload_vec(&p->d_cs, cs);
+  if (s == HYGT_OK && !cs.empty()) {
+    std::vector<uint2> mncs(pairs);
+    for (size_t e = 0; e < pairs; ++e) mncs[e] = make_uint2(mn[e], cs[e]);
+    s = upload_vec(&p->d_mncs, mncs);
+  }
   if (s != HYGT_OK) {
     free_pmpt(p);
     return s;

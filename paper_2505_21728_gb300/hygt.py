@@ -92,6 +92,10 @@ def _load() -> ctypes.CDLL:
     f32 = ctypes.c_float
     L.hygt_adam_step.argtypes = [P, P, P, P, i64, f32, f32, f32, f32, i32, P]
     L.hygt_adam_step.restype = i32
+    for name in ("hygt_secondary_forward_batch", "hygt_secondary_inverse_batch"):
+        f = getattr(L, name)
+        f.argtypes = [P, P, i32, P, P, i64, P, P]
+        f.restype = i32
     for name in ("hygt_secondary_forward", "hygt_secondary_inverse"):
         f = getattr(L, name)
         f.argtypes = [P, i32, P, P, P, i64, P, P]
@@ -287,6 +291,16 @@ def hygt_secondary_forward(plan, log2m, d_x, d_y, d_set, nblocks, stream, d_stat
 def hygt_secondary_inverse(plan, log2m, d_y, d_x, d_set, nblocks, stream, d_status):
     return int(_lib.hygt_secondary_inverse(plan, log2m, d_y, d_x, d_set, nblocks, stream,
                                            d_status))
+
+
+def hygt_secondary_forward_batch(plan, d_work, log2m, d_x, d_y, nblocks, stream, d_status):
+    return int(_lib.hygt_secondary_forward_batch(plan, d_work, log2m, d_x, d_y, nblocks, stream,
+                                                 d_status))
+
+
+def hygt_secondary_inverse_batch(plan, d_work, log2m, d_y, d_x, nblocks, stream, d_status):
+    return int(_lib.hygt_secondary_inverse_batch(plan, d_work, log2m, d_y, d_x, nblocks, stream,
+                                                 d_status))
 
 
 def hygt_pmpt_create(n, passes, num_sets, angle_idx, theta, m_idx, n_idx, angle_bits=8,
@@ -774,6 +788,26 @@ class Batch:
             out = torch.empty(y.shape, dtype=torch.int16, device=y.device)
         return self._run(hygt_inverse_batch, "hygt_inverse_batch", y, out, torch.int32,
                          torch.int16, status, stream)
+
+    def secondary_forward(self, x, log2m, out=None, status=None, stream=None):
+        """The secondary pipeline (DCT-II primary fused, 4x4 / 8x8 blocks)
+        through this schedule: int16 [B, N] -> int32 [B, N]."""
+        import torch
+        if out is None:
+            out = torch.empty(x.shape, dtype=torch.int32, device=x.device)
+        fn = lambda h, w, px, po, nb, st, ps: hygt_secondary_forward_batch(  # noqa: E731
+            h, w, int(log2m), px, po, nb, st, ps)
+        return self._run(fn, "hygt_secondary_forward_batch", x, out, torch.int16, torch.int32,
+                         status, stream)
+
+    def secondary_inverse(self, y, log2m, out=None, status=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(y.shape, dtype=torch.int16, device=y.device)
+        fn = lambda h, w, py, po, nb, st, ps: hygt_secondary_inverse_batch(  # noqa: E731
+            h, w, int(log2m), py, po, nb, st, ps)
+        return self._run(fn, "hygt_secondary_inverse_batch", y, out, torch.int32, torch.int16,
+                         status, stream)
 
     def forward_f32(self, x, out=None, status=None, stream=None):
         """FP32 forward through the bucketed schedule (N >= 16)."""

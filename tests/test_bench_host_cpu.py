@@ -64,10 +64,13 @@ def test_measured_peak_and_fallback(tmp_path, monkeypatch):
     assert bench.measured_peaks() == (6800.0, "fallback")
 
 
-def _tree(tmp_path, kernel_text):
+def _tree(tmp_path, kernel_text, name="batch_fwd.cu"):
     csrc = tmp_path / "paper_2505_21728_gb300" / "csrc"
     csrc.mkdir(parents=True, exist_ok=True)
-    (csrc / "k.cu").write_text(kernel_text)
+    for f in bench.BATCH_SOURCES:
+        if not (csrc / f).exists():
+            (csrc / f).write_text("// " + f)
+    (csrc / name).write_text(kernel_text)
     (tmp_path / "profiles").mkdir(exist_ok=True)
 
 
@@ -77,11 +80,16 @@ def test_traffic_only_for_the_current_kernel_sources(tmp_path, monkeypatch):
     sha1 = bench.kernel_source_sha()
     (tmp_path / "profiles" / "k.md").write_text(
         "# summary\n"
-        "bench-traffic: kernel=fwd workload=w8 sha=%s bytes_per_launch=1392074752\n"
-        "bench-traffic: kernel=inv workload=w8 sha=%s bytes_per_launch=1.5e9\n" % (sha1, sha1))
-    assert bench.ncu_traffic("fwd", "w8") == 1392074752
-    assert bench.ncu_traffic("inv", "w8") == 1500000000
+        "bench-traffic: kernel=fwd workload=w8 sha=%s tuning=12,0,0 bytes_per_launch=1572022272\n"
+        "bench-traffic: kernel=inv workload=w8 sha=%s tuning=4,0,2 bytes_per_launch=1.6e9\n"
+        % (sha1, sha1))
+    assert bench.ncu_traffic("fwd", "w8") == 1572022272
+    assert bench.ncu_traffic("fwd", "w8", (12, 0, 0, 0.5)) == 1572022272
+    assert bench.ncu_traffic("fwd", "w8", (12, 0, 2, 0.5)) is None   # another launch variant
+    assert bench.ncu_traffic("inv", "w8", (4, 0, 2)) == 1600000000
     assert bench.ncu_traffic("fwd", "other") is None
-    _tree(tmp_path, "kernel v2")      # the kernels changed since the capture
+    _tree(tmp_path, "kernel v1", name="secondary.cu")  # another kernel's source: no effect
+    assert bench.kernel_source_sha() == sha1
+    _tree(tmp_path, "kernel v2")      # the batch kernels changed since the capture
     assert bench.kernel_source_sha() != sha1
     assert bench.ncu_traffic("fwd", "w8") is None

@@ -87,3 +87,36 @@ def test_secondary_bad_sets_and_arguments(gpu, orc):
     assert e.shape == (0, 64)
     fp.close()
     plan.close()
+
+
+@pytest.mark.parametrize("log2m,B", [(2, 30011), (3, 12007)])
+@pytest.mark.parametrize("rounds,perm_kind", [(2, "between"), (3, "all")])
+def test_secondary_fused_bucketed_bit_exact(gpu, orc, log2m, B, rounds, perm_kind):
+    """4x4 and 8x8 blocks through the bucketed kernels with the primary
+    fused: bit for bit the oracle (skip and bad set indices included), for
+    the default launch and both staging choices."""
+    import torch
+    log2n = 2 * log2m
+    N, S, M = 1 << log2n, 105, 1 << log2m
+    q = inputs.angle_indices(S, rounds, log2n, seed=log2m + 9 * rounds)
+    perms = inputs.permutations(S, rounds, N, seed=log2m + 1,
+                                between_rounds_only=(perm_kind == "between"))
+    x = inputs.laplacian_blocks(B, M * M, 30.0, -32768, 32767, seed=log2m + 5)
+    sets = inputs.set_indices(B, S, seed=log2m + 6, skip_frac=0.1)
+    sets[11] = 999
+    ye, s1 = orc.secondary_fwd(x, log2m, q, log2n, rounds, perms, sets)
+    xe, s2 = orc.secondary_inv(ye, log2m, q, log2n, rounds, perms, sets)
+    assert s1 == s2 == orc.ERR_SET
+    plan = gpu.Plan(log2n, rounds, q, perms)
+    b = gpu.Batch(plan, B).build(_t(sets))
+    for stage in (-1, 0, 1):
+        for inv in (0, 1):
+            assert gpu.hygt_batch_set_tuning(plan.handle, inv, 0, 0, stage) == gpu.HYGT_OK
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        y = b.secondary_forward(_t(x), log2m, status=st)
+        xr = b.secondary_inverse(_t(ye), log2m, status=st)
+        torch.cuda.synchronize()
+        assert int(st.item()) == gpu.HYGT_ERR_SET_INDEX
+        assert np.array_equal(y.cpu().numpy(), ye), stage
+        assert np.array_equal(xr.cpu().numpy(), xe), stage
+    plan.close()
