@@ -179,8 +179,12 @@ hygt_status hygt_inverse_batch(hygt_plan plan, const void *d_work, const int32_t
  *   stage          -1: the default; 0: blocks read straight from global
  *        memory; 1: each warp copies its next task's blocks into shared
  *        memory (cp.async) while it transforms the current one; 2: each
- *        warp prefetches its next task's blocks into L2 (N >= 16 for 1 and
- *        2; smaller blocks return HYGT_ERR_UNSUPPORTED).
+ *        warp prefetches its next task's blocks into L2; 3: as 1, by one
+ *        bulk copy (cp.async.bulk, completing on a per-warp mbarrier) per
+ *        block; an input that is not 16-byte aligned falls back to 0 (N >= 16
+ *        for 1, 2 and 3; smaller blocks return HYGT_ERR_UNSUPPORTED).  A bulk
+ *        copy that has not landed within about a second makes the warp stop
+ *        and write HYGT_ERR_CUDA to d_status.
  * Results do not depend on the tuning.  A choice whose shared memory does
  * not fit makes the next bucketed call return HYGT_ERR_UNSUPPORTED.  Not
  * thread-safe with concurrent calls on the same plan.

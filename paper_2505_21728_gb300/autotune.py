@@ -164,10 +164,11 @@ def batch_candidates(max_warps, log2n):
     """(warps_per_cta, ctas_per_sm, stage) points the batch tuner times:
     blocks per CTA through the warps of a CTA, CTAs per SM, and the staging
     depth (0: none, 1: the next task's blocks copied into shared memory
-    ahead, 2: prefetched into L2 ahead; N >= 16 only)."""
+    ahead, 2: prefetched into L2 ahead, 3: as 1 by one bulk copy per block;
+    N >= 16 only)."""
     warps = sorted({w for w in (max_warps, (3 * max_warps) // 4, max_warps // 2,
                                 max_warps // 3, 4) if w >= 2})
-    stages = (0, 1, 2) if log2n >= 4 else (-1,)
+    stages = (0, 1, 2, 3) if log2n >= 4 else (-1,)
     out = []
     for w in warps:
         for c in (0, 1, 2):

@@ -547,7 +547,7 @@ hygt_status hygt_inverse_batch_f32(hygt_plan plan, const void* d_work, const flo
 hygt_status hygt_batch_set_tuning(hygt_plan plan, int inverse, int warps_per_cta,
                                   int ctas_per_sm, int stage) {
   if (!plan || (inverse != 0 && inverse != 1) || warps_per_cta < 0 || ctas_per_sm < 0 ||
-      ctas_per_sm > 8 || stage < -1 || stage > 2)
+      ctas_per_sm > 8 || stage < -1 || stage > 3)
     return HYGT_ERR_ARG;
   const int max_warps = hygt::batch_threads(plan->log2n, inverse) / 32;
   if (warps_per_cta > max_warps) return HYGT_ERR_ARG;

@@ -463,15 +463,101 @@ struct BatchStage {
 };
 
 // Shared memory of one warp: permutation buffer, then (staged kernels) the
-// stage and the block ids.
-template <int LOG2N, int KIND, bool STAGED = batch_staged(LOG2N, KIND)>
+// stage and the block ids, or (bulk-staged kernels) the stage and the
+// warp's mbarrier.
+template <int LOG2N, int KIND, bool STAGED = batch_staged(LOG2N, KIND), bool BULK = false>
 __host__ __device__ constexpr int batch_warp_bytes() {
   return perm_buf_words(LOG2N, KIND) * 4 +
-         (STAGED ? BatchStage<LOG2N, KIND>::BYTES + BatchStage<LOG2N, KIND>::IDS_BYTES : 0);
+         (STAGED ? BatchStage<LOG2N, KIND>::BYTES + BatchStage<LOG2N, KIND>::IDS_BYTES : 0) +
+         (BULK ? BatchStage<LOG2N, KIND>::BYTES + 16 : 0);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// ---------------------------------------------------------------- bulk stage
+// Bulk-staged kernels: each warp task's blocks are copied into the warp's
+// stage with one cp.async.bulk per block (issued by the lane that owns the
+// slot; the copy engine moves the bytes), completing on the warp's
+// mbarrier; a task is copied while the previous one computes.  Stage layout:
+// slot s of the task at s * N * IB bytes.
+__device__ __forceinline__ uint64_t batch_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for phase `parity` of the mbarrier at shared address `bar`, at most
+// about one second; false on timeout.
+__device__ __forceinline__ bool batch_mbar_wait(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = batch_ns();
+  for (uint32_t it = 0;; ++it) {
+    uint32_t done = 0;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 63) == 63 && batch_ns() - t0 > 1000000000ull) return false;
+  }
+}
+
+// Issue the copies of one task: slots l + 32 j of the task (j < GJ) with
+// block ids ids[j] (-1: none).  Lane 0 announces the task's bytes on the
+// barrier first.
+template <int LOG2N, int KIND, int GJ>
+__device__ __forceinline__ void bulk_issue(const BatchParams& p, const int (&ids)[GJ],
+                                           char* stage, uint32_t bar, int lane32) {
+  using St = BatchStage<LOG2N, KIND>;
+  constexpr uint32_t BB = St::N * St::IB;
+  int cnt = 0;
+#pragma unroll
+  for (int j = 0; j < GJ; ++j)
+    cnt += __popc(__ballot_sync(kFullMask, ids[j] >= 0 && (long long)ids[j] < p.nblocks));
+  if (lane32 == 0)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"((uint32_t)cnt * BB)
+                 : "memory");
+  // the stage was last read by this warp's generic loads (ordered by the
+  // caller's __syncwarp); order them before the copy engine's writes
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < GJ; ++j) {
+    const int slot = lane32 + 32 * j;
+    if (slot < St::G && ids[j] >= 0 && (long long)ids[j] < p.nblocks) {
+      const char* src = static_cast<const char*>(p.in) + (long long)ids[j] * BB;
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+          "[%3];" ::"r"(smem_u32(stage + slot * BB)),
+          "l"(src), "r"(BB), "r"(bar)
+          : "memory");
+    }
+  }
+}
+
+// This lane's E values of the block in stage slot `slot`.
+template <int LOG2N, int KIND>
+__device__ __forceinline__ void bulk_read(const char* stage, int slot, int lane,
+                                          int32_t (&v)[BatchStage<LOG2N, KIND>::E]) {
+  using St = BatchStage<LOG2N, KIND>;
+  constexpr int LB = St::E * St::IB;  // bytes of one lane
+  const char* src = stage + slot * (St::N * St::IB) + lane * LB;
+#pragma unroll
+  for (int q = 0; q < LB / 16; ++q) {
+    const uint4 t = *reinterpret_cast<const uint4*>(src + 16 * q);
+    const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      if constexpr (St::IB == 2) {
+        v[q * 8 + 2 * x] = (int32_t)(int16_t)(w[x] & 0xffffu);
+        v[q * 8 + 2 * x + 1] = (int32_t)w[x] >> 16;
+      } else {
+        v[q * 4 + x] = (int32_t)w[x];
+      }
+    }
+  }
 }
 
 // Asynchronous global -> shared copy of BYTES (4, 8 or 16); zero-filled
@@ -644,7 +730,8 @@ __device__ __forceinline__ void batch_primary(
 // perm_region_words(LOG2N) words (the permutation buffer), then for staged
 // kernels (STAGED: the input copied into shared memory one task ahead) the
 // stage and the block ids (batch_warp_bytes in all).
-template <int LOG2N, int KIND, bool CACHED, bool STAGED, bool PRIM = false, bool PF = false>
+template <int LOG2N, int KIND, bool CACHED, bool STAGED, bool PRIM = false, bool PF = false,
+          bool BULK = false>
 __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, long long t1,
                                             const int* cache, int set_lo, int32_t* pbuf) {
   using M = BatchMath<LOG2N, KIND == 1>;
@@ -655,6 +742,9 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
   constexpr int G = GROUPS * K;
   constexpr int RW = perm_region_words(LOG2N);
   constexpr bool INV = (KIND == 1);
+  static_assert(!(STAGED && BULK), "one staging scheme at a time");
+  static_assert(!BULK || (LOG2N >= 4 && G == BatchStage<LOG2N, KIND>::G),
+                "bulk copies of whole blocks need N * input bytes >= 16");
   const int lane32 = threadIdx.x & 31;
   const int lane = lane32 % L;
   const int grp = lane32 / L;
@@ -678,6 +768,29 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
     cp_async_commit();
   }
 
+  // bulk stage: the task's block ids in registers (slot l + 32 j in lane l),
+  // this task's and the next one's
+  constexpr int GJ = (G + 31) / 32;
+  char* bstage = reinterpret_cast<char*>(pbuf + perm_buf_words(LOG2N, KIND));
+  const uint32_t bbar = smem_u32(bstage + BatchStage<LOG2N, KIND>::BYTES);
+  uint32_t bphase = 0;
+  int ids_cur[GJ], ids_next[GJ];
+  if constexpr (BULK) {
+    if (t0 >= t1) return;
+    if (lane32 == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bbar) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < GJ; ++j) {
+      const int sl = lane32 + 32 * j;
+      ids_cur[j] = sl < G ? __ldg(p.order + t0 * G + sl) : -1;
+      ids_next[j] = (sl < G && t0 + 1 < t1) ? __ldg(p.order + (t0 + 1) * G + sl) : -1;
+    }
+    bulk_issue<LOG2N, KIND, GJ>(p, ids_cur, bstage, bbar, lane32);
+  }
+
   int bucket = 0, bucket_end = 0;
   for (long long t = t0; t < t1; ++t) {
     const int slot = (int)(t * G);
@@ -688,7 +801,33 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
     int b[K];
     bool active[K];
     int32_t v[K][E];
-    if constexpr (STAGED) {
+    if constexpr (BULK) {
+      // every lane observes the phase (visibility of the copied bytes); the
+      // decision to give up is warp-uniform
+      if (!__all_sync(kFullMask, batch_mbar_wait(bbar, bphase))) {
+        if (lane32 == 0 && p.status) atomicCAS(p.status, 0, 2);
+        batch_mbar_wait(bbar, bphase);  // bounded wait for the copies in flight
+        return;
+      }
+      bphase ^= 1u;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int sl = k * GROUPS + grp;  // sl / 32 == (k * GROUPS) / 32: GROUPS divides 32
+        b[k] = __shfl_sync(kFullMask, ids_cur[(k * GROUPS) >> 5], sl & 31);
+        active[k] = b[k] >= 0 && b[k] < p.nblocks;
+        bulk_read<LOG2N, KIND>(bstage, sl, lane, v[k]);
+      }
+      __syncwarp();
+      if (t + 1 < t1) {
+#pragma unroll
+        for (int j = 0; j < GJ; ++j) {
+          ids_cur[j] = ids_next[j];
+          const int sl = lane32 + 32 * j;
+          ids_next[j] = (sl < G && t + 2 < t1) ? __ldg(p.order + (t + 2) * G + sl) : -1;
+        }
+        bulk_issue<LOG2N, KIND, GJ>(p, ids_cur, bstage, bbar, lane32);
+      }
+    } else if constexpr (STAGED) {
       cp_async_wait_all();
       __syncwarp();
 #pragma unroll
@@ -769,7 +908,7 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
 // tables (max_cached_sets x set_words) followed by batch_warp_bytes per warp.
 // KIND 0: int16 -> int32 forward; KIND 1: int32 -> int16 inverse.
 template <int LOG2N, int KIND, bool STAGED = batch_staged(LOG2N, KIND), bool PRIM = false,
-          bool PF = false>
+          bool PF = false, bool BULK = false>
 __device__ __forceinline__ void batch_cta(const BatchParams& p, long long cta, long long ncta,
                                           int32_t* smem) {
   constexpr int GS = batch_group(LOG2N);                 // schedule group
@@ -812,33 +951,35 @@ __device__ __forceinline__ void batch_cta(const BatchParams& p, long long cta, l
   }
   __syncthreads();
 
-  int32_t* wbuf = pbuf + (size_t)warp * (batch_warp_bytes<LOG2N, KIND, STAGED>() / 4);
+  int32_t* wbuf = pbuf + (size_t)warp * (batch_warp_bytes<LOG2N, KIND, STAGED, BULK>() / 4);
   if (cached)
-    batch_tasks<LOG2N, KIND, true, STAGED, PRIM, PF>(p, t0, t1, cache, set_lo, wbuf);
+    batch_tasks<LOG2N, KIND, true, STAGED, PRIM, PF, BULK>(p, t0, t1, cache, set_lo, wbuf);
   else
-    batch_tasks<LOG2N, KIND, false, STAGED, PRIM, PF>(p, t0, t1, cache, set_lo, wbuf);
+    batch_tasks<LOG2N, KIND, false, STAGED, PRIM, PF, BULK>(p, t0, t1, cache, set_lo, wbuf);
 }
 
 // Dynamic shared memory of batch_cta for block size 2^LOG2N without the set
 // tables: batch_warp_bytes per warp.
-template <int LOG2N, int KIND, bool STAGED = batch_staged(LOG2N, KIND)>
+template <int LOG2N, int KIND, bool STAGED = batch_staged(LOG2N, KIND), bool BULK = false>
 __host__ __device__ inline size_t batch_pbuf_bytes(int threads) {
-  return (size_t)(threads / 32) * batch_warp_bytes<LOG2N, KIND, STAGED>();
+  return (size_t)(threads / 32) * batch_warp_bytes<LOG2N, KIND, STAGED, BULK>();
 }
 
 // The kernel may be launched with fewer threads than batch_threads (a
 // multiple of 32): the launch tuning picks the warps per CTA.
-template <int LOG2N, int KIND, bool STAGED, bool PRIM = false, bool PF = false>
+template <int LOG2N, int KIND, bool STAGED, bool PRIM = false, bool PF = false,
+          bool BULK = false>
 __global__ void __launch_bounds__(batch_threads(LOG2N, KIND), 1) hygt_batch_kernel(BatchParams p) {
   extern __shared__ __align__(16) int32_t bsmem[];
-  batch_cta<LOG2N, KIND, STAGED, PRIM, PF>(p, blockIdx.x, gridDim.x, bsmem);
+  batch_cta<LOG2N, KIND, STAGED, PRIM, PF, BULK>(p, blockIdx.x, gridDim.x, bsmem);
 }
 
 // Launch tuning of the bucketed kernels (one per plan and direction): warps
 // per CTA (0: batch_threads / 32), CTAs per SM (0: as many as fit), and
 // how the next task's input is fetched ahead (-1: the measured default
 // batch_staged; 0: not at all; 1: copied into shared memory one task ahead;
-// 2: prefetched into L2 one task ahead; 1 and 2 for N >= 16).
+// 2: prefetched into L2 one task ahead; 3: copied into shared memory one
+// task ahead by one bulk copy per block; 1, 2 and 3 for N >= 16).
 struct BatchTune {
   int warps = 0;
   int ctas_per_sm = 0;

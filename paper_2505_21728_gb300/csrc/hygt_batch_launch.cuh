@@ -10,9 +10,10 @@
 
 namespace hygt {
 
-template <int LOG2N, int KIND, bool STAGED, bool PRIM = false, bool PF = false>
+template <int LOG2N, int KIND, bool STAGED, bool PRIM = false, bool PF = false,
+          bool BULK = false>
 inline cudaError_t launch_variant(BatchParams p, cudaStream_t stream, const BatchTune& tune) {
-  auto kern = hygt_batch_kernel<LOG2N, KIND, STAGED, PRIM, PF>;
+  auto kern = hygt_batch_kernel<LOG2N, KIND, STAGED, PRIM, PF, BULK>;
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
@@ -21,7 +22,7 @@ inline cudaError_t launch_variant(BatchParams p, cudaStream_t stream, const Batc
   constexpr int kMaxWarps = batch_threads(LOG2N, KIND) / 32;
   const int warps = tune.warps > 0 && tune.warps < kMaxWarps ? tune.warps : kMaxWarps;
   const int threads = warps * 32;
-  const size_t pbuf = batch_pbuf_bytes<LOG2N, KIND, STAGED>(threads);
+  const size_t pbuf = batch_pbuf_bytes<LOG2N, KIND, STAGED, BULK>(threads);
   const size_t set_bytes = (size_t)p.set_words * 4;
   // with several CTAs per SM each gets its share of the shared memory
   const int want = tune.ctas_per_sm > 0 ? tune.ctas_per_sm : 1;
@@ -49,6 +50,16 @@ inline cudaError_t launch_variant(BatchParams p, cudaStream_t stream, const Batc
   return cudaGetLastError();
 }
 
+// The staging choice of a launch: the tuned one, else the measured default;
+// bulk copies need a 16-byte aligned input (whole blocks are copied), else
+// no stage.
+template <int LOG2N, int KIND>
+inline int batch_stage_of(const BatchParams& p, const BatchTune& tune) {
+  const int stage = tune.stage < 0 ? (batch_staged(LOG2N, KIND) ? 1 : 0) : tune.stage;
+  if (stage == 3 && (reinterpret_cast<uintptr_t>(p.in) & 15) != 0) return 0;
+  return stage;
+}
+
 // Staging exists as a tuning choice for N >= 16; smaller blocks keep the
 // measured default (no stage).
 template <int LOG2N, int KIND>
@@ -56,7 +67,9 @@ inline cudaError_t launch_batch_sized(const BatchParams& p, cudaStream_t stream,
                                       const BatchTune& tune) {
   constexpr bool kDefault = batch_staged(LOG2N, KIND);
   if constexpr (LOG2N >= 4) {
-    const int stage = tune.stage < 0 ? (kDefault ? 1 : 0) : tune.stage;
+    const int stage = batch_stage_of<LOG2N, KIND>(p, tune);
+    if (stage == 3)
+      return launch_variant<LOG2N, KIND, false, false, false, true>(p, stream, tune);
     if (stage == 2) return launch_variant<LOG2N, KIND, false, false, true>(p, stream, tune);
     return stage == 1 ? launch_variant<LOG2N, KIND, true>(p, stream, tune)
                       : launch_variant<LOG2N, KIND, false>(p, stream, tune);
@@ -84,7 +97,8 @@ inline cudaError_t launch_batch(int log2n, const BatchParams& p, cudaStream_t st
 template <int LOG2N, int KIND>
 inline cudaError_t launch_primary_sized(const BatchParams& p, cudaStream_t stream,
                                         const BatchTune& tune) {
-  const int stage = tune.stage < 0 ? (batch_staged(LOG2N, KIND) ? 1 : 0) : tune.stage;
+  const int stage = batch_stage_of<LOG2N, KIND>(p, tune);
+  if (stage == 3) return launch_variant<LOG2N, KIND, false, true, false, true>(p, stream, tune);
   if (stage == 2) return launch_variant<LOG2N, KIND, false, true, true>(p, stream, tune);
   return stage == 1 ? launch_variant<LOG2N, KIND, true, true>(p, stream, tune)
                     : launch_variant<LOG2N, KIND, false, true>(p, stream, tune);

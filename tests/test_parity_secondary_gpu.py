@@ -94,7 +94,7 @@ def test_secondary_bad_sets_and_arguments(gpu, orc):
 def test_secondary_fused_bucketed_bit_exact(gpu, orc, log2m, B, rounds, perm_kind):
     """4x4 and 8x8 blocks through the bucketed kernels with the primary
     fused: bit for bit the oracle (skip and bad set indices included), for
-    the default launch and both staging choices."""
+    the default launch and every staging choice."""
     import torch
     log2n = 2 * log2m
     N, S, M = 1 << log2n, 105, 1 << log2m
@@ -109,7 +109,7 @@ def test_secondary_fused_bucketed_bit_exact(gpu, orc, log2m, B, rounds, perm_kin
     assert s1 == s2 == orc.ERR_SET
     plan = gpu.Plan(log2n, rounds, q, perms)
     b = gpu.Batch(plan, B).build(_t(sets))
-    for stage in (-1, 0, 1):
+    for stage in (-1, 0, 1, 2, 3):
         for inv in (0, 1):
             assert gpu.hygt_batch_set_tuning(plan.handle, inv, 0, 0, stage) == gpu.HYGT_OK
         st = torch.zeros(1, dtype=torch.int32, device="cuda")
