@@ -63,7 +63,7 @@ def parse_args():
                          "then launch no tuning kernels)")
     ap.add_argument("--fwd-tuning", default=None,
                     help="--case batch/stress: launch tuning of the forward, "
-                         "'warps,ctas_per_sm,stage' (hygt_batch_set_tuning)")
+                         "'warps,ctas_per_sm,stage[,layout]' (hygt_batch_set_tuning)")
     ap.add_argument("--inv-tuning", default=None, help="the same for the inverse")
     return ap.parse_args()
 
@@ -208,10 +208,16 @@ def kernel_source_sha(files=BATCH_SOURCES) -> str:
 def ncu_traffic(kernel: str, workload: str, tuning=None):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
     the current kernel sources and (when given) the same launch tuning (a line
-    'bench-traffic: kernel=... workload=... sha=... tuning=w,c,s
-    bytes_per_launch=...' in profiles/*.md); else None."""
+    'bench-traffic: kernel=... workload=... sha=... tuning=w,c,s[,layout]
+    bytes_per_launch=...' in profiles/*.md; the layout is written when it is
+    not 0); else None.  ``tuning``: (warps, ctas_per_sm, stage[, layout, ...])."""
     sha = kernel_source_sha()
-    want = None if tuning is None else ",".join(str(int(v)) for v in tuning[:3])
+    want = None
+    if tuning is not None:
+        vals = [int(v) for v in tuning[:3]]
+        if len(tuning) > 4 and int(tuning[3]) != 0:
+            vals.append(int(tuning[3]))
+        want = ",".join(str(v) for v in vals)
     for p in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
         with open(p) as f:
             for line in f:
@@ -398,7 +404,7 @@ def run_ours(args, rank, world, local):
                    "sets": w.num_sets, "parallelism": "dp%d" % world,
                    "step": "bucket blocks by set, integer forward, integer inverse",
                    "launch_tuning": {d: {"warps_per_cta": v[0], "ctas_per_sm": v[1],
-                                         "stage": v[2], "tuner_ms": v[3]}
+                                         "stage": v[2], "layout": v[3], "tuner_ms": v[4]}
                                      for d, v in tuning.items()},
                    "l2": "inputs larger than L2 (%.0f MB read + %.0f MB written per step "
                          "vs %d MB L2), no flush" % (count * 6 * N / 1e6, count * 6 * N / 1e6,
@@ -792,7 +798,8 @@ def mixed_leg(dev, stream, steps=20, name="mixed_frame_2160p16"):
                      "concurrent" if all(c > 0 for c in split) else "sequential"),
             "cta_split": split,
             "class_launch_tuning": {str(n): {d: {"warps_per_cta": v[0], "ctas_per_sm": v[1],
-                                                 "stage": v[2], "tuner_ms": v[3]}
+                                                 "stage": v[2], "layout": v[3],
+                                                 "tuner_ms": v[4]}
                                              for d, v in t.items()}
                                     for n, t in tunings.items()},
             "gpu_launches_per_step": 3 * 3 + (6 if all(c == -1 for c in split) else 2),

@@ -184,15 +184,22 @@ hygt_status hygt_inverse_batch(hygt_plan plan, const void *d_work, const int32_t
  *        block; an input that is not 16-byte aligned falls back to 0 (N >= 16
  *        for 1, 2 and 3; smaller blocks return HYGT_ERR_UNSUPPORTED).  A bulk
  *        copy that has not landed within about a second makes the warp stop
- *        and write HYGT_ERR_CUDA to d_status.
+ *        and write HYGT_ERR_CUDA to d_status;
+ *   layout         0: a block spread over a group of lanes (several values
+ *        per lane, cross-lane passes by shuffles); 1: one lane per block
+ *        (every pass in registers, multipliers shared by the warp's blocks
+ *        through broadcast loads) for 4x4 and 8x8 blocks with stage -1 .. 2
+ *        (other blocks, and stage 3, return HYGT_ERR_UNSUPPORTED).  The
+ *        secondary-transform calls use layout 0 whatever is set.
+ * max_warps (get) is the largest warps_per_cta of the layout currently set.
  * Results do not depend on the tuning.  A choice whose shared memory does
  * not fit makes the next bucketed call return HYGT_ERR_UNSUPPORTED.  Not
  * thread-safe with concurrent calls on the same plan.
  */
 hygt_status hygt_batch_set_tuning(hygt_plan plan, int inverse, int warps_per_cta,
-                                  int ctas_per_sm, int stage);
+                                  int ctas_per_sm, int stage, int layout);
 hygt_status hygt_batch_get_tuning(hygt_plan plan, int inverse, int *warps_per_cta,
-                                  int *ctas_per_sm, int *stage, int *max_warps);
+                                  int *ctas_per_sm, int *stage, int *layout, int *max_warps);
 
 /*
  * FP32 HyGT through the same set-bucketed schedule (the FP32 forward and

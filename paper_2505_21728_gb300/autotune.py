@@ -1,6 +1,6 @@
 """Autotuners: the launch tuning of the bucketed kernels (blocks per CTA,
-CTAs per SM, staging depth; ``tune_batch``) and the mode of the mixed-size
-launch (``tune_split``).
+CTAs per SM, staging depth, register layout; ``tune_batch``) and the mode
+of the mixed-size launch (``tune_split``).
 
 Mixed launch.
 
@@ -160,20 +160,47 @@ def tune_split(mb, reps=5, use_cache=True, verbose=False):
 
 
 # ---------------------------------------------------------------- launch tuning
-def batch_candidates(max_warps, log2n):
-    """(warps_per_cta, ctas_per_sm, stage) points the batch tuner times:
-    blocks per CTA through the warps of a CTA, CTAs per SM, and the staging
-    depth (0: none, 1: the next task's blocks copied into shared memory
-    ahead, 2: prefetched into L2 ahead, 3: as 1 by one bulk copy per block;
-    N >= 16 only)."""
+def batch_candidates(max_warps, log2n, layout=0):
+    """(warps_per_cta, ctas_per_sm, stage, layout) points the batch tuner
+    times for one register layout: blocks per CTA through the warps of a
+    CTA, CTAs per SM, and the staging depth (0: none, 1: the next task's
+    blocks copied into shared memory ahead, 2: prefetched into L2 ahead, 3:
+    as 1 by one bulk copy per block; N >= 16 only; layout 1 without 3)."""
     warps = sorted({w for w in (max_warps, (3 * max_warps) // 4, max_warps // 2,
                                 max_warps // 3, 4) if w >= 2})
-    stages = (0, 1, 2, 3) if log2n >= 4 else (-1,)
+    if log2n < 4:
+        stages = (-1,)
+    else:
+        stages = (0, 1, 2, 3) if layout == 0 else (0, 1, 2)
     out = []
     for w in warps:
         for c in (0, 1, 2):
             for s in stages:
-                out.append((w, c, s))
+                out.append((w, c, s, layout))
+    return out
+
+
+def batch_layouts(plan, inverse):
+    """Register layouts the plan supports for one direction (0 always; 1,
+    one lane per block, for 4x4 and 8x8 blocks)."""
+    out = [0]
+    if hygt.hygt_batch_set_tuning(plan.handle, inverse, 0, 0, -1, 1) == hygt.HYGT_OK:
+        out.append(1)
+    hygt._check(hygt.hygt_batch_set_tuning(plan.handle, inverse, 0, 0, -1, 0),
+                "hygt_batch_set_tuning")
+    return out
+
+
+def all_batch_candidates(plan, inverse):
+    """batch_candidates over every layout the plan supports."""
+    out = []
+    for lay in batch_layouts(plan, inverse):
+        hygt._check(hygt.hygt_batch_set_tuning(plan.handle, inverse, 0, 0, -1, lay),
+                    "hygt_batch_set_tuning")
+        max_warps = hygt.hygt_batch_get_tuning(plan.handle, inverse)[4]
+        out += batch_candidates(max_warps, plan.log2n, lay)
+    hygt._check(hygt.hygt_batch_set_tuning(plan.handle, inverse, 0, 0, -1, 0),
+                "hygt_batch_set_tuning")
     return out
 
 
@@ -195,10 +222,10 @@ def _time_dir(fn, reps):
 
 
 def tune_batch(batch, x, y, xr, reps=5, use_cache=True, verbose=False, time_fn=None):
-    """Times every launch tuning of ``batch_candidates`` for the bucketed
-    forward and inverse of ``batch`` (a hygt.Batch with its schedule built)
-    and sets the fastest on the plan (hygt_batch_set_tuning).  Returns
-    {"forward": (warps, ctas_per_sm, stage, ms), "inverse": (...)}.
+    """Times every launch tuning of ``all_batch_candidates`` for the
+    bucketed forward and inverse of ``batch`` (a hygt.Batch with its schedule
+    built) and sets the fastest on the plan (hygt_batch_set_tuning).  Returns
+    {"forward": (warps, ctas_per_sm, stage, layout, ms), "inverse": (...)}.
     Results are cached by GPU name, block size, rounds, sets and block count.
     ``time_fn(direction, tuning)`` replaces the GPU timing (tests)."""
     plan = batch.plan
@@ -206,8 +233,8 @@ def tune_batch(batch, x, y, xr, reps=5, use_cache=True, verbose=False, time_fn=N
     cache, path = {}, _cache_path()
     if use_cache:
         import torch
-        key = "batch|%s|N%d_R%d_S%d_B%d" % (torch.cuda.get_device_name(), plan.N, plan.rounds,
-                                             plan.num_sets, batch.nblocks)
+        key = "batch2|%s|N%d_R%d_S%d_B%d" % (torch.cuda.get_device_name(), plan.N, plan.rounds,
+                                              plan.num_sets, batch.nblocks)
         if os.path.exists(path):
             try:
                 with open(path) as f:
@@ -217,14 +244,13 @@ def tune_batch(batch, x, y, xr, reps=5, use_cache=True, verbose=False, time_fn=N
         if key in cache:
             res = {d: tuple(v) for d, v in cache[key].items()}
             for inv, d in ((0, "forward"), (1, "inverse")):
-                hygt._check(hygt.hygt_batch_set_tuning(plan.handle, inv, *res[d][:3]),
+                hygt._check(hygt.hygt_batch_set_tuning(plan.handle, inv, *res[d][:4]),
                             "hygt_batch_set_tuning")
             return res
     res = {}
     for inv, d in ((0, "forward"), (1, "inverse")):
-        max_warps = hygt.hygt_batch_get_tuning(plan.handle, inv)[3]
         best = None
-        for cand in batch_candidates(max_warps, plan.log2n):
+        for cand in all_batch_candidates(plan, inv):
             if hygt.hygt_batch_set_tuning(plan.handle, inv, *cand) != hygt.HYGT_OK:
                 continue
             if time_fn is not None:
@@ -238,11 +264,11 @@ def tune_batch(batch, x, y, xr, reps=5, use_cache=True, verbose=False, time_fn=N
                     continue  # this point does not fit (shared memory)
             if verbose:
                 print("tune %s %s: %.4f ms" % (d, cand, ms))
-            if best is None or ms < best[3]:
-                best = (cand[0], cand[1], cand[2], ms)
+            if best is None or ms < best[4]:
+                best = tuple(cand[:4]) + (ms,)
         if best is None:
-            best = (0, 0, -1, float("nan"))
-        hygt._check(hygt.hygt_batch_set_tuning(plan.handle, inv, *best[:3]),
+            best = (0, 0, -1, 0, float("nan"))
+        hygt._check(hygt.hygt_batch_set_tuning(plan.handle, inv, *best[:4]),
                     "hygt_batch_set_tuning")
         res[d] = best
     if use_cache and key is not None:

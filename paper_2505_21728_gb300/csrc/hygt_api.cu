@@ -37,6 +37,8 @@ struct hygt_plan_s {
   unsigned perm_mask = 0;
   int* d_ktab = nullptr;      // batch path: per-set tables [S][ktab_words]
   int ktab_words = 0;         // words per set, padded to a multiple of 4
+  int* d_ktab1 = nullptr;     // the same for layout 1 (one lane per block; 4x4, 8x8)
+  int ktab1_words = 0;
   hygt::BatchTune tune[2];    // batch path launch tuning: forward, inverse
 };
 
@@ -75,6 +77,7 @@ void free_plan(hygt_plan p) {
   if (p->d_tab_f32) cudaFree(p->d_tab_f32);
   if (p->d_perm) cudaFree(p->d_perm);
   if (p->d_ktab) cudaFree(p->d_ktab);
+  if (p->d_ktab1) cudaFree(p->d_ktab1);
   delete p;
 }
 
@@ -175,16 +178,17 @@ std::vector<int> perm_region_layout(int N, int E, const uint8_t* perm) {
   return word;
 }
 
-// Per-set tables of the batch kernels (layout: hygt::SetTableShape).  Register
-// passes store (c, s - c, -(c + s)) per pair in per-lane segments; lane passes
-// store (c, s) for the m side and (c, -s) for the n side of each pair; then
-// the permutation gather sources as byte offsets in a block's permutation
-// region, per lane.
-bool build_ktab(int log2n, int rounds, int num_sets, const uint8_t* q, const std::vector<int>& ct,
-                const std::vector<int>& st, const std::vector<uint8_t>& perm, unsigned mask,
-                std::vector<int>* out, int* words) {
+// Per-set tables of the batch kernels (layout: hygt::SetTableShape) for
+// 2^log2e values per lane.  Register passes store (c, s - c, -(c + s)) per
+// pair in per-lane segments; lane passes store (c, s) for the m side and
+// (c, -s) for the n side of each pair; then the permutation gather sources
+// as byte offsets in a block's permutation region, per lane.
+bool build_ktab(int log2n, int log2e, int rounds, int num_sets, const uint8_t* q,
+                const std::vector<int>& ct, const std::vector<int>& st,
+                const std::vector<uint8_t>& perm, unsigned mask, std::vector<int>* out,
+                int* words) {
   const int N = 1 << log2n;
-  const hygt::SetTableShape sh{log2n, hygt::batch_log2e(log2n), rounds, mask ? 1 : 0};
+  const hygt::SetTableShape sh{log2n, log2e, rounds, mask ? 1 : 0};
   const int E = sh.e();
   const int w = (sh.set_words() + 3) & ~3;
   *words = w;
@@ -328,12 +332,20 @@ hygt_status hygt_create(hygt_plan* out, int log2n, int rounds, int num_sets,
   if (s == HYGT_OK) s = upload_perms(p, perm, mask);
   if (s == HYGT_OK) {
     std::vector<int> kt;
-    if (!build_ktab(log2n, rounds, num_sets, h_angle_idx, ct, st, perm, mask, &kt,
-                    &p->ktab_words)) {
+    if (!build_ktab(log2n, hygt::batch_log2e(log2n), rounds, num_sets, h_angle_idx, ct, st, perm,
+                    mask, &kt, &p->ktab_words)) {
       free_plan(p);
       return HYGT_ERR_ARG;
     }
     s = upload(reinterpret_cast<void**>(&p->d_ktab), kt.data(), kt.size() * 4, kt.size() * 4);
+    if (s == HYGT_OK && hygt::batch_layout_ok(log2n, 1)) {
+      if (!build_ktab(log2n, hygt::batch_log2e(log2n, 1), rounds, num_sets, h_angle_idx, ct, st,
+                      perm, mask, &kt, &p->ktab1_words)) {
+        free_plan(p);
+        return HYGT_ERR_ARG;
+      }
+      s = upload(reinterpret_cast<void**>(&p->d_ktab1), kt.data(), kt.size() * 4, kt.size() * 4);
+    }
   }
   if (s != HYGT_OK) {
     free_plan(p);
@@ -469,6 +481,8 @@ static hygt::BatchParams make_batch_params(hygt_plan plan, const void* d_work, c
   p.tmax = L.tmax;
   p.ktab = plan->d_ktab;
   p.set_words = plan->ktab_words;
+  p.ktab1 = plan->d_ktab1;
+  p.set_words1 = plan->ktab1_words;
   p.perm_mask = plan->perm_mask;
   p.perms = plan->perm_mask ? 1 : 0;
   p.rounds = plan->rounds;
@@ -545,28 +559,31 @@ hygt_status hygt_inverse_batch_f32(hygt_plan plan, const void* d_work, const flo
 }
 
 hygt_status hygt_batch_set_tuning(hygt_plan plan, int inverse, int warps_per_cta,
-                                  int ctas_per_sm, int stage) {
+                                  int ctas_per_sm, int stage, int layout) {
   if (!plan || (inverse != 0 && inverse != 1) || warps_per_cta < 0 || ctas_per_sm < 0 ||
-      ctas_per_sm > 8 || stage < -1 || stage > 3)
+      ctas_per_sm > 8 || stage < -1 || stage > 3 || layout < 0 || layout > 1)
     return HYGT_ERR_ARG;
-  const int max_warps = hygt::batch_threads(plan->log2n, inverse) / 32;
+  const int max_warps = hygt::batch_threads(plan->log2n, inverse, layout) / 32;
   if (warps_per_cta > max_warps) return HYGT_ERR_ARG;
   if (stage >= 0 && plan->log2n < 4) return HYGT_ERR_UNSUPPORTED;
+  if (layout == 1 && (!plan->d_ktab1 || stage == 3)) return HYGT_ERR_UNSUPPORTED;
   hygt::BatchTune& t = plan->tune[inverse];
   t.warps = warps_per_cta;
   t.ctas_per_sm = ctas_per_sm;
   t.stage = stage;
+  t.layout = layout;
   return HYGT_OK;
 }
 
 hygt_status hygt_batch_get_tuning(hygt_plan plan, int inverse, int* warps_per_cta,
-                                  int* ctas_per_sm, int* stage, int* max_warps) {
+                                  int* ctas_per_sm, int* stage, int* layout, int* max_warps) {
   if (!plan || (inverse != 0 && inverse != 1)) return HYGT_ERR_ARG;
   const hygt::BatchTune& t = plan->tune[inverse];
   if (warps_per_cta) *warps_per_cta = t.warps;
   if (ctas_per_sm) *ctas_per_sm = t.ctas_per_sm;
   if (stage) *stage = t.stage;
-  if (max_warps) *max_warps = hygt::batch_threads(plan->log2n, inverse) / 32;
+  if (layout) *layout = t.layout;
+  if (max_warps) *max_warps = hygt::batch_threads(plan->log2n, inverse, t.layout) / 32;
   return HYGT_OK;
 }
 

@@ -44,8 +44,19 @@ namespace hygt {
 // forward (more blocks per lane group) wants the registers of 384 threads,
 // and so does the 16x16 inverse (four blocks per lane group); the inverse on
 // 32-value blocks the warps of 640; otherwise 512.
-__host__ __device__ constexpr int batch_threads(int log2n, int kind) {
-  return log2n <= 3 ? 512 : (kind == 0 || log2n == 8) ? 384 : (log2n == 5 ? 640 : 512);
+//
+// Layout 1 (one lane per block, log2n 4 and 6 only) holds a whole block in
+// one lane: every pass is a register pass, no shuffles, and a warp task's
+// 32 K blocks share their multipliers by broadcast loads.  Its CTAs have 384
+// threads (the registers of a 64-value block).
+__host__ __device__ constexpr bool batch_layout_ok(int log2n, int lay) {
+  return lay == 0 || (lay == 1 && (log2n == 4 || log2n == 6));
+}
+__host__ __device__ constexpr int batch_threads(int log2n, int kind, int lay = 0) {
+  return lay == 1 ? 384
+         : log2n <= 3 ? 512
+         : (kind == 0 || log2n == 8) ? 384
+                                     : (log2n == 5 ? 640 : 512);
 }
 constexpr int kBucketThreads = 512;  // threads per CTA of the bucketing kernels
 constexpr int kBucketTile = 8192;    // blocks per CTA tile in the scatter pass
@@ -64,7 +75,8 @@ constexpr int kBucketTile = 8192;    // blocks per CTA tile in the scatter pass
 // the 8x8 inverse with K = 8 on 384 threads is 27% slower than K = 4 on
 // 512); for 4x4 blocks E = 8 (two lanes) with K = 8 / 4 rather than one
 // lane per block (forward 5% faster).
-__host__ __device__ constexpr int batch_log2e(int log2n) {
+__host__ __device__ constexpr int batch_log2e(int log2n, int lay = 0) {
+  if (lay == 1) return log2n;
   switch (log2n) {
     case 4: return 3;   // 4x4: 8 values per lane, 2 lanes
     case 5: return 4;
@@ -74,7 +86,8 @@ __host__ __device__ constexpr int batch_log2e(int log2n) {
     default: return log2n;  // N <= 8: one lane per block
   }
 }
-__host__ __device__ constexpr int batch_k(int log2n, bool inv) {
+__host__ __device__ constexpr int batch_k(int log2n, bool inv, int lay = 0) {
+  if (lay == 1) return log2n == 4 ? (inv ? 2 : 4) : 1;
   switch (log2n) {
     case 1: case 2: return 1;
     case 4: case 6: return inv ? 4 : 8;
@@ -83,8 +96,8 @@ __host__ __device__ constexpr int batch_k(int log2n, bool inv) {
     default: return 2;
   }
 }
-__host__ __device__ constexpr int batch_task_group(int log2n, bool inv) {
-  return (32 >> (log2n - batch_log2e(log2n))) * batch_k(log2n, inv);
+__host__ __device__ constexpr int batch_task_group(int log2n, bool inv, int lay = 0) {
+  return (32 >> (log2n - batch_log2e(log2n, lay))) * batch_k(log2n, inv, lay);
 }
 __host__ __device__ constexpr int batch_group(int log2n) {
   return batch_task_group(log2n, false) > batch_task_group(log2n, true)
@@ -184,8 +197,8 @@ struct SetTableShape {
 // lanes) then reach 32 distinct banks in every permutation access.  q(x)
 // numbers the elements of one colour in increasing order, so the words
 // cover 0 .. N-1.
-__host__ __device__ constexpr int perm_region_words(int log2n) {
-  return (1 << log2n) + (1 << (log2n - batch_log2e(log2n)));
+__host__ __device__ constexpr int perm_region_words(int log2n, int lay = 0) {
+  return (1 << log2n) + (1 << (log2n - batch_log2e(log2n, lay)));
 }
 
 // ---------------------------------------------------------------- transform
@@ -199,6 +212,8 @@ struct BatchParams {
   long long tmax;        // capacity of order[] in warp tasks (bounds the task count)
   const int* ktab;       // per-set tables, [S][set_words]
   int set_words;
+  const int* ktab1;      // the same for layout 1 (one lane per block), or null
+  int set_words1;
   unsigned perm_mask;
   int perms;
   int rounds;
@@ -208,13 +223,13 @@ struct BatchParams {
   int* status;
 };
 
-template <int LOG2N, bool INV>
+template <int LOG2N, bool INV, int LAY = 0>
 struct BatchMath {
   static constexpr int N = 1 << LOG2N;
-  static constexpr int LOG2E = batch_log2e(LOG2N);
+  static constexpr int LOG2E = batch_log2e(LOG2N, LAY);
   static constexpr int E = 1 << LOG2E;
   static constexpr int L = N / E;
-  static constexpr int K = batch_k(LOG2N, INV);
+  static constexpr int K = batch_k(LOG2N, INV, LAY);
   using Blocks = int32_t[K][E];
 
   template <int P>
@@ -323,22 +338,22 @@ struct BatchMath {
   }
 };
 
-template <int LOG2N, int KIND>
+template <int LOG2N, int KIND, int LAY = 0>
 __device__ __forceinline__ void batch_load(const BatchParams& p, long long b, int lane,
-                                           int32_t (&v)[BatchMath<LOG2N, false>::E]) {
+                                           int32_t (&v)[BatchMath<LOG2N, false, LAY>::E]) {
   constexpr int N = 1 << LOG2N;
-  constexpr int E = BatchMath<LOG2N, false>::E;
+  constexpr int E = BatchMath<LOG2N, false, LAY>::E;
   if constexpr (KIND == 0)
     load_i16<E>(static_cast<const int16_t*>(p.in) + b * N + lane * E, v);
   else
     load_i32<E>(static_cast<const int32_t*>(p.in) + b * N + lane * E, v);
 }
 
-template <int LOG2N, int KIND>
+template <int LOG2N, int KIND, int LAY = 0>
 __device__ __forceinline__ void batch_store(const BatchParams& p, long long b, int lane,
-                                            const int32_t (&v)[BatchMath<LOG2N, false>::E]) {
+                                            const int32_t (&v)[BatchMath<LOG2N, false, LAY>::E]) {
   constexpr int N = 1 << LOG2N;
-  constexpr int E = BatchMath<LOG2N, false>::E;
+  constexpr int E = BatchMath<LOG2N, false, LAY>::E;
   if constexpr (KIND == 0)
     store_i32<E>(static_cast<int32_t*>(p.out) + b * N + lane * E, v);
   else
@@ -346,11 +361,14 @@ __device__ __forceinline__ void batch_store(const BatchParams& p, long long b, i
 }
 
 // A lane's permutation segment (see SetTableShape): 2E bytes in registers.
-template <int E>
+// OWN_ID (a block per lane, E >= 16): the own words are the identity, so
+// only the E source bytes (the second half of the segment) are loaded.
+template <int E, bool OWN_ID = false>
 struct PermBytes {
-  static constexpr int W = (2 * E + 3) / 4;
+  static constexpr int W = OWN_ID ? E / 4 : (2 * E + 3) / 4;
   uint32_t w[W < 4 ? W : (W + 3) / 4 * 4];
   __device__ __forceinline__ void load(const int* seg) {
+    if constexpr (OWN_ID) seg += E / 4;
     if constexpr (W % 4 == 0) {
 #pragma unroll
       for (int q = 0; q < W / 4; ++q) {
@@ -363,9 +381,13 @@ struct PermBytes {
     }
   }
   // word of this lane's element i in the region / of the element's gather source
-  __device__ __forceinline__ int own(int i) const { return (w[i >> 2] >> (8 * (i & 3))) & 0xFF; }
+  __device__ __forceinline__ int own(int i) const {
+    if constexpr (OWN_ID) return i;
+    return (w[i >> 2] >> (8 * (i & 3))) & 0xFF;
+  }
   __device__ __forceinline__ int src(int i) const {
-    return (w[(E + i) >> 2] >> (8 * ((E + i) & 3))) & 0xFF;
+    constexpr int B = OWN_ID ? 0 : E;
+    return (w[(B + i) >> 2] >> (8 * ((B + i) & 3))) & 0xFF;
   }
 };
 
@@ -376,27 +398,33 @@ struct PermBytes {
 // passes, more independent loads in flight); the 16x16 inverse runs one
 // block per pass (a 16x16 region is 1 KB; measured 1-3% faster with two
 // blocks per lane group), while two passes cost 4x4 blocks 8-10%.
-__host__ __device__ constexpr int batch_perm_k(int log2n, int kind) {
-  return (log2n == 8 && kind == 1) ? 1 : batch_k(log2n, kind == 1);
+__host__ __device__ constexpr int batch_perm_k(int log2n, int kind, int lay = 0) {
+  return (log2n == 8 && kind == 1) ? 1 : batch_k(log2n, kind == 1, lay);
 }
-__host__ __device__ constexpr int perm_buf_words(int log2n, int kind) {
-  return (32 >> (log2n - batch_log2e(log2n))) * batch_perm_k(log2n, kind) *
-         perm_region_words(log2n);
+__host__ __device__ constexpr int perm_buf_words(int log2n, int kind, int lay = 0) {
+  return (32 >> (log2n - batch_log2e(log2n, lay))) * batch_perm_k(log2n, kind, lay) *
+         perm_region_words(log2n, lay);
+}
+
+// Whether a lane's permutation bytes skip the identity own words.
+__host__ __device__ constexpr bool perm_own_id(int log2n, int lay) {
+  return log2n == batch_log2e(log2n, lay) && (1 << log2n) >= 16;
 }
 
 // The permutation slot of one round for the K blocks of this lane group
 // (regions of the warp's buffer `pbuf`): forward, the gather
 // v'[e] = v[perm[e]]; inverse, its undoing v'[perm[e]] = v[e].
-template <int LOG2N, int KIND>
+template <int LOG2N, int KIND, int LAY = 0>
 __device__ __forceinline__ void perm_slot(
-    int32_t (&v)[BatchMath<LOG2N, KIND == 1>::K][BatchMath<LOG2N, KIND == 1>::E],
-    const PermBytes<BatchMath<LOG2N, KIND == 1>::E>& pb, int32_t* pbuf, int grp) {
-  using M = BatchMath<LOG2N, KIND == 1>;
+    int32_t (&v)[BatchMath<LOG2N, KIND == 1, LAY>::K][BatchMath<LOG2N, KIND == 1, LAY>::E],
+    const PermBytes<BatchMath<LOG2N, KIND == 1, LAY>::E, perm_own_id(LOG2N, LAY)>& pb,
+    int32_t* pbuf, int grp) {
+  using M = BatchMath<LOG2N, KIND == 1, LAY>;
   constexpr int E = M::E;
   constexpr int K = M::K;
   constexpr int GROUPS = 32 / M::L;
-  constexpr int RW = perm_region_words(LOG2N);
-  constexpr int KP = batch_perm_k(LOG2N, KIND);
+  constexpr int RW = perm_region_words(LOG2N, LAY);
+  constexpr int KP = batch_perm_k(LOG2N, KIND, LAY);
   static_assert(K % KP == 0, "permutation passes must cover the lane group's blocks");
 #pragma unroll
   for (int k0 = 0; k0 < K; k0 += KP) {
@@ -443,13 +471,13 @@ __host__ __device__ constexpr bool batch_staged(int log2n, int kind) {
   return (kind == 0 || kind == 1) && (log2n == 5 || log2n == 6);
 }
 
-template <int LOG2N, int KIND>
+template <int LOG2N, int KIND, int LAY = 0>
 struct BatchStage {
   static constexpr int N = 1 << LOG2N;
   static constexpr int IB = KIND == 0 ? 2 : 4;  // input bytes per value
-  static constexpr int E = 1 << batch_log2e(LOG2N);
+  static constexpr int E = 1 << batch_log2e(LOG2N, LAY);
   static constexpr int L = N / E;
-  static constexpr int K = batch_k(LOG2N, KIND == 1);
+  static constexpr int K = batch_k(LOG2N, KIND == 1, LAY);
   static constexpr int GROUPS = 32 / L;
   static constexpr int G = GROUPS * K;
   static constexpr int LANE_BYTES = E * IB;
@@ -465,11 +493,12 @@ struct BatchStage {
 // Shared memory of one warp: permutation buffer, then (staged kernels) the
 // stage and the block ids, or (bulk-staged kernels) the stage and the
 // warp's mbarrier.
-template <int LOG2N, int KIND, bool STAGED = batch_staged(LOG2N, KIND), bool BULK = false>
+template <int LOG2N, int KIND, bool STAGED = batch_staged(LOG2N, KIND), bool BULK = false,
+          int LAY = 0>
 __host__ __device__ constexpr int batch_warp_bytes() {
-  return perm_buf_words(LOG2N, KIND) * 4 +
-         (STAGED ? BatchStage<LOG2N, KIND>::BYTES + BatchStage<LOG2N, KIND>::IDS_BYTES : 0) +
-         (BULK ? BatchStage<LOG2N, KIND>::BYTES + 16 : 0);
+  return perm_buf_words(LOG2N, KIND, LAY) * 4 +
+         (STAGED ? BatchStage<LOG2N, KIND, LAY>::BYTES + BatchStage<LOG2N, KIND, LAY>::IDS_BYTES : 0) +
+         (BULK ? BatchStage<LOG2N, KIND, LAY>::BYTES + 16 : 0);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -507,10 +536,10 @@ __device__ __forceinline__ bool batch_mbar_wait(uint32_t bar, uint32_t parity) {
 // Issue the copies of one task: slots l + 32 j of the task (j < GJ) with
 // block ids ids[j] (-1: none).  Lane 0 announces the task's bytes on the
 // barrier first.
-template <int LOG2N, int KIND, int GJ>
+template <int LOG2N, int KIND, int GJ, int LAY = 0>
 __device__ __forceinline__ void bulk_issue(const BatchParams& p, const int (&ids)[GJ],
                                            char* stage, uint32_t bar, int lane32) {
-  using St = BatchStage<LOG2N, KIND>;
+  using St = BatchStage<LOG2N, KIND, LAY>;
   constexpr uint32_t BB = St::N * St::IB;
   int cnt = 0;
 #pragma unroll
@@ -538,10 +567,10 @@ __device__ __forceinline__ void bulk_issue(const BatchParams& p, const int (&ids
 }
 
 // This lane's E values of the block in stage slot `slot`.
-template <int LOG2N, int KIND>
+template <int LOG2N, int KIND, int LAY = 0>
 __device__ __forceinline__ void bulk_read(const char* stage, int slot, int lane,
-                                          int32_t (&v)[BatchStage<LOG2N, KIND>::E]) {
-  using St = BatchStage<LOG2N, KIND>;
+                                          int32_t (&v)[BatchStage<LOG2N, KIND, LAY>::E]) {
+  using St = BatchStage<LOG2N, KIND, LAY>;
   constexpr int LB = St::E * St::IB;  // bytes of one lane
   const char* src = stage + slot * (St::N * St::IB) + lane * LB;
 #pragma unroll
@@ -589,10 +618,10 @@ __device__ __forceinline__ void stage_order(const BatchParams& p, long long t, i
 }
 
 // Copy the input blocks listed in `ids` into the stage.
-template <int LOG2N, int KIND>
+template <int LOG2N, int KIND, int LAY = 0>
 __device__ __forceinline__ void stage_blocks(const BatchParams& p, const int* ids, char* stage,
                                              int lane32) {
-  using St = BatchStage<LOG2N, KIND>;
+  using St = BatchStage<LOG2N, KIND, LAY>;
   const char* in = static_cast<const char*>(p.in);
   const uint32_t sbase = smem_u32(stage);
 #pragma unroll
@@ -610,10 +639,10 @@ __device__ __forceinline__ void stage_blocks(const BatchParams& p, const int* id
 }
 
 // This lane's E values of block k of the staged task.
-template <int LOG2N, int KIND>
+template <int LOG2N, int KIND, int LAY = 0>
 __device__ __forceinline__ void stage_read(const char* stage, int k, int lane32,
-                                           int32_t (&v)[BatchStage<LOG2N, KIND>::E]) {
-  using St = BatchStage<LOG2N, KIND>;
+                                           int32_t (&v)[BatchStage<LOG2N, KIND, LAY>::E]) {
+  using St = BatchStage<LOG2N, KIND, LAY>;
   constexpr int VPC = St::CH / St::IB;  // values per copy
 #pragma unroll
   for (int j = 0; j < St::J; ++j) {
@@ -731,19 +760,22 @@ __device__ __forceinline__ void batch_primary(
 // kernels (STAGED: the input copied into shared memory one task ahead) the
 // stage and the block ids (batch_warp_bytes in all).
 template <int LOG2N, int KIND, bool CACHED, bool STAGED, bool PRIM = false, bool PF = false,
-          bool BULK = false>
+          bool BULK = false, int LAY = 0>
 __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, long long t1,
                                             const int* cache, int set_lo, int32_t* pbuf) {
-  using M = BatchMath<LOG2N, KIND == 1>;
+  using M = BatchMath<LOG2N, KIND == 1, LAY>;
   constexpr int E = M::E;
   constexpr int L = M::L;
   constexpr int K = M::K;
   constexpr int GROUPS = 32 / L;
   constexpr int G = GROUPS * K;
-  constexpr int RW = perm_region_words(LOG2N);
+  constexpr int RW = perm_region_words(LOG2N, LAY);
   constexpr bool INV = (KIND == 1);
   static_assert(!(STAGED && BULK), "one staging scheme at a time");
-  static_assert(!BULK || (LOG2N >= 4 && G == BatchStage<LOG2N, KIND>::G),
+  static_assert(!(BULK && LAY != 0), "the bulk stage reads a block with several lanes");
+  static_assert(!(PRIM && LAY != 0), "the fused primary runs in the lane-group layout");
+  static_assert(batch_group(LOG2N) % G == 0, "the schedule group must hold whole tasks");
+  static_assert(!BULK || (LOG2N >= 4 && G == BatchStage<LOG2N, KIND, LAY>::G),
                 "bulk copies of whole blocks need N * input bytes >= 16");
   const int lane32 = threadIdx.x & 31;
   const int lane = lane32 % L;
@@ -755,8 +787,8 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
   const SetTableShape sh{LOG2N, M::LOG2E, R, p.perms};
   const int rw = sh.round_words();
 
-  char* stage = reinterpret_cast<char*>(pbuf + perm_buf_words(LOG2N, KIND));
-  int* ids = reinterpret_cast<int*>(stage + BatchStage<LOG2N, KIND>::BYTES);  // [2][G]
+  char* stage = reinterpret_cast<char*>(pbuf + perm_buf_words(LOG2N, KIND, LAY));
+  int* ids = reinterpret_cast<int*>(stage + BatchStage<LOG2N, KIND, LAY>::BYTES);  // [2][G]
   if constexpr (STAGED) {
     if (t0 >= t1) return;
     // prologue: ids of the first task, then its blocks and the next task's ids
@@ -764,15 +796,15 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
     cp_async_wait_all();
     __syncwarp();
     if (t0 + 1 < t1) stage_order<G>(p, t0 + 1, ids + ((t0 + 1) & 1) * G, lane32);
-    stage_blocks<LOG2N, KIND>(p, ids + (t0 & 1) * G, stage, lane32);
+    stage_blocks<LOG2N, KIND, LAY>(p, ids + (t0 & 1) * G, stage, lane32);
     cp_async_commit();
   }
 
   // bulk stage: the task's block ids in registers (slot l + 32 j in lane l),
   // this task's and the next one's
   constexpr int GJ = (G + 31) / 32;
-  char* bstage = reinterpret_cast<char*>(pbuf + perm_buf_words(LOG2N, KIND));
-  const uint32_t bbar = smem_u32(bstage + BatchStage<LOG2N, KIND>::BYTES);
+  char* bstage = reinterpret_cast<char*>(pbuf + perm_buf_words(LOG2N, KIND, LAY));
+  const uint32_t bbar = smem_u32(bstage + BatchStage<LOG2N, KIND, LAY>::BYTES);
   uint32_t bphase = 0;
   int ids_cur[GJ], ids_next[GJ];
   if constexpr (BULK) {
@@ -788,7 +820,7 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
       ids_cur[j] = sl < G ? __ldg(p.order + t0 * G + sl) : -1;
       ids_next[j] = (sl < G && t0 + 1 < t1) ? __ldg(p.order + (t0 + 1) * G + sl) : -1;
     }
-    bulk_issue<LOG2N, KIND, GJ>(p, ids_cur, bstage, bbar, lane32);
+    bulk_issue<LOG2N, KIND, GJ, LAY>(p, ids_cur, bstage, bbar, lane32);
   }
 
   int bucket = 0, bucket_end = 0;
@@ -815,7 +847,7 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
         const int sl = k * GROUPS + grp;  // sl / 32 == (k * GROUPS) / 32: GROUPS divides 32
         b[k] = __shfl_sync(kFullMask, ids_cur[(k * GROUPS) >> 5], sl & 31);
         active[k] = b[k] >= 0 && b[k] < p.nblocks;
-        bulk_read<LOG2N, KIND>(bstage, sl, lane, v[k]);
+        bulk_read<LOG2N, KIND, LAY>(bstage, sl, lane, v[k]);
       }
       __syncwarp();
       if (t + 1 < t1) {
@@ -825,7 +857,7 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
           const int sl = lane32 + 32 * j;
           ids_next[j] = (sl < G && t + 2 < t1) ? __ldg(p.order + (t + 2) * G + sl) : -1;
         }
-        bulk_issue<LOG2N, KIND, GJ>(p, ids_cur, bstage, bbar, lane32);
+        bulk_issue<LOG2N, KIND, GJ, LAY>(p, ids_cur, bstage, bbar, lane32);
       }
     } else if constexpr (STAGED) {
       cp_async_wait_all();
@@ -834,26 +866,29 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
       for (int k = 0; k < K; ++k) {
         b[k] = ids[(t & 1) * G + k * GROUPS + grp];
         active[k] = b[k] >= 0 && b[k] < p.nblocks;
-        stage_read<LOG2N, KIND>(stage, k, lane32, v[k]);  // zero-filled when inactive
+        stage_read<LOG2N, KIND, LAY>(stage, k, lane32, v[k]);  // zero-filled when inactive
       }
       __syncwarp();
       if (t + 1 < t1) {  // next task's blocks, and the ids of the one after
         if (t + 2 < t1) stage_order<G>(p, t + 2, ids + (t & 1) * G, lane32);
-        stage_blocks<LOG2N, KIND>(p, ids + ((t + 1) & 1) * G, stage, lane32);
+        stage_blocks<LOG2N, KIND, LAY>(p, ids + ((t + 1) & 1) * G, stage, lane32);
       }
       cp_async_commit();
     } else {
       if constexpr (PF) {
         // pull the next task's blocks into L2 while this one computes: each
-        // lane asks for its own E values of each block
+        // lane asks for the 128-byte lines of its own E values of each block
         if (t + 1 < t1) {
+          constexpr int LB = E * (KIND == 0 ? 2 : 4);
 #pragma unroll
           for (int k = 0; k < K; ++k) {
             const int nbk = __ldg(p.order + slot + G + k * GROUPS + grp);
             if (nbk >= 0 && nbk < p.nblocks) {
               const char* a = static_cast<const char*>(p.in) +
                               ((long long)nbk * (1 << LOG2N) + lane * E) * (KIND == 0 ? 2 : 4);
-              asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a));
+#pragma unroll
+              for (int o = 0; o < LB; o += 128)
+                asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a + o));
             }
           }
         }
@@ -863,7 +898,7 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
         b[k] = __ldg(p.order + slot + k * GROUPS + grp);
         active[k] = b[k] >= 0 && b[k] < p.nblocks;
         if (active[k]) {
-          batch_load<LOG2N, KIND>(p, b[k], lane, v[k]);
+          batch_load<LOG2N, KIND, LAY>(p, b[k], lane, v[k]);
         } else {
 #pragma unroll
           for (int i = 0; i < E; ++i) v[k][i] = 0;
@@ -879,11 +914,11 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
       for (int rr = 0; rr < R; ++rr) {
         const int r = INV ? (R - 1 - rr) : rr;
         const bool has_perm = p.perms && ((p.perm_mask >> r) & 1u);
-        PermBytes<E> pb;
+        PermBytes<E, perm_own_id(LOG2N, LAY)> pb;
         if (has_perm) pb.load(stab + sh.perm_offset(r) + lane * sh.perm_seg());
-        if (INV && has_perm) perm_slot<LOG2N, KIND>(v, pb, pbuf, grp);  // undo slot r's gather
+        if (INV && has_perm) perm_slot<LOG2N, KIND, LAY>(v, pb, pbuf, grp);  // undo slot r's gather
         M::template round<0>(v, stab + r * rw, lane, half, f);
-        if (!INV && has_perm) perm_slot<LOG2N, KIND>(v, pb, pbuf, grp);  // gather of slot r
+        if (!INV && has_perm) perm_slot<LOG2N, KIND, LAY>(v, pb, pbuf, grp);  // gather of slot r
       }
     } else if (bucket == S + 1) {  // bad set index: zeros, status
 #pragma unroll
@@ -898,7 +933,7 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
     }
 #pragma unroll
     for (int k = 0; k < K; ++k)
-      if (active[k]) batch_store<LOG2N, KIND>(p, b[k], lane, v[k]);
+      if (active[k]) batch_store<LOG2N, KIND, LAY>(p, b[k], lane, v[k]);
   }
   if constexpr (STAGED) cp_async_wait_all();
 }
@@ -908,12 +943,11 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
 // tables (max_cached_sets x set_words) followed by batch_warp_bytes per warp.
 // KIND 0: int16 -> int32 forward; KIND 1: int32 -> int16 inverse.
 template <int LOG2N, int KIND, bool STAGED = batch_staged(LOG2N, KIND), bool PRIM = false,
-          bool PF = false, bool BULK = false>
+          bool PF = false, bool BULK = false, int LAY = 0>
 __device__ __forceinline__ void batch_cta(const BatchParams& p, long long cta, long long ncta,
                                           int32_t* smem) {
-  constexpr int GS = batch_group(LOG2N);                 // schedule group
-  constexpr int G = batch_task_group(LOG2N, KIND == 1);  // this kernel's task size
-  constexpr int RW = perm_region_words(LOG2N);
+  constexpr int GS = batch_group(LOG2N);                      // schedule group
+  constexpr int G = batch_task_group(LOG2N, KIND == 1, LAY);  // this kernel's task size
 
   // The schedule must have been built for this block count, set count and G.
   if (p.meta[1] != (int)p.nblocks || p.meta[2] != p.num_sets || p.meta[3] != GS) {
@@ -951,27 +985,30 @@ __device__ __forceinline__ void batch_cta(const BatchParams& p, long long cta, l
   }
   __syncthreads();
 
-  int32_t* wbuf = pbuf + (size_t)warp * (batch_warp_bytes<LOG2N, KIND, STAGED, BULK>() / 4);
+  int32_t* wbuf =
+      pbuf + (size_t)warp * (batch_warp_bytes<LOG2N, KIND, STAGED, BULK, LAY>() / 4);
   if (cached)
-    batch_tasks<LOG2N, KIND, true, STAGED, PRIM, PF, BULK>(p, t0, t1, cache, set_lo, wbuf);
+    batch_tasks<LOG2N, KIND, true, STAGED, PRIM, PF, BULK, LAY>(p, t0, t1, cache, set_lo, wbuf);
   else
-    batch_tasks<LOG2N, KIND, false, STAGED, PRIM, PF, BULK>(p, t0, t1, cache, set_lo, wbuf);
+    batch_tasks<LOG2N, KIND, false, STAGED, PRIM, PF, BULK, LAY>(p, t0, t1, cache, set_lo, wbuf);
 }
 
 // Dynamic shared memory of batch_cta for block size 2^LOG2N without the set
 // tables: batch_warp_bytes per warp.
-template <int LOG2N, int KIND, bool STAGED = batch_staged(LOG2N, KIND), bool BULK = false>
+template <int LOG2N, int KIND, bool STAGED = batch_staged(LOG2N, KIND), bool BULK = false,
+          int LAY = 0>
 __host__ __device__ inline size_t batch_pbuf_bytes(int threads) {
-  return (size_t)(threads / 32) * batch_warp_bytes<LOG2N, KIND, STAGED, BULK>();
+  return (size_t)(threads / 32) * batch_warp_bytes<LOG2N, KIND, STAGED, BULK, LAY>();
 }
 
 // The kernel may be launched with fewer threads than batch_threads (a
 // multiple of 32): the launch tuning picks the warps per CTA.
 template <int LOG2N, int KIND, bool STAGED, bool PRIM = false, bool PF = false,
-          bool BULK = false>
-__global__ void __launch_bounds__(batch_threads(LOG2N, KIND), 1) hygt_batch_kernel(BatchParams p) {
+          bool BULK = false, int LAY = 0>
+__global__ void __launch_bounds__(batch_threads(LOG2N, KIND, LAY), 1)
+    hygt_batch_kernel(BatchParams p) {
   extern __shared__ __align__(16) int32_t bsmem[];
-  batch_cta<LOG2N, KIND, STAGED, PRIM, PF, BULK>(p, blockIdx.x, gridDim.x, bsmem);
+  batch_cta<LOG2N, KIND, STAGED, PRIM, PF, BULK, LAY>(p, blockIdx.x, gridDim.x, bsmem);
 }
 
 // Launch tuning of the bucketed kernels (one per plan and direction): warps
@@ -979,11 +1016,14 @@ __global__ void __launch_bounds__(batch_threads(LOG2N, KIND), 1) hygt_batch_kern
 // how the next task's input is fetched ahead (-1: the measured default
 // batch_staged; 0: not at all; 1: copied into shared memory one task ahead;
 // 2: prefetched into L2 one task ahead; 3: copied into shared memory one
-// task ahead by one bulk copy per block; 1, 2 and 3 for N >= 16).
+// task ahead by one bulk copy per block; 1, 2 and 3 for N >= 16), and the
+// register layout (0: lane groups; 1: one lane per block, 4x4 and 8x8
+// blocks, stages 0 to 2).
 struct BatchTune {
   int warps = 0;
   int ctas_per_sm = 0;
   int stage = -1;
+  int layout = 0;
 };
 
 // Set tables a CTA keeps in shared memory: as many as its share of the

@@ -11,18 +11,23 @@
 namespace hygt {
 
 template <int LOG2N, int KIND, bool STAGED, bool PRIM = false, bool PF = false,
-          bool BULK = false>
+          bool BULK = false, int LAY = 0>
 inline cudaError_t launch_variant(BatchParams p, cudaStream_t stream, const BatchTune& tune) {
-  auto kern = hygt_batch_kernel<LOG2N, KIND, STAGED, PRIM, PF, BULK>;
+  auto kern = hygt_batch_kernel<LOG2N, KIND, STAGED, PRIM, PF, BULK, LAY>;
+  if constexpr (LAY == 1) {  // the layout's own set tables
+    if (!p.ktab1) return cudaErrorInvalidConfiguration;
+    p.ktab = p.ktab1;
+    p.set_words = p.set_words1;
+  }
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
   const DeviceInfo info = device_info(dev);
-  constexpr int G = batch_task_group(LOG2N, KIND == 1);
-  constexpr int kMaxWarps = batch_threads(LOG2N, KIND) / 32;
+  constexpr int G = batch_task_group(LOG2N, KIND == 1, LAY);
+  constexpr int kMaxWarps = batch_threads(LOG2N, KIND, LAY) / 32;
   const int warps = tune.warps > 0 && tune.warps < kMaxWarps ? tune.warps : kMaxWarps;
   const int threads = warps * 32;
-  const size_t pbuf = batch_pbuf_bytes<LOG2N, KIND, STAGED, BULK>(threads);
+  const size_t pbuf = batch_pbuf_bytes<LOG2N, KIND, STAGED, BULK, LAY>(threads);
   const size_t set_bytes = (size_t)p.set_words * 4;
   // with several CTAs per SM each gets its share of the shared memory
   const int want = tune.ctas_per_sm > 0 ? tune.ctas_per_sm : 1;
@@ -66,6 +71,16 @@ template <int LOG2N, int KIND>
 inline cudaError_t launch_batch_sized(const BatchParams& p, cudaStream_t stream,
                                       const BatchTune& tune) {
   constexpr bool kDefault = batch_staged(LOG2N, KIND);
+  if constexpr (batch_layout_ok(LOG2N, 1)) {
+    if (tune.layout == 1) {
+      const int stage = tune.stage < 0 ? 0 : tune.stage;
+      if (stage == 2) return launch_variant<LOG2N, KIND, false, false, true, false, 1>(p, stream, tune);
+      if (stage == 1) return launch_variant<LOG2N, KIND, true, false, false, false, 1>(p, stream, tune);
+      if (stage == 0) return launch_variant<LOG2N, KIND, false, false, false, false, 1>(p, stream, tune);
+      return cudaErrorInvalidConfiguration;
+    }
+  }
+  if (tune.layout != 0) return cudaErrorInvalidConfiguration;
   if constexpr (LOG2N >= 4) {
     const int stage = batch_stage_of<LOG2N, KIND>(p, tune);
     if (stage == 3)

@@ -121,9 +121,9 @@ def _load() -> ctypes.CDLL:
     L.dense_klt_build.restype = i32
     L.dense_klt_apply.argtypes = [P, P, P, P, i64, i32, P, P]
     L.dense_klt_apply.restype = i32
-    L.hygt_batch_set_tuning.argtypes = [P, i32, i32, i32, i32]
+    L.hygt_batch_set_tuning.argtypes = [P, i32, i32, i32, i32, i32]
     L.hygt_batch_set_tuning.restype = i32
-    L.hygt_batch_get_tuning.argtypes = [P, i32] + [ctypes.POINTER(i32)] * 4
+    L.hygt_batch_get_tuning.argtypes = [P, i32] + [ctypes.POINTER(i32)] * 5
     L.hygt_batch_get_tuning.restype = i32
     L.hygt_mixed_ctas.argtypes = []
     L.hygt_mixed_ctas.restype = i32
@@ -362,14 +362,15 @@ def dense_klt_apply(d, d_work, d_x, d_y, nblocks, kind, stream, d_status):
     return int(_lib.dense_klt_apply(d, d_work, d_x, d_y, nblocks, kind, stream, d_status))
 
 
-def hygt_batch_set_tuning(plan, inverse, warps_per_cta, ctas_per_sm, stage):
+def hygt_batch_set_tuning(plan, inverse, warps_per_cta, ctas_per_sm, stage, layout=0):
     return int(_lib.hygt_batch_set_tuning(plan, int(inverse), int(warps_per_cta),
-                                          int(ctas_per_sm), int(stage)))
+                                          int(ctas_per_sm), int(stage), int(layout)))
 
 
 def hygt_batch_get_tuning(plan, inverse):
-    """(warps_per_cta, ctas_per_sm, stage, max_warps) of one direction."""
-    vals = [ctypes.c_int() for _ in range(4)]
+    """(warps_per_cta, ctas_per_sm, stage, layout, max_warps) of one
+    direction; max_warps is that of the layout set."""
+    vals = [ctypes.c_int() for _ in range(5)]
     _check(_lib.hygt_batch_get_tuning(plan, int(inverse), *[ctypes.byref(v) for v in vals]),
            "hygt_batch_get_tuning")
     return tuple(v.value for v in vals)

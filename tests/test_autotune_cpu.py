@@ -112,14 +112,16 @@ def test_batch_tuner_picks_the_modelled_best(at, monkeypatch):
     from paper_2505_21728_gb300 import hygt
     state = {}
 
-    def fake_set(plan, inv, w, c, s):
+    def fake_set(plan, inv, w, c, s, lay=0):
         if c == 2 and w > 8:  # pretend these do not fit
             return hygt.HYGT_ERR_UNSUPPORTED
-        state[inv] = (w, c, s)
+        if lay == 1 and s == 1:  # nor these
+            return hygt.HYGT_ERR_UNSUPPORTED
+        state[inv] = (w, c, s, lay)
         return hygt.HYGT_OK
 
     def fake_get(plan, inv):
-        return state.get(inv, (0, 0, -1)) + (12,)
+        return state.get(inv, (0, 0, -1, 0)) + (12,)
 
     monkeypatch.setattr(hygt, "hygt_batch_set_tuning", fake_set)
     monkeypatch.setattr(hygt, "hygt_batch_get_tuning", fake_get)
@@ -131,11 +133,12 @@ def test_batch_tuner_picks_the_modelled_best(at, monkeypatch):
         plan, nblocks = _P(), 1000
 
     def model(direction, cand):
-        w, c, s = cand
+        w, c, s, lay = cand
         base = 1.0 + abs(w - 9) * 0.1 + (0.05 if c == 0 else 0.0)
+        base -= 0.3 if lay == 1 and direction == "inverse" else 0.0
         return base - (0.2 if s == 1 and direction == "forward" else 0.0)
 
     res = at.tune_batch(_B(), None, None, None, use_cache=False, time_fn=model)
-    assert res["forward"][:3] == (9, 1, 1)
-    assert res["inverse"][:3] in ((9, 1, 0), (9, 1, 1))
-    assert state[0] == (9, 1, 1)
+    assert res["forward"][:4] == (9, 1, 1, 0)
+    assert res["inverse"][:4] == (9, 1, 0, 1)   # layout 1, first of the equal stages
+    assert state[0] == (9, 1, 1, 0) and state[1] == (9, 1, 0, 1)

@@ -87,6 +87,8 @@ def test_traffic_only_for_the_current_kernel_sources(tmp_path, monkeypatch):
     assert bench.ncu_traffic("fwd", "w8", (12, 0, 0, 0.5)) == 1572022272
     assert bench.ncu_traffic("fwd", "w8", (12, 0, 2, 0.5)) is None   # another launch variant
     assert bench.ncu_traffic("inv", "w8", (4, 0, 2)) == 1600000000
+    assert bench.ncu_traffic("fwd", "w8", (12, 0, 0, 0, 0.5)) == 1572022272  # layout 0
+    assert bench.ncu_traffic("fwd", "w8", (12, 0, 0, 1, 0.5)) is None        # layout 1
     assert bench.ncu_traffic("fwd", "other") is None
     _tree(tmp_path, "kernel v1", name="secondary.cu")  # another kernel's source: no effect
     assert bench.kernel_source_sha() == sha1

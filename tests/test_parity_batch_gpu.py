@@ -215,7 +215,8 @@ def test_batch_f32_parity(gpu, orc, log2n, rounds, perm_kind):
 @pytest.mark.parametrize("log2n,rounds", [(4, 2), (5, 2), (6, 2), (7, 2), (8, 3)])
 def test_batch_every_launch_tuning_bit_exact(gpu, orc, log2n, rounds):
     """Every point the launch tuner can pick (warps per CTA, CTAs per SM,
-    staging depth) gives the oracle's integers, forward and inverse."""
+    staging depth, register layout) gives the oracle's integers, forward and
+    inverse."""
     import torch
     from paper_2505_21728_gb300 import autotune
     N, S = 1 << log2n, 105
@@ -230,10 +231,11 @@ def test_batch_every_launch_tuning_bit_exact(gpu, orc, log2n, rounds):
     b = gpu.Batch(plan, B).build(_t(sets))
     dx, dy = _t(x), _t(ye)
     ran = 0
+    layouts = set()
     for inv in (0, 1):
-        max_w = gpu.hygt_batch_get_tuning(plan.handle, inv)[3]
-        for cand in autotune.batch_candidates(max_w, log2n):
+        for cand in autotune.all_batch_candidates(plan, inv):
             assert gpu.hygt_batch_set_tuning(plan.handle, inv, *cand) == gpu.HYGT_OK
+            layouts.add(cand[3])
             st = torch.zeros(1, dtype=torch.int32, device="cuda")
             try:
                 out = b.forward(dx, status=st) if inv == 0 else b.inverse(dy, status=st)
@@ -244,8 +246,9 @@ def test_batch_every_launch_tuning_bit_exact(gpu, orc, log2n, rounds):
             assert int(st.item()) == 0, cand
             assert np.array_equal(out.cpu().numpy(), xe if inv else ye), (inv, cand)
             ran += 1
-        gpu.hygt_batch_set_tuning(plan.handle, inv, 0, 0, -1)
+        gpu.hygt_batch_set_tuning(plan.handle, inv, 0, 0, -1, 0)
     assert ran >= 8
+    assert layouts == ({0, 1} if log2n in (4, 6) else {0})
     plan.close()
 
 
@@ -263,8 +266,8 @@ def test_tune_batch_sets_a_fitting_point(gpu, tmp_path, monkeypatch):
     xr = torch.empty_like(x)
     res = autotune.tune_batch(b, x, y, xr, reps=2)
     for inv, d in ((0, "forward"), (1, "inverse")):
-        w, c, s, ms = res[d]
-        assert gpu.hygt_batch_get_tuning(plan.handle, inv)[:3] == (w, c, s)
+        w, c, s, lay, ms = res[d]
+        assert gpu.hygt_batch_get_tuning(plan.handle, inv)[:4] == (w, c, s, lay)
         assert ms > 0
     again = autotune.tune_batch(b, x, y, xr, reps=2)  # from the cache
     assert again == {k: tuple(v) for k, v in res.items()}
