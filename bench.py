@@ -207,17 +207,17 @@ def kernel_source_sha(files=BATCH_SOURCES) -> str:
 
 def ncu_traffic(kernel: str, workload: str, tuning=None):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel sources and (when given) the same launch tuning (a line
-    'bench-traffic: kernel=... workload=... sha=... tuning=w,c,s[,layout]
-    bytes_per_launch=...' in profiles/*.md; the layout is written when it is
-    not 0); else None.  ``tuning``: (warps, ctas_per_sm, stage[, layout, ...])."""
+    the current kernel sources and (when given) the same kernel variant: a
+    line 'bench-traffic: kernel=... workload=... sha=... variant=s,l
+    bytes_per_launch=...' in profiles/*.md, with s the staging choice and l
+    the register layout of the launch tuning (warps per CTA and CTAs per SM
+    change the launch, not the bytes a launch moves); else None.
+    ``tuning``: (warps, ctas_per_sm, stage[, layout, ...])."""
     sha = kernel_source_sha()
     want = None
     if tuning is not None:
-        vals = [int(v) for v in tuning[:3]]
-        if len(tuning) > 4 and int(tuning[3]) != 0:
-            vals.append(int(tuning[3]))
-        want = ",".join(str(v) for v in vals)
+        lay = int(tuning[3]) if len(tuning) > 4 else 0
+        want = "%d,%d" % (int(tuning[2]), lay)
     for p in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
         with open(p) as f:
             for line in f:
@@ -225,7 +225,7 @@ def ncu_traffic(kernel: str, workload: str, tuning=None):
                     continue
                 kv = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
                 if kv.get("kernel") == kernel and kv.get("workload") == workload \
-                        and kv.get("sha") == sha and (want is None or kv.get("tuning") == want):
+                        and kv.get("sha") == sha and (want is None or kv.get("variant") == want):
                     return int(float(kv["bytes_per_launch"]))
     return None
 

@@ -80,12 +80,13 @@ def test_traffic_only_for_the_current_kernel_sources(tmp_path, monkeypatch):
     sha1 = bench.kernel_source_sha()
     (tmp_path / "profiles" / "k.md").write_text(
         "# summary\n"
-        "bench-traffic: kernel=fwd workload=w8 sha=%s tuning=12,0,0 bytes_per_launch=1572022272\n"
-        "bench-traffic: kernel=inv workload=w8 sha=%s tuning=4,0,2 bytes_per_launch=1.6e9\n"
+        "bench-traffic: kernel=fwd workload=w8 sha=%s variant=0,0 bytes_per_launch=1572022272\n"
+        "bench-traffic: kernel=inv workload=w8 sha=%s variant=2,0 bytes_per_launch=1.6e9\n"
         % (sha1, sha1))
     assert bench.ncu_traffic("fwd", "w8") == 1572022272
     assert bench.ncu_traffic("fwd", "w8", (12, 0, 0, 0.5)) == 1572022272
-    assert bench.ncu_traffic("fwd", "w8", (12, 0, 2, 0.5)) is None   # another launch variant
+    assert bench.ncu_traffic("fwd", "w8", (4, 2, 0, 0.5)) == 1572022272     # same kernel
+    assert bench.ncu_traffic("fwd", "w8", (12, 0, 2, 0.5)) is None   # another staging variant
     assert bench.ncu_traffic("inv", "w8", (4, 0, 2)) == 1600000000
     assert bench.ncu_traffic("fwd", "w8", (12, 0, 0, 0, 0.5)) == 1572022272  # layout 0
     assert bench.ncu_traffic("fwd", "w8", (12, 0, 0, 1, 0.5)) is None        # layout 1
