@@ -192,7 +192,10 @@ def measured_peaks():
 
 # the sources of the set-bucketed integer kernels (the benchmark's dominant kernels)
 BATCH_SOURCES = ("hygt_batch.cuh", "hygt_batch_launch.cuh", "hygt_device.cuh", "hygt_primary.cuh",
-                 "hygt_launch.cuh", "batch_int.cu", "batch_fwd.cu", "batch_inv.cu")
+                 "hygt_launch.cuh", "batch_int.cu", "batch_fwd.cu", "batch_inv.cu",
+                 "batch_n_small.cu", "batch_n_4_fwd.cu", "batch_n_4_inv.cu", "batch_n_5.cu",
+                 "batch_n_6_fwd.cu", "batch_n_6_inv.cu", "batch_n_7.cu", "batch_n_8_fwd.cu",
+                 "batch_n_8_inv.cu")
 
 
 def kernel_source_sha(files=BATCH_SOURCES) -> str:

@@ -186,11 +186,15 @@ hygt_status hygt_inverse_batch(hygt_plan plan, const void *d_work, const int32_t
  *        copy that has not landed within about a second makes the warp stop
  *        and write HYGT_ERR_CUDA to d_status;
  *   layout         0: a block spread over a group of lanes (several values
- *        per lane, cross-lane passes by shuffles); 1: one lane per block
- *        (every pass in registers, multipliers shared by the warp's blocks
- *        through broadcast loads) for 4x4 and 8x8 blocks with stage -1 .. 2
- *        (other blocks, and stage 3, return HYGT_ERR_UNSUPPORTED).  The
- *        secondary-transform calls use layout 0 whatever is set.
+ *        per lane, cross-lane passes by shuffles, several blocks per lane
+ *        group sharing each multiplier load); 1: one lane per block (every
+ *        pass in registers, multipliers shared by the warp's blocks through
+ *        broadcast loads; 4x4 and 8x8 blocks); 2: more values per lane and
+ *        fewer blocks per lane group (8x8, 16x16: 32 values, 2 blocks) or
+ *        the reverse (4x4: 4 values, 8 / 4 blocks).  Layouts 1 and 2 take
+ *        stage -1 .. 2; other block sizes, and stage 3, return
+ *        HYGT_ERR_UNSUPPORTED.  The secondary-transform calls use layout 0
+ *        whatever is set.
  * max_warps (get) is the largest warps_per_cta of the layout currently set.
  * Results do not depend on the tuning.  A choice whose shared memory does
  * not fit makes the next bucketed call return HYGT_ERR_UNSUPPORTED.  Not

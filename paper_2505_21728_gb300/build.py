@@ -74,7 +74,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return obj
 
     srcs = _sources()
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(os.cpu_count() or 8, len(srcs)))) as ex:
         objs = list(ex.map(compile_one, srcs))
     libdir = _cuda_lib_dir(nvcc)
     tmp = SO + ".tmp.%d" % os.getpid()

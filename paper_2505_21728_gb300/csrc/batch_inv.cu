@@ -1,18 +1,28 @@
-// batch_inv.cu -- inverse launchers of the set-bucketed kernels (the
-// instantiations of hygt_batch_launch.cuh for the inverse direction).
-#include "hygt_batch_launch.cuh"
+// batch_inv.cu -- inverse launchers of the set-bucketed kernels: dispatch on
+// the block size to the per-size launchers of batch_n*.cu.
+#include "hygt_batch.cuh"
 
 namespace hygt {
 
 cudaError_t launch_batch_inv(int log2n, const BatchParams& p, cudaStream_t stream,
                              const BatchTune& tune) {
-  return launch_batch<1>(log2n, p, stream, tune);
+  switch (log2n) {
+    case 1: return launch_batch_n<1, 1>(p, stream, tune);
+    case 2: return launch_batch_n<2, 1>(p, stream, tune);
+    case 3: return launch_batch_n<3, 1>(p, stream, tune);
+    case 4: return launch_batch_n<4, 1>(p, stream, tune);
+    case 5: return launch_batch_n<5, 1>(p, stream, tune);
+    case 6: return launch_batch_n<6, 1>(p, stream, tune);
+    case 7: return launch_batch_n<7, 1>(p, stream, tune);
+    case 8: return launch_batch_n<8, 1>(p, stream, tune);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_batch_primary_inv(int log2n, const BatchParams& p, cudaStream_t stream,
                                      const BatchTune& tune) {
-  if (log2n == 4) return launch_primary_sized<4, 1>(p, stream, tune);
-  if (log2n == 6) return launch_primary_sized<6, 1>(p, stream, tune);
+  if (log2n == 4) return launch_primary_n<4, 1>(p, stream, tune);
+  if (log2n == 6) return launch_primary_n<6, 1>(p, stream, tune);
   return cudaErrorInvalidValue;
 }
 

@@ -1,0 +1,9 @@
+// batch_n_4_inv.cu -- bucketed inverse kernels for 4x4 blocks (with the fused DCT-II primary).
+#include "hygt_batch_launch.cuh"
+
+namespace hygt {
+
+template cudaError_t launch_batch_n<4, 1>(const BatchParams&, cudaStream_t, const BatchTune&);
+template cudaError_t launch_primary_n<4, 1>(const BatchParams&, cudaStream_t, const BatchTune&);
+
+}  // namespace hygt

@@ -37,8 +37,8 @@ struct hygt_plan_s {
   unsigned perm_mask = 0;
   int* d_ktab = nullptr;      // batch path: per-set tables [S][ktab_words]
   int ktab_words = 0;         // words per set, padded to a multiple of 4
-  int* d_ktab1 = nullptr;     // the same for layout 1 (one lane per block; 4x4, 8x8)
-  int ktab1_words = 0;
+  int* d_ktabs[hygt::kBatchLayouts] = {};  // the same per register layout ([0] = d_ktab)
+  int ktabs_words[hygt::kBatchLayouts] = {};
   hygt::BatchTune tune[2];    // batch path launch tuning: forward, inverse
 };
 
@@ -77,7 +77,8 @@ void free_plan(hygt_plan p) {
   if (p->d_tab_f32) cudaFree(p->d_tab_f32);
   if (p->d_perm) cudaFree(p->d_perm);
   if (p->d_ktab) cudaFree(p->d_ktab);
-  if (p->d_ktab1) cudaFree(p->d_ktab1);
+  for (int l = 1; l < hygt::kBatchLayouts; ++l)
+    if (p->d_ktabs[l]) cudaFree(p->d_ktabs[l]);
   delete p;
 }
 
@@ -338,13 +339,17 @@ hygt_status hygt_create(hygt_plan* out, int log2n, int rounds, int num_sets,
       return HYGT_ERR_ARG;
     }
     s = upload(reinterpret_cast<void**>(&p->d_ktab), kt.data(), kt.size() * 4, kt.size() * 4);
-    if (s == HYGT_OK && hygt::batch_layout_ok(log2n, 1)) {
-      if (!build_ktab(log2n, hygt::batch_log2e(log2n, 1), rounds, num_sets, h_angle_idx, ct, st,
-                      perm, mask, &kt, &p->ktab1_words)) {
+    p->d_ktabs[0] = p->d_ktab;
+    p->ktabs_words[0] = p->ktab_words;
+    for (int l = 1; l < hygt::kBatchLayouts && s == HYGT_OK; ++l) {
+      if (!hygt::batch_layout_ok(log2n, l)) continue;
+      if (!build_ktab(log2n, hygt::batch_log2e(log2n, l), rounds, num_sets, h_angle_idx, ct, st,
+                      perm, mask, &kt, &p->ktabs_words[l])) {
         free_plan(p);
         return HYGT_ERR_ARG;
       }
-      s = upload(reinterpret_cast<void**>(&p->d_ktab1), kt.data(), kt.size() * 4, kt.size() * 4);
+      s = upload(reinterpret_cast<void**>(&p->d_ktabs[l]), kt.data(), kt.size() * 4,
+                 kt.size() * 4);
     }
   }
   if (s != HYGT_OK) {
@@ -481,8 +486,10 @@ static hygt::BatchParams make_batch_params(hygt_plan plan, const void* d_work, c
   p.tmax = L.tmax;
   p.ktab = plan->d_ktab;
   p.set_words = plan->ktab_words;
-  p.ktab1 = plan->d_ktab1;
-  p.set_words1 = plan->ktab1_words;
+  for (int l = 0; l < hygt::kBatchLayouts; ++l) {
+    p.ktabs[l] = plan->d_ktabs[l];
+    p.set_words_of[l] = plan->ktabs_words[l];
+  }
   p.perm_mask = plan->perm_mask;
   p.perms = plan->perm_mask ? 1 : 0;
   p.rounds = plan->rounds;
@@ -561,12 +568,12 @@ hygt_status hygt_inverse_batch_f32(hygt_plan plan, const void* d_work, const flo
 hygt_status hygt_batch_set_tuning(hygt_plan plan, int inverse, int warps_per_cta,
                                   int ctas_per_sm, int stage, int layout) {
   if (!plan || (inverse != 0 && inverse != 1) || warps_per_cta < 0 || ctas_per_sm < 0 ||
-      ctas_per_sm > 8 || stage < -1 || stage > 3 || layout < 0 || layout > 1)
+      ctas_per_sm > 8 || stage < -1 || stage > 3 || layout < 0 || layout >= hygt::kBatchLayouts)
     return HYGT_ERR_ARG;
   const int max_warps = hygt::batch_threads(plan->log2n, inverse, layout) / 32;
   if (warps_per_cta > max_warps) return HYGT_ERR_ARG;
   if (stage >= 0 && plan->log2n < 4) return HYGT_ERR_UNSUPPORTED;
-  if (layout == 1 && (!plan->d_ktab1 || stage == 3)) return HYGT_ERR_UNSUPPORTED;
+  if (layout != 0 && (!plan->d_ktabs[layout] || stage == 3)) return HYGT_ERR_UNSUPPORTED;
   hygt::BatchTune& t = plan->tune[inverse];
   t.warps = warps_per_cta;
   t.ctas_per_sm = ctas_per_sm;

@@ -45,15 +45,19 @@ namespace hygt {
 // and so does the 16x16 inverse (four blocks per lane group); the inverse on
 // 32-value blocks the warps of 640; otherwise 512.
 //
-// Layout 1 (one lane per block, log2n 4 and 6 only) holds a whole block in
-// one lane: every pass is a register pass, no shuffles, and a warp task's
-// 32 K blocks share their multipliers by broadcast loads.  Its CTAs have 384
-// threads (the registers of a 64-value block).
+// Other register layouts (launch-tuning choices, batch_log2e / batch_k):
+// layout 1 holds a whole block in one lane (4x4, 8x8): every pass is a
+// register pass, no shuffles, and a warp task's 32 K blocks share their
+// multipliers by broadcast loads; layout 2 holds more values per lane with
+// fewer blocks per lane group (8x8, 16x16: E = 32, K = 2) or fewer values
+// with more blocks (4x4: E = 4, K = 8 / 4).  Their CTAs have 384 threads.
+constexpr int kBatchLayouts = 3;
 __host__ __device__ constexpr bool batch_layout_ok(int log2n, int lay) {
-  return lay == 0 || (lay == 1 && (log2n == 4 || log2n == 6));
+  return lay == 0 || (lay == 1 && (log2n == 4 || log2n == 6)) ||
+         (lay == 2 && (log2n == 4 || log2n == 6 || log2n == 8));
 }
 __host__ __device__ constexpr int batch_threads(int log2n, int kind, int lay = 0) {
-  return lay == 1 ? 384
+  return lay != 0 ? 384
          : log2n <= 3 ? 512
          : (kind == 0 || log2n == 8) ? 384
                                      : (log2n == 5 ? 640 : 512);
@@ -77,6 +81,7 @@ constexpr int kBucketTile = 8192;    // blocks per CTA tile in the scatter pass
 // lane per block (forward 5% faster).
 __host__ __device__ constexpr int batch_log2e(int log2n, int lay = 0) {
   if (lay == 1) return log2n;
+  if (lay == 2) return log2n == 4 ? 2 : 5;
   switch (log2n) {
     case 4: return 3;   // 4x4: 8 values per lane, 2 lanes
     case 5: return 4;
@@ -88,6 +93,7 @@ __host__ __device__ constexpr int batch_log2e(int log2n, int lay = 0) {
 }
 __host__ __device__ constexpr int batch_k(int log2n, bool inv, int lay = 0) {
   if (lay == 1) return log2n == 4 ? (inv ? 2 : 4) : 1;
+  if (lay == 2) return log2n == 4 ? (inv ? 4 : 8) : 2;
   switch (log2n) {
     case 1: case 2: return 1;
     case 4: case 6: return inv ? 4 : 8;
@@ -212,8 +218,8 @@ struct BatchParams {
   long long tmax;        // capacity of order[] in warp tasks (bounds the task count)
   const int* ktab;       // per-set tables, [S][set_words]
   int set_words;
-  const int* ktab1;      // the same for layout 1 (one lane per block), or null
-  int set_words1;
+  const int* ktabs[3];   // the same for each register layout (null: not built)
+  int set_words_of[3];
   unsigned perm_mask;
   int perms;
   int rounds;
@@ -1039,7 +1045,14 @@ __host__ inline int batch_cached_sets(size_t max_smem, size_t pbuf, size_t set_b
   return (int)(fit < cap ? fit : cap);
 }
 
-// Host launchers (batch_int.cu).
+// Launchers of one block size and direction (hygt_batch_launch.cuh,
+// instantiated in batch_n*.cu).
+template <int LOG2N, int KIND>
+cudaError_t launch_batch_n(const BatchParams& p, cudaStream_t stream, const BatchTune& tune);
+template <int LOG2N, int KIND>
+cudaError_t launch_primary_n(const BatchParams& p, cudaStream_t stream, const BatchTune& tune);
+
+// Host launchers (batch_int.cu, batch_fwd.cu, batch_inv.cu).
 cudaError_t batch_build(const uint16_t* d_set, long long nblocks, int num_sets, int group,
                         void* d_work, cudaStream_t stream);
 cudaError_t launch_batch_fwd(int log2n, const BatchParams& p, cudaStream_t stream,

@@ -1,6 +1,6 @@
 // hygt_batch_launch.cuh -- launch templates of the set-bucketed kernels,
-// included by the per-direction translation units (batch_fwd.cu,
-// batch_inv.cu) so that their many instantiations compile in parallel.
+// instantiated per block size and direction by the batch_n*.cu translation
+// units, so that their many kernels compile in parallel.
 #pragma once
 
 #include <atomic>
@@ -14,10 +14,10 @@ template <int LOG2N, int KIND, bool STAGED, bool PRIM = false, bool PF = false,
           bool BULK = false, int LAY = 0>
 inline cudaError_t launch_variant(BatchParams p, cudaStream_t stream, const BatchTune& tune) {
   auto kern = hygt_batch_kernel<LOG2N, KIND, STAGED, PRIM, PF, BULK, LAY>;
-  if constexpr (LAY == 1) {  // the layout's own set tables
-    if (!p.ktab1) return cudaErrorInvalidConfiguration;
-    p.ktab = p.ktab1;
-    p.set_words = p.set_words1;
+  if constexpr (LAY != 0) {  // the layout's own set tables
+    if (!p.ktabs[LAY]) return cudaErrorInvalidConfiguration;
+    p.ktab = p.ktabs[LAY];
+    p.set_words = p.set_words_of[LAY];
   }
   int dev = 0;
   cudaError_t err = cudaGetDevice(&dev);
@@ -65,6 +65,16 @@ inline int batch_stage_of(const BatchParams& p, const BatchTune& tune) {
   return stage;
 }
 
+// A register layout other than the default: stages 0 (default), 1 and 2.
+template <int LOG2N, int KIND, int LAY>
+inline cudaError_t launch_layout(const BatchParams& p, cudaStream_t stream, const BatchTune& tune) {
+  const int stage = tune.stage < 0 ? 0 : tune.stage;
+  if (stage == 2) return launch_variant<LOG2N, KIND, false, false, true, false, LAY>(p, stream, tune);
+  if (stage == 1) return launch_variant<LOG2N, KIND, true, false, false, false, LAY>(p, stream, tune);
+  if (stage == 0) return launch_variant<LOG2N, KIND, false, false, false, false, LAY>(p, stream, tune);
+  return cudaErrorInvalidConfiguration;
+}
+
 // Staging exists as a tuning choice for N >= 16; smaller blocks keep the
 // measured default (no stage).
 template <int LOG2N, int KIND>
@@ -72,13 +82,10 @@ inline cudaError_t launch_batch_sized(const BatchParams& p, cudaStream_t stream,
                                       const BatchTune& tune) {
   constexpr bool kDefault = batch_staged(LOG2N, KIND);
   if constexpr (batch_layout_ok(LOG2N, 1)) {
-    if (tune.layout == 1) {
-      const int stage = tune.stage < 0 ? 0 : tune.stage;
-      if (stage == 2) return launch_variant<LOG2N, KIND, false, false, true, false, 1>(p, stream, tune);
-      if (stage == 1) return launch_variant<LOG2N, KIND, true, false, false, false, 1>(p, stream, tune);
-      if (stage == 0) return launch_variant<LOG2N, KIND, false, false, false, false, 1>(p, stream, tune);
-      return cudaErrorInvalidConfiguration;
-    }
+    if (tune.layout == 1) return launch_layout<LOG2N, KIND, 1>(p, stream, tune);
+  }
+  if constexpr (batch_layout_ok(LOG2N, 2)) {
+    if (tune.layout == 2) return launch_layout<LOG2N, KIND, 2>(p, stream, tune);
   }
   if (tune.layout != 0) return cudaErrorInvalidConfiguration;
   if constexpr (LOG2N >= 4) {
@@ -93,25 +100,13 @@ inline cudaError_t launch_batch_sized(const BatchParams& p, cudaStream_t stream,
   }
 }
 
-template <int KIND>
-inline cudaError_t launch_batch(int log2n, const BatchParams& p, cudaStream_t stream,
-                                const BatchTune& tune) {
-  switch (log2n) {
-    case 1: return launch_batch_sized<1, KIND>(p, stream, tune);
-    case 2: return launch_batch_sized<2, KIND>(p, stream, tune);
-    case 3: return launch_batch_sized<3, KIND>(p, stream, tune);
-    case 4: return launch_batch_sized<4, KIND>(p, stream, tune);
-    case 5: return launch_batch_sized<5, KIND>(p, stream, tune);
-    case 6: return launch_batch_sized<6, KIND>(p, stream, tune);
-    case 7: return launch_batch_sized<7, KIND>(p, stream, tune);
-    case 8: return launch_batch_sized<8, KIND>(p, stream, tune);
-    default: return cudaErrorInvalidValue;
-  }
+template <int LOG2N, int KIND>
+cudaError_t launch_batch_n(const BatchParams& p, cudaStream_t stream, const BatchTune& tune) {
+  return launch_batch_sized<LOG2N, KIND>(p, stream, tune);
 }
 
 template <int LOG2N, int KIND>
-inline cudaError_t launch_primary_sized(const BatchParams& p, cudaStream_t stream,
-                                        const BatchTune& tune) {
+cudaError_t launch_primary_n(const BatchParams& p, cudaStream_t stream, const BatchTune& tune) {
   const int stage = batch_stage_of<LOG2N, KIND>(p, tune);
   if (stage == 3) return launch_variant<LOG2N, KIND, false, true, false, true>(p, stream, tune);
   if (stage == 2) return launch_variant<LOG2N, KIND, false, true, true>(p, stream, tune);
