@@ -1032,9 +1032,11 @@ def _int_case_data(name, nblocks):
     return w, d, plan, x, s
 
 
-def case_batch(args, name=DEFAULT_WORKLOAD):
-    """bucket + integer forward + integer inverse (8x8 blocks, 105 sets)"""
+def case_batch(args, name=None):
+    """bucket + integer forward + integer inverse (8x8 blocks, 105 sets, or
+    --workload: a named workload or a class of a mixed batch)"""
     import torch
+    name = name or args.workload
     from paper_2505_21728_gb300 import hygt
     w, d, plan, x, s = _int_case_data(name, args.nblocks)
     for inv, t in ((0, args.fwd_tuning), (1, args.inv_tuning)):

@@ -181,7 +181,16 @@ def truncated(w: Workload, nblocks: int) -> Workload:
 
 
 def get(name: str) -> Workload:
-    return _REGISTRY[name]
+    """A named workload, or one block-size class of a mixed batch
+    ("mixed_frame_2160p16/N16", "/N64", "/N256")."""
+    if name in _REGISTRY:
+        return _REGISTRY[name]
+    base, _, cls = name.partition("/")
+    if base in _MIXED and cls:
+        for c in _MIXED[base].classes():
+            if c.name == name:
+                return c
+    raise KeyError(name)
 
 
 def names():
