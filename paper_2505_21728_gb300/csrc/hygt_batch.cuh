@@ -50,11 +50,13 @@ namespace hygt {
 // register pass, no shuffles, and a warp task's 32 K blocks share their
 // multipliers by broadcast loads; layout 2 holds more values per lane with
 // fewer blocks per lane group (8x8, 16x16: E = 32, K = 2) or fewer values
-// with more blocks (4x4: E = 4, K = 8 / 4).  Their CTAs have 384 threads.
-constexpr int kBatchLayouts = 3;
+// with more blocks (4x4: E = 4, K = 8 / 4); layout 3 (8x8) is layout 0 with
+// the forward's 8 blocks per lane group in the inverse too.  Their CTAs have
+// 384 threads.
+constexpr int kBatchLayouts = 4;
 __host__ __device__ constexpr bool batch_layout_ok(int log2n, int lay) {
   return lay == 0 || (lay == 1 && (log2n == 4 || log2n == 6)) ||
-         (lay == 2 && (log2n == 4 || log2n == 6 || log2n == 8));
+         (lay == 2 && (log2n == 4 || log2n == 6 || log2n == 8)) || (lay == 3 && log2n == 6);
 }
 __host__ __device__ constexpr int batch_threads(int log2n, int kind, int lay = 0) {
   return lay != 0 ? 384
@@ -82,6 +84,7 @@ constexpr int kBucketTile = 8192;    // blocks per CTA tile in the scatter pass
 __host__ __device__ constexpr int batch_log2e(int log2n, int lay = 0) {
   if (lay == 1) return log2n;
   if (lay == 2) return log2n == 4 ? 2 : 5;
+  if (lay == 3) return 3;
   switch (log2n) {
     case 4: return 3;   // 4x4: 8 values per lane, 2 lanes
     case 5: return 4;
@@ -94,6 +97,7 @@ __host__ __device__ constexpr int batch_log2e(int log2n, int lay = 0) {
 __host__ __device__ constexpr int batch_k(int log2n, bool inv, int lay = 0) {
   if (lay == 1) return log2n == 4 ? (inv ? 2 : 4) : 1;
   if (lay == 2) return log2n == 4 ? (inv ? 4 : 8) : 2;
+  if (lay == 3) return 8;
   switch (log2n) {
     case 1: case 2: return 1;
     case 4: case 6: return inv ? 4 : 8;
@@ -218,8 +222,8 @@ struct BatchParams {
   long long tmax;        // capacity of order[] in warp tasks (bounds the task count)
   const int* ktab;       // per-set tables, [S][set_words]
   int set_words;
-  const int* ktabs[3];   // the same for each register layout (null: not built)
-  int set_words_of[3];
+  const int* ktabs[4];   // the same for each register layout (null: not built)
+  int set_words_of[4];
   unsigned perm_mask;
   int perms;
   int rounds;
