@@ -192,7 +192,7 @@ hygt_status hygt_inverse_batch(hygt_plan plan, const void *d_work, const int32_t
  *        broadcast loads; 4x4 and 8x8 blocks); 2: more values per lane and
  *        fewer blocks per lane group (8x8, 16x16: 32 values, 2 blocks) or
  *        the reverse (4x4: 4 values, 8 / 4 blocks); 3: layout 0 with 8
- *        blocks per lane group in the inverse as in the forward (8x8).
+ *        blocks per lane group in the inverse as in the forward (4x4, 8x8).
  *        Layouts 1 to 3 take stage -1 .. 2; other block sizes, and stage 3,
  *        return
  *        HYGT_ERR_UNSUPPORTED.  The secondary-transform calls use layout 0

@@ -187,7 +187,7 @@ def batch_layouts(plan, inverse):
     """Register layouts the plan supports for one direction (0 always; 1,
     one lane per block, for 4x4 and 8x8 blocks; 2, other values per lane and
     blocks per lane group, for 4x4, 8x8 and 16x16 blocks; 3, eight blocks per
-    lane group in both directions, for 8x8 blocks)."""
+    lane group in both directions, for 4x4 and 8x8 blocks)."""
     out = [0]
     for lay in range(1, BATCH_LAYOUTS):
         if hygt.hygt_batch_set_tuning(plan.handle, inverse, 0, 0, -1, lay) == hygt.HYGT_OK:

@@ -50,13 +50,13 @@ namespace hygt {
 // register pass, no shuffles, and a warp task's 32 K blocks share their
 // multipliers by broadcast loads; layout 2 holds more values per lane with
 // fewer blocks per lane group (8x8, 16x16: E = 32, K = 2) or fewer values
-// with more blocks (4x4: E = 4, K = 8 / 4); layout 3 (8x8) is layout 0 with
-// the forward's 8 blocks per lane group in the inverse too.  Their CTAs have
-// 384 threads.
+// with more blocks (4x4: E = 4, K = 8 / 4); layout 3 (4x4, 8x8) is layout 0
+// with the forward's 8 blocks per lane group in the inverse too.  Their CTAs
+// have 384 threads.
 constexpr int kBatchLayouts = 4;
 __host__ __device__ constexpr bool batch_layout_ok(int log2n, int lay) {
   return lay == 0 || (lay == 1 && (log2n == 4 || log2n == 6)) ||
-         (lay == 2 && (log2n == 4 || log2n == 6 || log2n == 8)) || (lay == 3 && log2n == 6);
+         (lay == 2 && (log2n == 4 || log2n == 6 || log2n == 8)) || (lay == 3 && (log2n == 4 || log2n == 6));
 }
 __host__ __device__ constexpr int batch_threads(int log2n, int kind, int lay = 0) {
   return lay != 0 ? 384

@@ -248,7 +248,7 @@ def test_batch_every_launch_tuning_bit_exact(gpu, orc, log2n, rounds):
             ran += 1
         gpu.hygt_batch_set_tuning(plan.handle, inv, 0, 0, -1, 0)
     assert ran >= 8
-    assert layouts == {4: {0, 1, 2}, 6: {0, 1, 2, 3}, 8: {0, 2}}.get(log2n, {0})
+    assert layouts == {4: {0, 1, 2, 3}, 6: {0, 1, 2, 3}, 8: {0, 2}}.get(log2n, {0})
     plan.close()
 
 
