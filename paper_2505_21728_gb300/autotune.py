@@ -180,14 +180,16 @@ def batch_candidates(max_warps, log2n, layout=0):
     return out
 
 
-BATCH_LAYOUTS = 4
+BATCH_LAYOUTS = 5
 
 
 def batch_layouts(plan, inverse):
     """Register layouts the plan supports for one direction (0 always; 1,
     one lane per block, for 4x4 and 8x8 blocks; 2, other values per lane and
     blocks per lane group, for 4x4, 8x8 and 16x16 blocks; 3, eight blocks per
-    lane group in both directions, for 4x4 and 8x8 blocks)."""
+    lane group in both directions, for 4x4 and 8x8 blocks; 4, the cross-lane
+    passes replaced by register passes on the transposed block, for 16x16
+    blocks)."""
     out = [0]
     for lay in range(1, BATCH_LAYOUTS):
         if hygt.hygt_batch_set_tuning(plan.handle, inverse, 0, 0, -1, lay) == hygt.HYGT_OK:

@@ -183,13 +183,18 @@ std::vector<int> perm_region_layout(int N, int E, const uint8_t* perm) {
 // 2^log2e values per lane.  Register passes store (c, s - c, -(c + s)) per
 // pair in per-lane segments; lane passes store (c, s) for the m side and
 // (c, -s) for the n side of each pair; then the permutation gather sources
-// as byte offsets in a block's permutation region, per lane.
+// as byte offsets in a block's permutation region, per lane.  all_reg (the
+// transposed layout, E = N / E values per lane): passes p >= log2e are
+// register passes of the transposed block, and the permutation slot reads
+// the transposed block and writes the natural one.
 bool build_ktab(int log2n, int log2e, int rounds, int num_sets, const uint8_t* q,
                 const std::vector<int>& ct, const std::vector<int>& st,
                 const std::vector<uint8_t>& perm, unsigned mask, std::vector<int>* out,
-                int* words) {
+                int* words, bool all_reg = false) {
   const int N = 1 << log2n;
-  const hygt::SetTableShape sh{log2n, log2e, rounds, mask ? 1 : 0};
+  hygt::SetTableShape sh{log2n, log2e, rounds, mask ? 1 : 0};
+  sh.all_reg = all_reg;
+  if (all_reg && 2 * log2e != log2n) return false;
   const int E = sh.e();
   const int w = (sh.set_words() + 3) & ~3;
   *words = w;
@@ -207,6 +212,17 @@ bool build_ktab(int log2n, int log2e, int rounds, int num_sets, const uint8_t* q
             e3[0] = c;
             e3[1] = sn - c;
             e3[2] = -(c + sn);
+          } else if (all_reg) {
+            // transposed block: lane l holds elements (i << log2e) + l; the
+            // pair's m side m = (im << log2e) + l with im the register index
+            // of its slot jl (the kernel's register-pass order for bit p - log2e)
+            const int m = ((((j >> p) << (p + 1)) | (j & ((1 << p) - 1))));
+            const int l = m & (E - 1), im = m >> log2e, pb = p - log2e;
+            const int jl = ((im >> (pb + 1)) << pb) | (im & ((1 << pb) - 1));
+            int* e3 = row + l * sh.seg() + 3 * jl;
+            e3[0] = c;
+            e3[1] = sn - c;
+            e3[2] = -(c + sn);
           } else {
             int* m = row + sh.lane_word(j, 0);
             int* n = row + sh.lane_word(j, 1);
@@ -221,13 +237,34 @@ bool build_ktab(int log2n, int log2e, int rounds, int num_sets, const uint8_t* q
         std::vector<uint8_t> ident(N);
         for (int i = 0; i < N; ++i) ident[i] = (uint8_t)i;
         const uint8_t* pr = perm.empty() ? ident.data() : perm.data() + ((size_t)s * rounds + r) * N;
-        const std::vector<int> word = perm_region_layout(N, E, pr);
-        if (word.empty()) return false;
-        for (int l = 0; l < N / E; ++l) {
-          uint8_t* b = reinterpret_cast<uint8_t*>(t + sh.perm_offset(r) + l * sh.perm_seg());
-          for (int i = 0; i < E; ++i) {
-            b[i] = (uint8_t)word[l * E + i];
-            b[E + i] = (uint8_t)word[pr[l * E + i]];
+        if (!all_reg) {
+          const std::vector<int> word = perm_region_layout(N, E, pr);
+          if (word.empty()) return false;
+          for (int l = 0; l < N / E; ++l) {
+            uint8_t* b = reinterpret_cast<uint8_t*>(t + sh.perm_offset(r) + l * sh.perm_seg());
+            for (int i = 0; i < E; ++i) {
+              b[i] = (uint8_t)word[l * E + i];
+              b[E + i] = (uint8_t)word[pr[l * E + i]];
+            }
+          }
+        } else {
+          // The slot is written from the transposed block (lane l, register
+          // i' holds element i' E + l) and read as the natural one.  Relabel
+          // element x = a E + b as tr(x) = b E + a: the elements one register
+          // index of the transposed block writes are then one natural group,
+          // and the colouring of perm_region_layout keeps both the writes and
+          // the gathered reads on distinct banks; the word of x is that of tr(x).
+          auto tr = [&](int x) { return ((x & (E - 1)) << log2e) | (x >> log2e); };
+          std::vector<uint8_t> pt(N);
+          for (int e = 0; e < N; ++e) pt[e] = (uint8_t)tr(pr[e]);
+          const std::vector<int> word = perm_region_layout(N, E, pt.data());
+          if (word.empty()) return false;
+          for (int l = 0; l < N / E; ++l) {
+            uint8_t* b = reinterpret_cast<uint8_t*>(t + sh.perm_offset(r) + l * sh.perm_seg());
+            for (int i = 0; i < E; ++i) {
+              b[i] = (uint8_t)word[tr((i << log2e) + l)];
+              b[E + i] = (uint8_t)word[tr(pr[l * E + i])];
+            }
           }
         }
       }
@@ -344,7 +381,7 @@ hygt_status hygt_create(hygt_plan* out, int log2n, int rounds, int num_sets,
     for (int l = 1; l < hygt::kBatchLayouts && s == HYGT_OK; ++l) {
       if (!hygt::batch_layout_ok(log2n, l)) continue;
       if (!build_ktab(log2n, hygt::batch_log2e(log2n, l), rounds, num_sets, h_angle_idx, ct, st,
-                      perm, mask, &kt, &p->ktabs_words[l])) {
+                      perm, mask, &kt, &p->ktabs_words[l], hygt::batch_layout_all_reg(l))) {
         free_plan(p);
         return HYGT_ERR_ARG;
       }

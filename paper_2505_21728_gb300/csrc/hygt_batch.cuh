@@ -51,13 +51,18 @@ namespace hygt {
 // multipliers by broadcast loads; layout 2 holds more values per lane with
 // fewer blocks per lane group (8x8, 16x16: E = 32, K = 2) or fewer values
 // with more blocks (4x4: E = 4, K = 8 / 4); layout 3 (4x4, 8x8) is layout 0
-// with the forward's 8 blocks per lane group in the inverse too.  Their CTAs
-// have 384 threads.
-constexpr int kBatchLayouts = 4;
+// with the forward's 8 blocks per lane group in the inverse too; layout 4
+// (16x16) is layout 0 with the cross-lane passes replaced by register passes
+// on the transposed block (a shared-memory transpose in the middle of each
+// round, the transpose back folded into the permutation slot where there is
+// one).  Their CTAs have 384 threads.
+constexpr int kBatchLayouts = 5;
 __host__ __device__ constexpr bool batch_layout_ok(int log2n, int lay) {
   return lay == 0 || (lay == 1 && (log2n == 4 || log2n == 6)) ||
-         (lay == 2 && (log2n == 4 || log2n == 6 || log2n == 8)) || (lay == 3 && (log2n == 4 || log2n == 6));
+         (lay == 2 && (log2n == 4 || log2n == 6 || log2n == 8)) ||
+         (lay == 3 && (log2n == 4 || log2n == 6)) || (lay == 4 && log2n == 8);
 }
+__host__ __device__ constexpr bool batch_layout_all_reg(int lay) { return lay == 4; }
 __host__ __device__ constexpr int batch_threads(int log2n, int kind, int lay = 0) {
   return lay != 0 ? 384
          : log2n <= 3 ? 512
@@ -85,6 +90,7 @@ __host__ __device__ constexpr int batch_log2e(int log2n, int lay = 0) {
   if (lay == 1) return log2n;
   if (lay == 2) return log2n == 4 ? 2 : 5;
   if (lay == 3) return 3;
+  if (lay == 4) return log2n / 2;
   switch (log2n) {
     case 4: return 3;   // 4x4: 8 values per lane, 2 lanes
     case 5: return 4;
@@ -98,6 +104,7 @@ __host__ __device__ constexpr int batch_k(int log2n, bool inv, int lay = 0) {
   if (lay == 1) return log2n == 4 ? (inv ? 2 : 4) : 1;
   if (lay == 2) return log2n == 4 ? (inv ? 4 : 8) : 2;
   if (lay == 3) return 8;
+  if (lay == 4) return 4;
   switch (log2n) {
     case 1: case 2: return 1;
     case 4: case 6: return inv ? 4 : 8;
@@ -162,8 +169,14 @@ __host__ __device__ inline BatchLayout batch_layout(int num_sets, long long nblo
 //   below).
 // The segment strides are odd numbers of 16-byte chunks and the chunk skew
 // spreads the (up to 8) lanes of a block over distinct bank groups.
+// all_reg (the transposed layout, batch layout 4): every pass is stored as a
+// register pass -- passes p >= log2e for a lane that holds the elements
+// (i << log2e) + l of a transposed block (pairs over bit p - log2e of i) --
+// and each round's permutation bytes are those of the transposing slot
+// (own: the words of the lane's transposed elements; sources as above).
 struct SetTableShape {
   int log2n, log2e, rounds, perms;
+  bool all_reg = false;
   __host__ __device__ constexpr int n() const { return 1 << log2n; }
   __host__ __device__ constexpr int e() const { return 1 << log2e; }
   __host__ __device__ constexpr int lanes() const { return 1 << (log2n - log2e); }
@@ -178,7 +191,8 @@ struct SetTableShape {
     return 4 * (((2 * e() + 15) / 16) | (lanes() > 1 ? 1 : 0));
   }
   __host__ __device__ constexpr int pass_offset(int p) const {
-    return reg_row() * (p < log2e ? p : log2e) + lane_row() * (p < log2e ? 0 : p - log2e);
+    return all_reg ? reg_row() * p
+                   : reg_row() * (p < log2e ? p : log2e) + lane_row() * (p < log2e ? 0 : p - log2e);
   }
   __host__ __device__ constexpr int round_words() const { return pass_offset(log2n); }
   __host__ __device__ constexpr int perm_offset(int r) const {
@@ -222,8 +236,8 @@ struct BatchParams {
   long long tmax;        // capacity of order[] in warp tasks (bounds the task count)
   const int* ktab;       // per-set tables, [S][set_words]
   int set_words;
-  const int* ktabs[4];   // the same for each register layout (null: not built)
-  int set_words_of[4];
+  const int* ktabs[kBatchLayouts];  // the same for each register layout (null: not built)
+  int set_words_of[kBatchLayouts];
   unsigned perm_mask;
   int perms;
   int rounds;
@@ -335,6 +349,21 @@ struct BatchMath {
       reg_pass<P>(v, row, lane, half, f);
     else
       lane_pass<P>(v, row, lane, half, f);
+  }
+
+  // Pass p of the transposed layout (all passes register passes; passes
+  // p >= LOG2E act on bit p - LOG2E of the register index of the transposed
+  // block): passes [P0, P1) in increasing order forward, decreasing inverse.
+  template <int P0, int P1, int J = 0>
+  __device__ __forceinline__ static void tpasses(Blocks& v, const int* rtab, int lane,
+                                                 uint32_t half, int f) {
+    if constexpr (J < P1 - P0) {
+      constexpr int P = INV ? P1 - 1 - J : P0 + J;
+      SetTableShape sh{LOG2N, LOG2E, 1, 0};
+      sh.all_reg = true;
+      reg_pass<(P < LOG2E ? P : P - LOG2E)>(v, rtab + sh.pass_offset(P), lane, half, f);
+      tpasses<P0, P1, J + 1>(v, rtab, lane, half, f);
+    }
   }
 
   // All passes of one round: increasing p forward, decreasing p inverse.
@@ -450,6 +479,66 @@ __device__ __forceinline__ void perm_slot(
       const int32_t* region = pbuf + (kk * GROUPS + grp) * RW;
 #pragma unroll
       for (int i = 0; i < E; ++i) v[k0 + kk][i] = region[KIND == 1 ? pb.own(i) : pb.src(i)];
+    }
+    __syncwarp();
+  }
+}
+
+// Transposes of the K blocks of this lane group between the natural layout
+// (lane l holds elements l E + i) and the transposed one (lane l holds
+// elements i E + l; E = L), through the blocks' regions of the permutation
+// buffer.  Word of element x = a E + 4 q + r (q: 16-byte chunk of lane a's
+// row): a E + 4 (q ^ ((a >> 1) & (E / 4 - 1))) + r -- a natural row is
+// written or read as E / 4 16-byte chunks and a transposed column as E
+// words, both without bank conflicts.
+template <int LOG2N, int KIND, int LAY, bool TO_T>
+__device__ __forceinline__ void tr_slot(
+    int32_t (&v)[BatchMath<LOG2N, KIND == 1, LAY>::K][BatchMath<LOG2N, KIND == 1, LAY>::E],
+    int32_t* pbuf, int grp, int lane) {
+  using M = BatchMath<LOG2N, KIND == 1, LAY>;
+  constexpr int E = M::E;
+  constexpr int K = M::K;
+  constexpr int GROUPS = 32 / M::L;
+  constexpr int RW = perm_region_words(LOG2N, LAY);
+  constexpr int KP = batch_perm_k(LOG2N, KIND, LAY);
+  constexpr int QM = E / 4 - 1;
+  static_assert(M::L == E && E % 4 == 0, "square blocks of whole chunks");
+#pragma unroll
+  for (int k0 = 0; k0 < K; k0 += KP) {
+#pragma unroll
+    for (int kk = 0; kk < KP; ++kk) {
+      int32_t* region = pbuf + (kk * GROUPS + grp) * RW;
+      if constexpr (TO_T) {  // natural rows out
+#pragma unroll
+        for (int q = 0; q < E / 4; ++q)
+          *reinterpret_cast<int4*>(region + lane * E + 4 * (q ^ ((lane >> 1) & QM))) =
+              make_int4(v[k0 + kk][4 * q], v[k0 + kk][4 * q + 1], v[k0 + kk][4 * q + 2],
+                        v[k0 + kk][4 * q + 3]);
+      } else {  // transposed columns out
+#pragma unroll
+        for (int i = 0; i < E; ++i)
+          region[i * E + 4 * ((lane >> 2) ^ ((i >> 1) & QM)) + (lane & 3)] = v[k0 + kk][i];
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int kk = 0; kk < KP; ++kk) {
+      const int32_t* region = pbuf + (kk * GROUPS + grp) * RW;
+      if constexpr (TO_T) {  // transposed columns in
+#pragma unroll
+        for (int i = 0; i < E; ++i)
+          v[k0 + kk][i] = region[i * E + 4 * ((lane >> 2) ^ ((i >> 1) & QM)) + (lane & 3)];
+      } else {  // natural rows in
+#pragma unroll
+        for (int q = 0; q < E / 4; ++q) {
+          const int4 t =
+              *reinterpret_cast<const int4*>(region + lane * E + 4 * (q ^ ((lane >> 1) & QM)));
+          v[k0 + kk][4 * q] = t.x;
+          v[k0 + kk][4 * q + 1] = t.y;
+          v[k0 + kk][4 * q + 2] = t.z;
+          v[k0 + kk][4 * q + 3] = t.w;
+        }
+      }
     }
     __syncwarp();
   }
@@ -794,7 +883,8 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
   const int f = p.frac_bits;
   const int R = p.rounds;
   const int S = p.num_sets;
-  const SetTableShape sh{LOG2N, M::LOG2E, R, p.perms};
+  SetTableShape sh{LOG2N, M::LOG2E, R, p.perms};
+  sh.all_reg = batch_layout_all_reg(LAY);
   const int rw = sh.round_words();
 
   char* stage = reinterpret_cast<char*>(pbuf + perm_buf_words(LOG2N, KIND, LAY));
@@ -926,9 +1016,33 @@ __device__ __forceinline__ void batch_tasks(const BatchParams& p, long long t0, 
         const bool has_perm = p.perms && ((p.perm_mask >> r) & 1u);
         PermBytes<E, perm_own_id(LOG2N, LAY)> pb;
         if (has_perm) pb.load(stab + sh.perm_offset(r) + lane * sh.perm_seg());
-        if (INV && has_perm) perm_slot<LOG2N, KIND, LAY>(v, pb, pbuf, grp);  // undo slot r's gather
-        M::template round<0>(v, stab + r * rw, lane, half, f);
-        if (!INV && has_perm) perm_slot<LOG2N, KIND, LAY>(v, pb, pbuf, grp);  // gather of slot r
+        if constexpr (batch_layout_all_reg(LAY)) {
+          // passes 0 .. LOG2E-1 on the natural block, the rest on the
+          // transposed one; the slot's gather reads the transposed block
+          const int* rt = stab + r * rw;
+          constexpr int LE = M::LOG2E;
+          if (!INV) {
+            M::template tpasses<0, LE>(v, rt, lane, half, f);
+            tr_slot<LOG2N, KIND, LAY, true>(v, pbuf, grp, lane);
+            M::template tpasses<LE, LOG2N>(v, rt, lane, half, f);
+            if (has_perm)
+              perm_slot<LOG2N, KIND, LAY>(v, pb, pbuf, grp);  // gather of slot r, transposing back
+            else
+              tr_slot<LOG2N, KIND, LAY, false>(v, pbuf, grp, lane);
+          } else {
+            if (has_perm)
+              perm_slot<LOG2N, KIND, LAY>(v, pb, pbuf, grp);  // undo slot r's gather, transposing
+            else
+              tr_slot<LOG2N, KIND, LAY, true>(v, pbuf, grp, lane);
+            M::template tpasses<LE, LOG2N>(v, rt, lane, half, f);
+            tr_slot<LOG2N, KIND, LAY, false>(v, pbuf, grp, lane);
+            M::template tpasses<0, LE>(v, rt, lane, half, f);
+          }
+        } else {
+          if (INV && has_perm) perm_slot<LOG2N, KIND, LAY>(v, pb, pbuf, grp);  // undo slot r's gather
+          M::template round<0>(v, stab + r * rw, lane, half, f);
+          if (!INV && has_perm) perm_slot<LOG2N, KIND, LAY>(v, pb, pbuf, grp);  // gather of slot r
+        }
       }
     } else if (bucket == S + 1) {  // bad set index: zeros, status
 #pragma unroll

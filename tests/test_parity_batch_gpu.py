@@ -248,7 +248,7 @@ def test_batch_every_launch_tuning_bit_exact(gpu, orc, log2n, rounds):
             ran += 1
         gpu.hygt_batch_set_tuning(plan.handle, inv, 0, 0, -1, 0)
     assert ran >= 8
-    assert layouts == {4: {0, 1, 2, 3}, 6: {0, 1, 2, 3}, 8: {0, 2}}.get(log2n, {0})
+    assert layouts == {4: {0, 1, 2, 3}, 6: {0, 1, 2, 3}, 8: {0, 2, 4}}.get(log2n, {0})
     plan.close()
 
 
@@ -271,4 +271,37 @@ def test_tune_batch_sets_a_fitting_point(gpu, tmp_path, monkeypatch):
         assert ms > 0
     again = autotune.tune_batch(b, x, y, xr, reps=2)  # from the cache
     assert again == {k: tuple(v) for k, v in res.items()}
+    plan.close()
+
+
+@pytest.mark.parametrize("perm_kind", ["none", "between", "all"])
+@pytest.mark.parametrize("stage", [0, 1, 2])
+def test_batch_16x16_transposed_layout_bit_exact(gpu, orc, perm_kind, stage):
+    """Layout 4 (16x16: cross-lane passes done as register passes on the
+    block transposed through shared memory, the transpose back folded into
+    the permutation slot where one follows): the oracle's integers, forward
+    and inverse, with no permutation, with slots between rounds only (the
+    last round transposes back explicitly) and with a slot after every round."""
+    import torch
+    log2n, R, S, B = 8, 3, 16, 3001
+    q = inputs.angle_indices(S, R, log2n, seed=71)
+    perms = None if perm_kind == "none" else inputs.permutations(
+        S, R, 256, seed=72, between_rounds_only=(perm_kind == "between"))
+    x = inputs.laplacian_blocks(B, 256, 30.0, -32768, 32767, seed=73)
+    sets = inputs.set_indices(B, S, seed=74, skip_frac=0.1)
+    sets[5] = 999
+    ye, s1 = orc.fwd_int(x, q, log2n, R, perms, sets)
+    xe, s2 = orc.inv_int(ye, q, log2n, R, perms, sets)
+    assert s1 == s2 == orc.ERR_SET
+    plan = gpu.Plan(log2n, R, q, perms)
+    for inv in (0, 1):
+        assert gpu.hygt_batch_set_tuning(plan.handle, inv, 0, 0, stage, 4) == gpu.HYGT_OK
+    b = gpu.Batch(plan, B).build(_t(sets))
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    y = b.forward(_t(x), status=st)
+    xr = b.inverse(_t(ye), status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == gpu.HYGT_ERR_SET_INDEX
+    assert np.array_equal(y.cpu().numpy(), ye)
+    assert np.array_equal(xr.cpu().numpy(), xe)
     plan.close()
