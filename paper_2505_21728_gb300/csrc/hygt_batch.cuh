@@ -55,12 +55,14 @@ namespace hygt {
 // (16x16) is layout 0 with the cross-lane passes replaced by register passes
 // on the transposed block (a shared-memory transpose in the middle of each
 // round, the transpose back folded into the permutation slot where there is
-// one).  Their CTAs have 384 threads.
+// one; 8x8 and 4x4 with K = 8 in both directions).  Their CTAs have 384
+// threads.
 constexpr int kBatchLayouts = 5;
 __host__ __device__ constexpr bool batch_layout_ok(int log2n, int lay) {
   return lay == 0 || (lay == 1 && (log2n == 4 || log2n == 6)) ||
          (lay == 2 && (log2n == 4 || log2n == 6 || log2n == 8)) ||
-         (lay == 3 && (log2n == 4 || log2n == 6)) || (lay == 4 && log2n == 8);
+         (lay == 3 && (log2n == 4 || log2n == 6)) ||
+         (lay == 4 && (log2n == 4 || log2n == 6 || log2n == 8));
 }
 __host__ __device__ constexpr bool batch_layout_all_reg(int lay) { return lay == 4; }
 __host__ __device__ constexpr int batch_threads(int log2n, int kind, int lay = 0) {
@@ -104,7 +106,7 @@ __host__ __device__ constexpr int batch_k(int log2n, bool inv, int lay = 0) {
   if (lay == 1) return log2n == 4 ? (inv ? 2 : 4) : 1;
   if (lay == 2) return log2n == 4 ? (inv ? 4 : 8) : 2;
   if (lay == 3) return 8;
-  if (lay == 4) return 4;
+  if (lay == 4) return log2n == 8 ? 4 : 8;
   switch (log2n) {
     case 1: case 2: return 1;
     case 4: case 6: return inv ? 4 : 8;
@@ -488,9 +490,10 @@ __device__ __forceinline__ void perm_slot(
 // (lane l holds elements l E + i) and the transposed one (lane l holds
 // elements i E + l; E = L), through the blocks' regions of the permutation
 // buffer.  Word of element x = a E + 4 q + r (q: 16-byte chunk of lane a's
-// row): a E + 4 (q ^ ((a >> 1) & (E / 4 - 1))) + r -- a natural row is
-// written or read as E / 4 16-byte chunks and a transposed column as E
-// words, both without bank conflicts.
+// row): a E + 4 (q ^ ((a E / 32) & (E / 4 - 1))) + r -- rows a and a + 32 / E
+// start on the same bank, so the key a E / 32 gives them different chunk
+// orders: a natural row is written or read as E / 4 16-byte chunks and a
+// transposed column as E words, both without bank conflicts.
 template <int LOG2N, int KIND, int LAY, bool TO_T>
 __device__ __forceinline__ void tr_slot(
     int32_t (&v)[BatchMath<LOG2N, KIND == 1, LAY>::K][BatchMath<LOG2N, KIND == 1, LAY>::E],
@@ -511,13 +514,13 @@ __device__ __forceinline__ void tr_slot(
       if constexpr (TO_T) {  // natural rows out
 #pragma unroll
         for (int q = 0; q < E / 4; ++q)
-          *reinterpret_cast<int4*>(region + lane * E + 4 * (q ^ ((lane >> 1) & QM))) =
+          *reinterpret_cast<int4*>(region + lane * E + 4 * (q ^ ((lane * E / 32) & QM))) =
               make_int4(v[k0 + kk][4 * q], v[k0 + kk][4 * q + 1], v[k0 + kk][4 * q + 2],
                         v[k0 + kk][4 * q + 3]);
       } else {  // transposed columns out
 #pragma unroll
         for (int i = 0; i < E; ++i)
-          region[i * E + 4 * ((lane >> 2) ^ ((i >> 1) & QM)) + (lane & 3)] = v[k0 + kk][i];
+          region[i * E + 4 * ((lane >> 2) ^ ((i * E / 32) & QM)) + (lane & 3)] = v[k0 + kk][i];
       }
     }
     __syncwarp();
@@ -527,12 +530,12 @@ __device__ __forceinline__ void tr_slot(
       if constexpr (TO_T) {  // transposed columns in
 #pragma unroll
         for (int i = 0; i < E; ++i)
-          v[k0 + kk][i] = region[i * E + 4 * ((lane >> 2) ^ ((i >> 1) & QM)) + (lane & 3)];
+          v[k0 + kk][i] = region[i * E + 4 * ((lane >> 2) ^ ((i * E / 32) & QM)) + (lane & 3)];
       } else {  // natural rows in
 #pragma unroll
         for (int q = 0; q < E / 4; ++q) {
           const int4 t =
-              *reinterpret_cast<const int4*>(region + lane * E + 4 * (q ^ ((lane >> 1) & QM)));
+              *reinterpret_cast<const int4*>(region + lane * E + 4 * (q ^ ((lane * E / 32) & QM)));
           v[k0 + kk][4 * q] = t.x;
           v[k0 + kk][4 * q + 1] = t.y;
           v[k0 + kk][4 * q + 2] = t.z;

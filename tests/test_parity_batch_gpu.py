@@ -248,7 +248,7 @@ def test_batch_every_launch_tuning_bit_exact(gpu, orc, log2n, rounds):
             ran += 1
         gpu.hygt_batch_set_tuning(plan.handle, inv, 0, 0, -1, 0)
     assert ran >= 8
-    assert layouts == {4: {0, 1, 2, 3}, 6: {0, 1, 2, 3}, 8: {0, 2, 4}}.get(log2n, {0})
+    assert layouts == {4: {0, 1, 2, 3, 4}, 6: {0, 1, 2, 3, 4}, 8: {0, 2, 4}}.get(log2n, {0})
     plan.close()
 
 
@@ -276,18 +276,19 @@ def test_tune_batch_sets_a_fitting_point(gpu, tmp_path, monkeypatch):
 
 @pytest.mark.parametrize("perm_kind", ["none", "between", "all"])
 @pytest.mark.parametrize("stage", [0, 1, 2])
-def test_batch_16x16_transposed_layout_bit_exact(gpu, orc, perm_kind, stage):
-    """Layout 4 (16x16: cross-lane passes done as register passes on the
-    block transposed through shared memory, the transpose back folded into
-    the permutation slot where one follows): the oracle's integers, forward
-    and inverse, with no permutation, with slots between rounds only (the
-    last round transposes back explicitly) and with a slot after every round."""
+@pytest.mark.parametrize("log2n,R,S,B", [(4, 2, 105, 20011), (6, 2, 105, 9001), (8, 3, 16, 3001)])
+def test_batch_transposed_layout_bit_exact(gpu, orc, log2n, R, S, B, perm_kind, stage):
+    """Layout 4 (cross-lane passes done as register passes on the block
+    transposed through shared memory, the transpose back folded into the
+    permutation slot where one follows): the oracle's integers, forward and
+    inverse, with no permutation, with slots between rounds only (the last
+    round transposes back explicitly) and with a slot after every round."""
     import torch
-    log2n, R, S, B = 8, 3, 16, 3001
+    N = 1 << log2n
     q = inputs.angle_indices(S, R, log2n, seed=71)
     perms = None if perm_kind == "none" else inputs.permutations(
-        S, R, 256, seed=72, between_rounds_only=(perm_kind == "between"))
-    x = inputs.laplacian_blocks(B, 256, 30.0, -32768, 32767, seed=73)
+        S, R, N, seed=72, between_rounds_only=(perm_kind == "between"))
+    x = inputs.laplacian_blocks(B, N, 30.0, -32768, 32767, seed=73)
     sets = inputs.set_indices(B, S, seed=74, skip_frac=0.1)
     sets[5] = 999
     ye, s1 = orc.fwd_int(x, q, log2n, R, perms, sets)
