@@ -194,7 +194,8 @@ hygt_status hygt_inverse_batch(hygt_plan plan, const void *d_work, const int32_t
  *        the reverse (4x4: 4 values, 8 / 4 blocks); 3: layout 0 with 8
  *        blocks per lane group in the inverse as in the forward (4x4, 8x8);
  *        4: layout 0 with the cross-lane passes done as register passes on
- *        the block transposed through shared memory (4x4, 8x8, 16x16).  Layouts 1 to 4
+ *        the block transposed through shared memory (4x4, 8x8, 16x16); 5:
+ *        layout 4 with 2 blocks per lane group (16x16).  Layouts 1 to 5
  *        take stage -1 .. 2; other block sizes, and stage 3, return
  *        HYGT_ERR_UNSUPPORTED.  The secondary-transform calls use layout 0
  *        whatever is set.

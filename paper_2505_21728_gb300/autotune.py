@@ -180,7 +180,7 @@ def batch_candidates(max_warps, log2n, layout=0):
     return out
 
 
-BATCH_LAYOUTS = 5
+BATCH_LAYOUTS = 6
 
 
 def batch_layouts(plan, inverse):
@@ -189,7 +189,8 @@ def batch_layouts(plan, inverse):
     blocks per lane group, for 4x4, 8x8 and 16x16 blocks; 3, eight blocks per
     lane group in both directions, for 4x4 and 8x8 blocks; 4, the cross-lane
     passes replaced by register passes on the transposed block, for 4x4,
-    8x8 and 16x16 blocks)."""
+    8x8 and 16x16 blocks; 5, layout 4 with two blocks per lane group, for
+    16x16 blocks)."""
     out = [0]
     for lay in range(1, BATCH_LAYOUTS):
         if hygt.hygt_batch_set_tuning(plan.handle, inverse, 0, 0, -1, lay) == hygt.HYGT_OK:

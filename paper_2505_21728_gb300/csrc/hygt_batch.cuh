@@ -55,16 +55,17 @@ namespace hygt {
 // (16x16) is layout 0 with the cross-lane passes replaced by register passes
 // on the transposed block (a shared-memory transpose in the middle of each
 // round, the transpose back folded into the permutation slot where there is
-// one; 8x8 and 4x4 with K = 8 in both directions).  Their CTAs have 384
-// threads.
-constexpr int kBatchLayouts = 5;
+// one; 8x8 and 4x4 with K = 8 in both directions); layout 5 (16x16) is
+// layout 4 with K = 2 (half-size warp tasks: a short batch ends with a
+// smaller tail).  Their CTAs have 384 threads.
+constexpr int kBatchLayouts = 6;
 __host__ __device__ constexpr bool batch_layout_ok(int log2n, int lay) {
   return lay == 0 || (lay == 1 && (log2n == 4 || log2n == 6)) ||
          (lay == 2 && (log2n == 4 || log2n == 6 || log2n == 8)) ||
          (lay == 3 && (log2n == 4 || log2n == 6)) ||
-         (lay == 4 && (log2n == 4 || log2n == 6 || log2n == 8));
+         (lay == 4 && (log2n == 4 || log2n == 6 || log2n == 8)) || (lay == 5 && log2n == 8);
 }
-__host__ __device__ constexpr bool batch_layout_all_reg(int lay) { return lay == 4; }
+__host__ __device__ constexpr bool batch_layout_all_reg(int lay) { return lay == 4 || lay == 5; }
 __host__ __device__ constexpr int batch_threads(int log2n, int kind, int lay = 0) {
   return lay != 0 ? 384
          : log2n <= 3 ? 512
@@ -92,7 +93,7 @@ __host__ __device__ constexpr int batch_log2e(int log2n, int lay = 0) {
   if (lay == 1) return log2n;
   if (lay == 2) return log2n == 4 ? 2 : 5;
   if (lay == 3) return 3;
-  if (lay == 4) return log2n / 2;
+  if (lay == 4 || lay == 5) return log2n / 2;
   switch (log2n) {
     case 4: return 3;   // 4x4: 8 values per lane, 2 lanes
     case 5: return 4;
@@ -107,6 +108,7 @@ __host__ __device__ constexpr int batch_k(int log2n, bool inv, int lay = 0) {
   if (lay == 2) return log2n == 4 ? (inv ? 4 : 8) : 2;
   if (lay == 3) return 8;
   if (lay == 4) return log2n == 8 ? 4 : 8;
+  if (lay == 5) return 2;
   switch (log2n) {
     case 1: case 2: return 1;
     case 4: case 6: return inv ? 4 : 8;

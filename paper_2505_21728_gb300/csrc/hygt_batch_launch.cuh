@@ -93,6 +93,9 @@ inline cudaError_t launch_batch_sized(const BatchParams& p, cudaStream_t stream,
   if constexpr (batch_layout_ok(LOG2N, 4)) {
     if (tune.layout == 4) return launch_layout<LOG2N, KIND, 4>(p, stream, tune);
   }
+  if constexpr (batch_layout_ok(LOG2N, 5)) {
+    if (tune.layout == 5) return launch_layout<LOG2N, KIND, 5>(p, stream, tune);
+  }
   if (tune.layout != 0) return cudaErrorInvalidConfiguration;
   if constexpr (LOG2N >= 4) {
     const int stage = batch_stage_of<LOG2N, KIND>(p, tune);

@@ -248,7 +248,7 @@ def test_batch_every_launch_tuning_bit_exact(gpu, orc, log2n, rounds):
             ran += 1
         gpu.hygt_batch_set_tuning(plan.handle, inv, 0, 0, -1, 0)
     assert ran >= 8
-    assert layouts == {4: {0, 1, 2, 3, 4}, 6: {0, 1, 2, 3, 4}, 8: {0, 2, 4}}.get(log2n, {0})
+    assert layouts == {4: {0, 1, 2, 3, 4}, 6: {0, 1, 2, 3, 4}, 8: {0, 2, 4, 5}}.get(log2n, {0})
     plan.close()
 
 
@@ -295,14 +295,15 @@ def test_batch_transposed_layout_bit_exact(gpu, orc, log2n, R, S, B, perm_kind, 
     xe, s2 = orc.inv_int(ye, q, log2n, R, perms, sets)
     assert s1 == s2 == orc.ERR_SET
     plan = gpu.Plan(log2n, R, q, perms)
-    for inv in (0, 1):
-        assert gpu.hygt_batch_set_tuning(plan.handle, inv, 0, 0, stage, 4) == gpu.HYGT_OK
     b = gpu.Batch(plan, B).build(_t(sets))
-    st = torch.zeros(1, dtype=torch.int32, device="cuda")
-    y = b.forward(_t(x), status=st)
-    xr = b.inverse(_t(ye), status=st)
-    torch.cuda.synchronize()
-    assert int(st.item()) == gpu.HYGT_ERR_SET_INDEX
-    assert np.array_equal(y.cpu().numpy(), ye)
-    assert np.array_equal(xr.cpu().numpy(), xe)
+    for lay in ((4, 5) if log2n == 8 else (4,)):  # 5: the same with two blocks per lane group
+        for inv in (0, 1):
+            assert gpu.hygt_batch_set_tuning(plan.handle, inv, 0, 0, stage, lay) == gpu.HYGT_OK
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        y = b.forward(_t(x), status=st)
+        xr = b.inverse(_t(ye), status=st)
+        torch.cuda.synchronize()
+        assert int(st.item()) == gpu.HYGT_ERR_SET_INDEX
+        assert np.array_equal(y.cpu().numpy(), ye), lay
+        assert np.array_equal(xr.cpu().numpy(), xe), lay
     plan.close()
