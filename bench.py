@@ -760,7 +760,9 @@ def mixed_leg(dev, stream, steps=20, name="mixed_frame_2160p16"):
     mb = hygt.MixedBatch(classes, device=dev)
     mb.build()
     tunings = autotune.tune_mixed_classes(mb, reps=3, use_cache=False)
-    split = autotune.tune_split(mb, reps=3, use_cache=False)
+    modes = {}
+    split = autotune.tune_split(mb, reps=3, use_cache=False, report=modes)
+    variants = mb.variants()
     graph = mb.graph()
     for _ in range(3):
         graph.launch()
@@ -800,6 +802,12 @@ def mixed_leg(dev, stream, steps=20, name="mixed_frame_2160p16"):
             "mode": ("separate launches" if all(c == -1 for c in split) else
                      "concurrent" if all(c > 0 for c in split) else "sequential"),
             "cta_split": split,
+            "modes_ms_fwd_inv": modes,
+            "single_launch_variants": {str(e["plan"].N): {"forward": {"stage": v[0][0],
+                                                                      "layout": v[0][1]},
+                                                          "inverse": {"stage": v[1][0],
+                                                                      "layout": v[1][1]}}
+                                       for e, v in zip(mb.entries, variants)},
             "class_launch_tuning": {str(n): {d: {"warps_per_cta": v[0], "ctas_per_sm": v[1],
                                                  "stage": v[2], "layout": v[3],
                                                  "tuner_ms": v[4]}

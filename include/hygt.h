@@ -415,7 +415,16 @@ hygt_status hygt_pmpt_inverse_f32(hygt_pmpt pmpt, const float *d_y, float *d_x,
  *     classes in turn, each class spread over all CTAs.
  * A single launch sizes its shared memory for its largest class, which
  * leaves less L1 cache to the smaller ones; the autotuner of the Python
- * package times the three and keeps the fastest.
+ * package times the three and keeps the fastest.  A single launch runs
+ * each class in the staging and register layout of its plan's launch
+ * tuning for that direction (hygt_batch_set_tuning) where its kernel has
+ * that pair, from a short menu per block size:
+ *   4x4    layout 0 (stage 0), layout 2 (stage 0 or 1);
+ *   8x8    layout 0 (stage 1), layout 3 (stage 0 or 2);
+ *   16x16  layout 0 (stage 0), layout 5 (stage 0 or 1), layout 4 (stage 0);
+ * a tuning whose pair is not on the menu runs the first entry of its
+ * layout, else layout 0 (stage -1 reads as the layout's default).  Warps
+ * per CTA and CTAs per SM are the launch's own: one CTA per SM.
  *
  * Each class: plan = integer plan with N = 16, 64 or 256 (others return
  * HYGT_ERR_UNSUPPORTED; at most one class per block size, else
@@ -433,6 +442,11 @@ hygt_status hygt_pmpt_inverse_f32(hygt_pmpt pmpt, const float *d_y, float *d_x,
  *        fixed at capture).  hygt_graph_launch replays it on `stream`;
  *        hygt_graph_destroy frees it.
  *   hygt_mixed_ctas  CTAs of one mixed launch on the current device.
+ *   hygt_mixed_class_variant  the staging and register layout in which a
+ *        single mixed launch runs a class of `plan` in direction `inverse`
+ *        (0 forward, 1 inverse) under the plan's current tuning; stage and
+ *        layout may be NULL.  HYGT_ERR_ARG for a NULL plan,
+ *        HYGT_ERR_UNSUPPORTED for a floating-point plan or another N.
  */
 typedef struct hygt_mixed_class {
   hygt_plan plan;
@@ -449,6 +463,7 @@ typedef struct hygt_mixed_class {
 typedef struct hygt_graph_s *hygt_graph;
 
 int hygt_mixed_ctas(void);
+hygt_status hygt_mixed_class_variant(hygt_plan plan, int inverse, int *stage, int *layout);
 hygt_status hygt_forward_mixed(const hygt_mixed_class *classes, int nclasses,
                                hygt_stream stream, int *d_status);
 hygt_status hygt_inverse_mixed(const hygt_mixed_class *classes, int nclasses,

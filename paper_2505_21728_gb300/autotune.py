@@ -75,9 +75,11 @@ def _with_split(mb, split):
     return arr
 
 
-def tune_split(mb, reps=5, use_cache=True, verbose=False):
+def tune_split(mb, reps=5, use_cache=True, verbose=False, report=None):
     """Returns the tuned CTA split (list, one entry per class) and applies it
-    to ``mb``.  ``mb`` must have its schedules built."""
+    to ``mb``.  ``mb`` must have its schedules built.  A dict given as
+    ``report`` receives the timings of the modes (ms per forward + inverse)
+    when they were measured in this call."""
     key = _key(mb)
     path = _cache_path()
     cache = {}
@@ -145,6 +147,9 @@ def tune_split(mb, reps=5, use_cache=True, verbose=False):
     if verbose:
         print("autotune: sequential %.4f ms, separate %.4f ms, alone" % (seq_ms, sep_ms), alone,
               "best", split, "%.4f ms" % best)
+    if report is not None:
+        report.update({"sequential_ms": seq_ms, "separate_ms": sep_ms,
+                       "best_concurrent_ms": min(t for _, t in trials), "chosen_ms": best})
     mb.set_split(split)
     if use_cache:
         cache[key] = {"split": split, "ms": best, "sequential_ms": seq_ms, "separate_ms": sep_ms,

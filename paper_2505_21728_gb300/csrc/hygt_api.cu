@@ -633,6 +633,18 @@ hygt_status hygt_batch_get_tuning(hygt_plan plan, int inverse, int* warps_per_ct
 
 int hygt_mixed_ctas(void) { return hygt::mixed_grid_ctas(); }
 
+hygt_status hygt_mixed_class_variant(hygt_plan plan, int inverse, int* stage, int* layout) {
+  if (!plan) return HYGT_ERR_ARG;
+  if (plan->is_float || (plan->log2n != 4 && plan->log2n != 6 && plan->log2n != 8))
+    return HYGT_ERR_UNSUPPORTED;
+  const hygt::BatchTune& tune = plan->tune[inverse ? 1 : 0];
+  const hygt::MixedVariant mv = hygt::mixed_variant(
+      plan->log2n, hygt::mixed_variant_of(plan->log2n, tune.stage, tune.layout));
+  if (stage) *stage = mv.stage;
+  if (layout) *layout = mv.layout;
+  return HYGT_OK;
+}
+
 // Validates the classes of a mixed launch and fills the kernel parameters.
 // How a mixed batch is run (from the classes' `ctas`).
 enum MixedMode { kMixedSequential, kMixedConcurrent, kMixedSeparate };
@@ -668,7 +680,9 @@ static hygt_status mixed_params(const hygt_mixed_class* cls, int nclasses, bool 
     }
     mp->cls[slot] = make_batch_params(plan, k.d_work, in, out, k.nblocks, d_status);
     mp->present[slot] = k.nblocks > 0 ? 1 : 0;
-    if (tunes) tunes[slot] = plan->tune[inverse ? 1 : 0];
+    const hygt::BatchTune& tune = plan->tune[inverse ? 1 : 0];
+    mp->variant[slot] = hygt::mixed_variant_of(plan->log2n, tune.stage, tune.layout);
+    if (tunes) tunes[slot] = tune;
     slot_ctas[slot] = k.ctas;
     if (k.ctas <= 0) explicit_split = false;
     if (k.ctas != -1) separate = false;

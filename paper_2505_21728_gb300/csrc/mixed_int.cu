@@ -8,7 +8,10 @@
 // the next without waiting for the others); or concurrent -- CTAs
 // [begin[c], begin[c + 1]) work on class c only, so the classes proceed on
 // disjoint SMs.  Which, and the split, is a launch parameter (chosen by the
-// autotuner).
+// autotuner).  This kernel runs every class in layout 0 with its default
+// staging; when a class's tuning names another entry of its menu
+// (mixed_variant), the launch goes to the layout-aware kernel of
+// hygt_mixed_lay.cuh instead.
 #include <algorithm>
 
 #include "hygt_batch.cuh"
@@ -90,6 +93,9 @@ static cudaError_t launch_mixed_kind(MixedParams mp, cudaStream_t stream) {
 }
 
 cudaError_t launch_mixed(int kind, const MixedParams& mp, cudaStream_t stream) {
+  bool tuned = false;  // a class in another layout or staging than layout 0's default
+  for (int k = 0; k < kMaxMixedClasses; ++k) tuned |= mp.present[k] && mp.variant[k] != 0;
+  if (tuned) return kind == 0 ? launch_mixed_lay<0>(mp, stream) : launch_mixed_lay<1>(mp, stream);
   return kind == 0 ? launch_mixed_kind<0>(mp, stream) : launch_mixed_kind<1>(mp, stream);
 }
 

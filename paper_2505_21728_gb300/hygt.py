@@ -127,6 +127,8 @@ def _load() -> ctypes.CDLL:
     L.hygt_batch_get_tuning.restype = i32
     L.hygt_mixed_ctas.argtypes = []
     L.hygt_mixed_ctas.restype = i32
+    L.hygt_mixed_class_variant.argtypes = [P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    L.hygt_mixed_class_variant.restype = i32
     for name in ("hygt_forward_mixed", "hygt_inverse_mixed"):
         f = getattr(L, name)
         f.argtypes = [ctypes.POINTER(MixedClass), i32, P, P]
@@ -378,6 +380,15 @@ def hygt_batch_get_tuning(plan, inverse):
 
 def hygt_mixed_ctas():
     return int(_lib.hygt_mixed_ctas())
+
+
+def hygt_mixed_class_variant(plan, inverse):
+    """(stage, layout) in which a single mixed launch runs a class of
+    ``plan`` in one direction under the plan's current tuning."""
+    st, lay = ctypes.c_int(), ctypes.c_int()
+    _check(_lib.hygt_mixed_class_variant(plan, int(inverse), ctypes.byref(st), ctypes.byref(lay)),
+           "hygt_mixed_class_variant")
+    return st.value, lay.value
 
 
 def hygt_forward_mixed(classes, nclasses, stream, d_status):
@@ -866,6 +877,12 @@ class MixedBatch:
         or zeros, every CTA runs every class in turn."""
         for i in range(self.n):
             self.classes[i].ctas = 0 if ctas is None else int(ctas[i])
+
+    def variants(self):
+        """Per class, ((stage, layout) forward, (stage, layout) inverse):
+        what a single mixed launch runs it in under the plans' tuning."""
+        return [(hygt_mixed_class_variant(e["plan"].handle, 0),
+                 hygt_mixed_class_variant(e["plan"].handle, 1)) for e in self.entries]
 
     def build(self, stream=None):
         for i, e in enumerate(self.entries):

@@ -97,3 +97,4 @@ def test_calls_reject_null_plan(lib):
     from paper_2505_21728_gb300 import hygt
     assert hygt.hygt_forward(None, None, None, None, 1, None, None) == hygt.HYGT_ERR_ARG
     assert hygt.hygt_inverse(None, None, None, None, 0, None, None) == hygt.HYGT_ERR_ARG
+    assert lib.hygt_mixed_class_variant(None, 0, None, None) == hygt.HYGT_ERR_ARG

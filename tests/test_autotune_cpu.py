@@ -60,8 +60,13 @@ def _run(at, monkeypatch, alone, seq_factor, sep_factor):
     monkeypatch.setattr(at, "_key", lambda mb: "cpu-model")
     monkeypatch.setattr(at.hygt, "hygt_mixed_ctas", lambda: G)
     mb = _FakeMixed(hygt, list(alone))
-    split = at.tune_split(mb, reps=1, use_cache=False)
+    report = {}
+    split = at.tune_split(mb, reps=1, use_cache=False, report=report)
     assert mb.split == split
+    # the report holds the modes' times; the chosen one is the least of them
+    # up to the search's 0.5% acceptance margin
+    least = min(report["sequential_ms"], report["separate_ms"], report["best_concurrent_ms"])
+    assert least <= report["chosen_ms"] <= least / 0.995
     return split, _model(alone, seq_factor, sep_factor)
 
 

@@ -163,3 +163,80 @@ def test_mixed_class_order_empty_and_duplicate(gpu, orc):
     with pytest.raises(gpu.HygtError) as ei:
         mb3.forward()
     assert ei.value.code == gpu.HYGT_ERR_ARG
+
+
+# (stage, layout) pairs of the layout-aware single launch, per log2 N; entry
+# 0 is layout 0 with its default staging.
+MIXED_MENU = {4: [(0, 0), (0, 2), (1, 2)],
+              6: [(1, 0), (0, 3), (2, 3)],
+              8: [(0, 0), (0, 5), (1, 5), (0, 4)]}
+
+
+@pytest.mark.parametrize("entry", [0, 1, 2, 3])
+def test_mixed_layout_variants_bit_exact(gpu, orc, entry):
+    """Every menu entry of the single launch (each class tuned to the
+    entry, the last one where its menu is shorter), sequential, with an
+    uneven CTA split and graph-replayed: every block bit-exact."""
+    import torch
+    from paper_2505_21728_gb300 import workloads
+    w = workloads.get_mixed("mixed_frame_2160p16", scale_down=60)
+    mb, datas = make_mixed(gpu, w)
+    want = []
+    for e in mb.entries:
+        plan = e["plan"]
+        menu = MIXED_MENU[plan.log2n]
+        stage, layout = menu[min(entry, len(menu) - 1)]
+        for inv in (0, 1):
+            assert gpu.hygt_batch_set_tuning(plan.handle, inv, 0, 0, stage, layout) == 0
+        want.append(((stage, layout), (stage, layout)))
+    assert mb.variants() == want
+    mb.build()
+    for split in (None, [9, 4, 2]):
+        mb.set_split(split)
+        for e in mb.entries:
+            e["y"].zero_()
+            e["xr"].zero_()
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        mb.forward(status=st)
+        mb.inverse(status=st)
+        torch.cuda.synchronize()
+        assert int(st.item()) == 0
+        check_against_oracle(orc, mb, datas)
+    mb.set_split(None)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    g = mb.graph(status=st)
+    for e in mb.entries:
+        e["y"].zero_()
+        e["xr"].zero_()
+    g.launch()
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    check_against_oracle(orc, mb, datas)
+    g.close()
+
+
+def test_mixed_layout_variant_mapping(gpu):
+    """A tuning whose pair the single launch lacks runs the first entry of
+    its layout, else layout 0 with its default staging; stage -1 reads as
+    the layout's default."""
+    from paper_2505_21728_gb300 import inputs
+    cases = {4: [((-1, 0), (0, 0)), ((2, 0), (0, 0)), ((2, 2), (0, 2)), ((0, 1), (0, 0)),
+                 ((1, 3), (0, 0)), ((-1, 2), (0, 2))],
+             6: [((-1, 0), (1, 0)), ((3, 0), (1, 0)), ((1, 3), (0, 3)), ((2, 3), (2, 3)),
+                 ((0, 1), (1, 0)), ((-1, 3), (0, 3))],
+             8: [((-1, 0), (0, 0)), ((3, 0), (0, 0)), ((2, 5), (0, 5)), ((1, 4), (0, 4)),
+                 ((0, 2), (0, 0)), ((-1, 5), (0, 5))]}
+    for log2n, pairs in cases.items():
+        N = 1 << log2n
+        q = inputs.angle_indices(3, 2, log2n, seed=log2n)
+        plan = gpu.Plan(log2n, 2, q, inputs.permutations(3, 2, N, seed=log2n))
+        for (stage, layout), expect in pairs:
+            assert gpu.hygt_batch_set_tuning(plan.handle, 1, 0, 0, stage, layout) == 0
+            assert gpu.hygt_mixed_class_variant(plan.handle, 1) == expect, (log2n, stage, layout)
+        plan.close()
+    # N = 32 has no class in a mixed launch
+    q = inputs.angle_indices(1, 2, 5, seed=5)
+    plan = gpu.Plan(5, 2, q, inputs.permutations(1, 2, 32, seed=5))
+    with pytest.raises(RuntimeError):
+        gpu.hygt_mixed_class_variant(plan.handle, 0)
+    plan.close()
