@@ -184,7 +184,17 @@ hygt_status hygt_inverse_batch(hygt_plan plan, const void *d_work, const int32_t
  *        block; an input that is not 16-byte aligned falls back to 0 (N >= 16
  *        for 1, 2 and 3; smaller blocks return HYGT_ERR_UNSUPPORTED).  A bulk
  *        copy that has not landed within about a second makes the warp stop
- *        and write HYGT_ERR_CUDA to d_status;
+ *        and write HYGT_ERR_CUDA to d_status; 4: no staging, and the warp
+ *        tasks taken in an order interleaved across the sets (task t of
+ *        every set, then task t + 1, ..., the warps of all CTAs sweeping the
+ *        sets together) instead of one contiguous range per warp, so that
+ *        blocks sharing a 128-byte line, which belong to different sets, are
+ *        read while the line is still in L2; with ctas_per_sm 0 as many CTAs
+ *        as the registers allow, reading the set tables from global memory,
+ *        else each CTA holds the tables of all sets in shared memory when
+ *        they fit its share (4x4 blocks in layouts 0 and 2; other block sizes and
+ *        layouts return HYGT_ERR_UNSUPPORTED; the single mixed launch runs
+ *        such a class in its layout's first menu entry);
  *   layout         0: a block spread over a group of lanes (several values
  *        per lane, cross-lane passes by shuffles, several blocks per lane
  *        group sharing each multiplier load); 1: one lane per block (every
@@ -196,9 +206,10 @@ hygt_status hygt_inverse_batch(hygt_plan plan, const void *d_work, const int32_t
  *        4: layout 0 with the cross-lane passes done as register passes on
  *        the block transposed through shared memory (4x4, 8x8, 16x16); 5:
  *        layout 4 with 2 blocks per lane group (16x16).  Layouts 1 to 5
- *        take stage -1 .. 2; other block sizes, and stage 3, return
- *        HYGT_ERR_UNSUPPORTED.  The secondary-transform calls use layout 0
- *        whatever is set.
+ *        take stage -1 .. 2 (layout 2 also 4 for 4x4 blocks); other block
+ *        sizes, and stage 3, return HYGT_ERR_UNSUPPORTED.  The
+ *        secondary-transform calls use layout 0 whatever is set, and run
+ *        stage 4 as stage 0.
  * max_warps (get) is the largest warps_per_cta of the layout currently set.
  * Results do not depend on the tuning.  A choice whose shared memory does
  * not fit makes the next bucketed call return HYGT_ERR_UNSUPPORTED.  Not

@@ -170,13 +170,18 @@ def batch_candidates(max_warps, log2n, layout=0):
     times for one register layout: blocks per CTA through the warps of a
     CTA, CTAs per SM, and the staging depth (0: none, 1: the next task's
     blocks copied into shared memory ahead, 2: prefetched into L2 ahead, 3:
-    as 1 by one bulk copy per block; N >= 16 only; layout 1 without 3)."""
+    as 1 by one bulk copy per block; N >= 16 only; layouts other than 0
+    without 3; 4: no staging, tasks interleaved across the sets so that the
+    blocks of a 128-byte line are read together, for 4x4 blocks in layouts 0
+    and 2, one CTA per SM when the set tables fill its shared memory)."""
     warps = sorted({w for w in (max_warps, (3 * max_warps) // 4, max_warps // 2,
                                 max_warps // 3, 4) if w >= 2})
     if log2n < 4:
         stages = (-1,)
     else:
         stages = (0, 1, 2, 3) if layout == 0 else (0, 1, 2)
+    if log2n == 4 and layout in (0, 2):
+        stages += (4,)
     out = []
     for w in warps:
         for c in (0, 1, 2):

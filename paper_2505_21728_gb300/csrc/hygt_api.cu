@@ -21,6 +21,7 @@
 #include "hygt_secondary.cuh"
 #include "hygt_grad.cuh"
 #include "hygt_mixed.cuh"
+#include "hygt_batch_il.cuh"
 #include "hygt_launch.cuh"
 
 struct hygt_plan_s {
@@ -536,6 +537,15 @@ static hygt::BatchParams make_batch_params(hygt_plan plan, const void* d_work, c
   return p;
 }
 
+// A bucketed launch in the plan's tuning: stage 4 is the set-interleaved
+// order, the others the batch kernels' own.
+static cudaError_t launch_batch_tuned(bool inverse, int log2n, const hygt::BatchParams& p,
+                                      cudaStream_t stream, const hygt::BatchTune& tune) {
+  if (tune.stage == 4) return hygt::launch_batch_il(inverse ? 1 : 0, log2n, p, stream, tune);
+  return inverse ? hygt::launch_batch_inv(log2n, p, stream, tune)
+                 : hygt::launch_batch_fwd(log2n, p, stream, tune);
+}
+
 static hygt_status batch_call(hygt_plan plan, const void* d_work, const void* in, void* out,
                               int64_t nblocks, hygt_stream stream, int* d_status, bool inverse) {
   hygt_status s = check_io(plan, in, out, nblocks);
@@ -543,9 +553,8 @@ static hygt_status batch_call(hygt_plan plan, const void* d_work, const void* in
   if (plan->is_float) return HYGT_ERR_UNSUPPORTED;
   if (!d_work || !aligned16(d_work) || nblocks > kBatchMaxBlocks) return HYGT_ERR_ARG;
   const hygt::BatchParams p = make_batch_params(plan, d_work, in, out, nblocks, d_status);
-  cudaError_t e =
-      inverse ? hygt::launch_batch_inv(plan->log2n, p, (cudaStream_t)stream, plan->tune[1])
-              : hygt::launch_batch_fwd(plan->log2n, p, (cudaStream_t)stream, plan->tune[0]);
+  cudaError_t e = launch_batch_tuned(inverse, plan->log2n, p, (cudaStream_t)stream,
+                                     plan->tune[inverse ? 1 : 0]);
   if (e == cudaErrorInvalidConfiguration) return HYGT_ERR_UNSUPPORTED;
   return to_status(e);
 }
@@ -605,12 +614,13 @@ hygt_status hygt_inverse_batch_f32(hygt_plan plan, const void* d_work, const flo
 hygt_status hygt_batch_set_tuning(hygt_plan plan, int inverse, int warps_per_cta,
                                   int ctas_per_sm, int stage, int layout) {
   if (!plan || (inverse != 0 && inverse != 1) || warps_per_cta < 0 || ctas_per_sm < 0 ||
-      ctas_per_sm > 8 || stage < -1 || stage > 3 || layout < 0 || layout >= hygt::kBatchLayouts)
+      ctas_per_sm > 8 || stage < -1 || stage > 4 || layout < 0 || layout >= hygt::kBatchLayouts)
     return HYGT_ERR_ARG;
   const int max_warps = hygt::batch_threads(plan->log2n, inverse, layout) / 32;
   if (warps_per_cta > max_warps) return HYGT_ERR_ARG;
   if (stage >= 0 && plan->log2n < 4) return HYGT_ERR_UNSUPPORTED;
   if (layout != 0 && (!plan->d_ktabs[layout] || stage == 3)) return HYGT_ERR_UNSUPPORTED;
+  if (stage == 4 && !hygt::batch_il_ok(plan->log2n, layout)) return HYGT_ERR_UNSUPPORTED;
   hygt::BatchTune& t = plan->tune[inverse];
   t.warps = warps_per_cta;
   t.ctas_per_sm = ctas_per_sm;
@@ -713,8 +723,7 @@ static cudaError_t mixed_launch(const hygt::MixedParams& mp, MixedMode mode, boo
   for (int k = 0; k < hygt::kMaxMixedClasses; ++k) {
     if (!mp.present[k]) continue;
     const int log2n = hygt::mixed_slot_log2n(k);
-    const cudaError_t e = inverse ? hygt::launch_batch_inv(log2n, mp.cls[k], stream, tunes[k])
-                                  : hygt::launch_batch_fwd(log2n, mp.cls[k], stream, tunes[k]);
+    const cudaError_t e = launch_batch_tuned(inverse, log2n, mp.cls[k], stream, tunes[k]);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

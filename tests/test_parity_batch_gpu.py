@@ -307,3 +307,51 @@ def test_batch_transposed_layout_bit_exact(gpu, orc, log2n, R, S, B, perm_kind, 
         assert np.array_equal(y.cpu().numpy(), ye), lay
         assert np.array_equal(xr.cpu().numpy(), xe), lay
     plan.close()
+
+
+@pytest.mark.parametrize("perm_kind", ["none", "all"])
+@pytest.mark.parametrize("layout", [0, 2])
+def test_batch_interleaved_order_bit_exact(gpu, orc, perm_kind, layout):
+    """Stage 4 (4x4 blocks: tasks taken one set after the other, all warps
+    sweeping the sets together): the oracle's integers, forward and inverse,
+    with the set tables in shared memory (one CTA per SM) and read from
+    global memory (two CTAs per SM: the tables no longer fit), a bad set
+    index, a batch whose blocks use only three sets, and a batch smaller
+    than one task."""
+    import torch
+    log2n, R, S, N = 4, 2, 105, 16
+    q = inputs.angle_indices(S, R, log2n, seed=81)
+    perms = None if perm_kind == "none" else inputs.permutations(S, R, N, seed=82)
+    plan = gpu.Plan(log2n, R, q, perms)
+    cases = []
+    x = inputs.laplacian_blocks(40009, N, 30.0, -32768, 32767, seed=83)
+    sets = inputs.set_indices(40009, S, seed=84, skip_frac=0.1)
+    sets[11] = 700
+    cases.append((x, sets, orc.ERR_SET))
+    few = inputs.set_indices(9000, 3, seed=85, skip_frac=0.05)  # sets 0..2 and skips
+    cases.append((inputs.laplacian_blocks(9000, N, 30.0, -32768, 32767, seed=86), few, 0))
+    cases.append((inputs.laplacian_blocks(5, N, 30.0, -32768, 32767, seed=87),
+                  inputs.set_indices(5, S, seed=88), 0))
+    for x, sets, want in cases:
+        B = x.shape[0]
+        ye, s1 = orc.fwd_int(x, q, log2n, R, perms, sets)
+        xe, s2 = orc.inv_int(ye, q, log2n, R, perms, sets)
+        assert s1 == s2 == want
+        b = gpu.Batch(plan, B).build(_t(sets))
+        for ctas in (1, 2):
+            for w in (0, 4):
+                for inv in (0, 1):
+                    assert gpu.hygt_batch_set_tuning(plan.handle, inv, w, ctas, 4, layout) == 0
+                st = torch.zeros(1, dtype=torch.int32, device="cuda")
+                y = b.forward(_t(x), status=st)
+                xr = b.inverse(_t(ye), status=st)
+                torch.cuda.synchronize()
+                assert int(st.item()) == (gpu.HYGT_ERR_SET_INDEX if want else 0)
+                assert np.array_equal(y.cpu().numpy(), ye), (B, ctas, w)
+                assert np.array_equal(xr.cpu().numpy(), xe), (B, ctas, w)
+    # other block sizes and layouts have no interleaved order
+    assert gpu.hygt_batch_set_tuning(plan.handle, 0, 0, 0, 4, 1) == gpu.HYGT_ERR_UNSUPPORTED
+    plan.close()
+    p6 = gpu.Plan(6, 2, inputs.angle_indices(3, 2, 6, seed=1))
+    assert gpu.hygt_batch_set_tuning(p6.handle, 0, 0, 0, 4, 0) == gpu.HYGT_ERR_UNSUPPORTED
+    p6.close()
