@@ -147,3 +147,18 @@ def test_batch_tuner_picks_the_modelled_best(at, monkeypatch):
     assert res["forward"][:4] == (9, 1, 1, 0)
     assert res["inverse"][:4] == (9, 1, 0, 1)   # layout 1, first of the equal stages
     assert state[0] == (9, 1, 1, 0) and state[1] == (9, 1, 0, 1)
+
+
+def test_batch_candidates_offer_the_interleaved_order_for_4x4_only(at):
+    """Stage 4 (tasks interleaved across the sets) is a candidate for 4x4
+    blocks in layouts 0 and 2, and for nothing else; the bulk stage (3) is
+    offered in layout 0 only."""
+    for log2n in range(2, 9):
+        for lay in range(6):
+            stages = {c[2] for c in at.batch_candidates(12, log2n, lay)}
+            assert all(c[3] == lay for c in at.batch_candidates(12, log2n, lay))
+            assert (4 in stages) == (log2n == 4 and lay in (0, 2)), (log2n, lay)
+            if log2n >= 4:
+                assert (3 in stages) == (lay == 0)
+            else:
+                assert stages == {-1}
