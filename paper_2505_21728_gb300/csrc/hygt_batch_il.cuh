@@ -10,10 +10,11 @@
 // warps advance through the sets together instead: round r of the
 // round-robin order holds task r of every set's bucket and an even share of
 // the skip and bad-set buckets' tasks, and warp w takes entries w, w + W,
-// w + 2W, ... of the rounds laid end to end.  Within a bucket the blocks follow the scatter's tile order,
-// which is nearly the same for every bucket, so task t of every set covers
-// about the same region of memory: a line's blocks are read within one
-// sweep of the warps, while the line is still in L2.  A CTA keeps the
+// w + 2W, ... of the rounds laid end to end.  Within a bucket the blocks
+// follow the scatter's tile order, which is nearly the same for every
+// bucket, so task t of every set covers about the same region of memory: a
+// line's blocks are read within one sweep of the warps, while the line is
+// still in L2.  A CTA keeps the
 // tables of all sets in shared memory (N = 16: 1,152 bytes a set in layout
 // 2) or reads them from global memory, by the launch tuning.  The
 // arithmetic is batch_tasks', one task per call, without staging.
