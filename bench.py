@@ -63,7 +63,8 @@ def parse_args():
                          "then launch no tuning kernels)")
     ap.add_argument("--fwd-tuning", default=None,
                     help="--case batch/stress: launch tuning of the forward, "
-                         "'warps,ctas_per_sm,stage[,layout]' (hygt_batch_set_tuning)")
+                         "'warps,ctas_per_sm,stage[,layout[,tail_64ths]]' "
+                         "(hygt_batch_set_tuning, hygt_batch_set_tail)")
     ap.add_argument("--inv-tuning", default=None, help="the same for the inverse")
     return ap.parse_args()
 
@@ -221,6 +222,8 @@ def ncu_traffic(kernel: str, workload: str, tuning=None):
     if tuning is not None:
         lay = int(tuning[3]) if len(tuning) > 4 else 0
         want = "%d,%d" % (int(tuning[2]), lay)
+        if len(tuning) > 5 and int(tuning[5]) > 0:  # the kernel with a dynamic tail
+            want += ",tail%d" % int(tuning[5])
     for p in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
         with open(p) as f:
             for line in f:
@@ -407,7 +410,8 @@ def run_ours(args, rank, world, local):
                    "sets": w.num_sets, "parallelism": "dp%d" % world,
                    "step": "bucket blocks by set, integer forward, integer inverse",
                    "launch_tuning": {d: {"warps_per_cta": v[0], "ctas_per_sm": v[1],
-                                         "stage": v[2], "layout": v[3], "tuner_ms": v[4]}
+                                         "stage": v[2], "layout": v[3], "tuner_ms": v[4],
+                                         "tail_64ths": v[5] if len(v) > 5 else 0}
                                      for d, v in tuning.items()},
                    "l2": "inputs larger than L2 (%.0f MB read + %.0f MB written per step "
                          "vs %d MB L2), no flush" % (count * 6 * N / 1e6, count * 6 * N / 1e6,
@@ -810,7 +814,8 @@ def mixed_leg(dev, stream, steps=20, name="mixed_frame_2160p16"):
                                        for e, v in zip(mb.entries, variants)},
             "class_launch_tuning": {str(n): {d: {"warps_per_cta": v[0], "ctas_per_sm": v[1],
                                                  "stage": v[2], "layout": v[3],
-                                                 "tuner_ms": v[4]}
+                                                 "tuner_ms": v[4],
+                                                 "tail_64ths": v[5] if len(v) > 5 else 0}
                                              for d, v in t.items()}
                                     for n, t in tunings.items()},
             "gpu_launches_per_step": 3 * 3 + (6 if all(c == -1 for c in split) else 2),
@@ -1050,8 +1055,11 @@ def case_batch(args, name=None):
     for inv, t in ((0, args.fwd_tuning), (1, args.inv_tuning)):
         if t:
             vals = [int(v) for v in t.split(",")]
-            hygt._check(hygt.hygt_batch_set_tuning(plan.handle, inv, *vals),
+            hygt._check(hygt.hygt_batch_set_tuning(plan.handle, inv, *vals[:4]),
                         "hygt_batch_set_tuning")
+            if len(vals) > 4:
+                hygt._check(hygt.hygt_batch_set_tail(plan.handle, inv, vals[4]),
+                            "hygt_batch_set_tail")
     b = hygt.Batch(plan, x.shape[0])
     y = torch.empty((x.shape[0], w.N), dtype=torch.int32, device="cuda")
     xr = torch.empty_like(x)

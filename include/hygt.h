@@ -142,10 +142,13 @@ hygt_status hygt_inverse_f32(hygt_plan plan, const float *d_y, float *d_x,
  * the blocks of each warp share their multipliers, then transformed.
  *
  *   hygt_batch_workspace_bytes  device bytes of the schedule for nblocks
- *                               blocks (0 if nblocks is out of range).
+ *                               blocks, with the 16 bytes of counters of
+ *                               the dynamic tail at its end (0 if nblocks
+ *                               is out of range).
  *   hygt_batch_build            buckets d_set (uint16 [nblocks]; NULL = set 0)
  *                               into the caller's workspace d_work (16-byte
- *                               aligned, >= the bytes above), async on stream.
+ *                               aligned, >= the bytes above) and zeroes the
+ *                               tail's counters, async on stream.
  *   hygt_forward_batch /        transform with a schedule built for the same
  *   hygt_inverse_batch          plan set count and nblocks (a schedule built
  *                               for other sizes makes the call write
@@ -219,6 +222,25 @@ hygt_status hygt_batch_set_tuning(hygt_plan plan, int inverse, int warps_per_cta
                                   int ctas_per_sm, int stage, int layout);
 hygt_status hygt_batch_get_tuning(hygt_plan plan, int inverse, int *warps_per_cta,
                                   int *ctas_per_sm, int *stage, int *layout, int *max_warps);
+
+/*
+ * Dynamic tail of the bucketed kernels (no counterpart in the paper; per plan
+ * and direction, like the launch tuning).  The kernels give each warp one
+ * contiguous range of the set-sorted order, fixed at launch; with a tail of
+ * t / 64 (t = 1 .. 32; 0, the default, turns it off) the first (64 - t) / 64
+ * of the order is split that way and the rest is handed out one warp task
+ * at a time, through an atomic counter in the schedule workspace, to the
+ * warps that finish their range, so that SMs done early take the work of
+ * late ones.  The tail's tasks read their set tables from global memory and
+ * run without a stage.  For 8x8 blocks in layouts 0 and 3 and 16x16 blocks
+ * in layouts 0, 4 and 5, any stage but 4 (others return
+ * HYGT_ERR_UNSUPPORTED, as does hygt_batch_set_tuning to such a point while
+ * a tail is set).  Results do not depend on it.  The single mixed launch and
+ * the secondary-transform calls do not use it.  One workspace serves one
+ * call at a time: the last warp of a launch puts the counter back to zero.
+ */
+hygt_status hygt_batch_set_tail(hygt_plan plan, int inverse, int tail_64ths);
+hygt_status hygt_batch_get_tail(hygt_plan plan, int inverse, int *tail_64ths);
 
 /*
  * FP32 HyGT through the same set-bucketed schedule (the FP32 forward and

@@ -240,19 +240,27 @@ def _time_dir(fn, reps):
     return statistics.median(times)
 
 
+# Dynamic tails the batch tuner tries on its best point, in 64ths of the
+# tasks (hygt_batch_set_tail); one is kept only if it is 1% faster.
+BATCH_TAILS = (4, 8, 16)
+
+
 def tune_batch(batch, x, y, xr, reps=5, use_cache=True, verbose=False, time_fn=None):
     """Times every launch tuning of ``all_batch_candidates`` for the
     bucketed forward and inverse of ``batch`` (a hygt.Batch with its schedule
-    built) and sets the fastest on the plan (hygt_batch_set_tuning).  Returns
-    {"forward": (warps, ctas_per_sm, stage, layout, ms), "inverse": (...)}.
-    Results are cached by GPU name, block size, rounds, sets and block count.
-    ``time_fn(direction, tuning)`` replaces the GPU timing (tests)."""
+    built), sets the fastest on the plan (hygt_batch_set_tuning), then tries
+    the dynamic tails of BATCH_TAILS on it (hygt_batch_set_tail).  Returns
+    {"forward": (warps, ctas_per_sm, stage, layout, ms, tail_64ths),
+    "inverse": (...)}.  Results are cached by GPU name, block size, rounds,
+    sets and block count.  ``time_fn(direction, point)`` replaces the GPU
+    timing (tests); ``point`` is a tuning, with the tail as a fifth entry
+    when one is timed."""
     plan = batch.plan
     key = None
     cache, path = {}, _cache_path()
     if use_cache:
         import torch
-        key = "batch2|%s|N%d_R%d_S%d_B%d" % (torch.cuda.get_device_name(), plan.N, plan.rounds,
+        key = "batch3|%s|N%d_R%d_S%d_B%d" % (torch.cuda.get_device_name(), plan.N, plan.rounds,
                                               plan.num_sets, batch.nblocks)
         if os.path.exists(path):
             try:
@@ -263,24 +271,32 @@ def tune_batch(batch, x, y, xr, reps=5, use_cache=True, verbose=False, time_fn=N
         if key in cache:
             res = {d: tuple(v) for d, v in cache[key].items()}
             for inv, d in ((0, "forward"), (1, "inverse")):
+                hygt._check(hygt.hygt_batch_set_tail(plan.handle, inv, 0), "hygt_batch_set_tail")
                 hygt._check(hygt.hygt_batch_set_tuning(plan.handle, inv, *res[d][:4]),
                             "hygt_batch_set_tuning")
+                hygt._check(hygt.hygt_batch_set_tail(plan.handle, inv, res[d][5]),
+                            "hygt_batch_set_tail")
             return res
     res = {}
     for inv, d in ((0, "forward"), (1, "inverse")):
+        fn = (lambda: batch.forward(x, out=y)) if inv == 0 else (lambda: batch.inverse(y, out=xr))
+
+        def timed(point):
+            if time_fn is not None:
+                return time_fn(d, point)
+            try:
+                return _time_dir(fn, reps)
+            except hygt.HygtError:
+                return None  # this point does not fit (shared memory)
+
+        hygt._check(hygt.hygt_batch_set_tail(plan.handle, inv, 0), "hygt_batch_set_tail")
         best = None
         for cand in all_batch_candidates(plan, inv):
             if hygt.hygt_batch_set_tuning(plan.handle, inv, *cand) != hygt.HYGT_OK:
                 continue
-            if time_fn is not None:
-                ms = time_fn(d, cand)
-            else:
-                fn = (lambda: batch.forward(x, out=y)) if inv == 0 else \
-                    (lambda: batch.inverse(y, out=xr))
-                try:
-                    ms = _time_dir(fn, reps)
-                except hygt.HygtError:
-                    continue  # this point does not fit (shared memory)
+            ms = timed(tuple(cand))
+            if ms is None:
+                continue
             if verbose:
                 print("tune %s %s: %.4f ms" % (d, cand, ms))
             if best is None or ms < best[4]:
@@ -289,7 +305,17 @@ def tune_batch(batch, x, y, xr, reps=5, use_cache=True, verbose=False, time_fn=N
             best = (0, 0, -1, 0, float("nan"))
         hygt._check(hygt.hygt_batch_set_tuning(plan.handle, inv, *best[:4]),
                     "hygt_batch_set_tuning")
-        res[d] = best
+        tail, tail_ms = 0, best[4]
+        for t in BATCH_TAILS:
+            if hygt.hygt_batch_set_tail(plan.handle, inv, t) != hygt.HYGT_OK:
+                break  # no dynamic tail for this point
+            ms = timed(tuple(best[:4]) + (t,))
+            if verbose and ms is not None:
+                print("tune %s %s tail %d/64: %.4f ms" % (d, best[:4], t, ms))
+            if ms is not None and ms < tail_ms and ms < best[4] * 0.99:
+                tail, tail_ms = t, ms
+        hygt._check(hygt.hygt_batch_set_tail(plan.handle, inv, tail), "hygt_batch_set_tail")
+        res[d] = tuple(best[:4]) + (tail_ms, tail)
     if use_cache and key is not None:
         cache[key] = {d: list(v) for d, v in res.items()}
         try:

@@ -22,6 +22,7 @@
 #include "hygt_grad.cuh"
 #include "hygt_mixed.cuh"
 #include "hygt_batch_il.cuh"
+#include "hygt_batch_dyn.cuh"
 #include "hygt_launch.cuh"
 
 struct hygt_plan_s {
@@ -41,6 +42,7 @@ struct hygt_plan_s {
   int* d_ktabs[hygt::kBatchLayouts] = {};  // the same per register layout ([0] = d_ktab)
   int ktabs_words[hygt::kBatchLayouts] = {};
   hygt::BatchTune tune[2];    // batch path launch tuning: forward, inverse
+  int tail[2] = {0, 0};       // dynamic tail of the batch path, 64ths of the tasks
 };
 
 namespace hygt {
@@ -493,7 +495,24 @@ hygt_status hygt_inverse_f32(hygt_plan plan, const float* d_y, float* d_x, const
 
 size_t hygt_batch_workspace_bytes(hygt_plan plan, int64_t nblocks) {
   if (!plan || nblocks < 0 || nblocks > kBatchMaxBlocks) return 0;
-  return hygt::batch_layout(plan->num_sets, nblocks, hygt::batch_group(plan->log2n)).total;
+  return hygt::batch_layout(plan->num_sets, nblocks, hygt::batch_group(plan->log2n)).total +
+         hygt::kDynCounterBytes;
+}
+
+// The schedule of a batch, then the dynamic tail's counters zeroed.
+static cudaError_t build_schedule(const uint16_t* d_set, int64_t nblocks, int num_sets,
+                                  int group, void* d_work, cudaStream_t stream) {
+  cudaError_t e = hygt::batch_build(d_set, nblocks, num_sets, group, d_work, stream);
+  if (e != cudaSuccess) return e;
+  const size_t total = hygt::batch_layout(num_sets, nblocks, group).total;
+  return cudaMemsetAsync(static_cast<char*>(d_work) + total, 0, hygt::kDynCounterBytes, stream);
+}
+
+// The dynamic tail's counters of a schedule workspace.
+static void* tail_counters(hygt_plan plan, const void* d_work, int64_t nblocks) {
+  const size_t total =
+      hygt::batch_layout(plan->num_sets, nblocks, hygt::batch_group(plan->log2n)).total;
+  return const_cast<char*>(static_cast<const char*>(d_work)) + total;
 }
 
 hygt_status hygt_batch_build(hygt_plan plan, const uint16_t* d_set, int64_t nblocks, void* d_work,
@@ -501,12 +520,12 @@ hygt_status hygt_batch_build(hygt_plan plan, const uint16_t* d_set, int64_t nblo
   if (!plan || nblocks < 0 || nblocks > kBatchMaxBlocks || !d_work || !aligned16(d_work))
     return HYGT_ERR_ARG;
   const int group = hygt::batch_group(plan->log2n);
-  if (work_bytes < hygt::batch_layout(plan->num_sets, nblocks, group).total) return HYGT_ERR_ARG;
+  if (work_bytes < hygt_batch_workspace_bytes(plan, nblocks)) return HYGT_ERR_ARG;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return HYGT_ERR_CUDA;
   if (dev != plan->device) return HYGT_ERR_ARG;
   return to_status(
-      hygt::batch_build(d_set, nblocks, plan->num_sets, group, d_work, (cudaStream_t)stream));
+      build_schedule(d_set, nblocks, plan->num_sets, group, d_work, (cudaStream_t)stream));
 }
 
 static hygt::BatchParams make_batch_params(hygt_plan plan, const void* d_work, const void* in,
@@ -538,10 +557,14 @@ static hygt::BatchParams make_batch_params(hygt_plan plan, const void* d_work, c
 }
 
 // A bucketed launch in the plan's tuning: stage 4 is the set-interleaved
-// order, the others the batch kernels' own.
+// order, a nonzero tail the kernels with a dynamic tail, the others the
+// batch kernels' own.
 static cudaError_t launch_batch_tuned(bool inverse, int log2n, const hygt::BatchParams& p,
-                                      cudaStream_t stream, const hygt::BatchTune& tune) {
+                                      cudaStream_t stream, const hygt::BatchTune& tune,
+                                      int tail = 0, void* counters = nullptr) {
   if (tune.stage == 4) return hygt::launch_batch_il(inverse ? 1 : 0, log2n, p, stream, tune);
+  if (tail > 0)
+    return hygt::launch_batch_dyn(inverse ? 1 : 0, log2n, p, counters, tail, stream, tune);
   return inverse ? hygt::launch_batch_inv(log2n, p, stream, tune)
                  : hygt::launch_batch_fwd(log2n, p, stream, tune);
 }
@@ -554,7 +577,8 @@ static hygt_status batch_call(hygt_plan plan, const void* d_work, const void* in
   if (!d_work || !aligned16(d_work) || nblocks > kBatchMaxBlocks) return HYGT_ERR_ARG;
   const hygt::BatchParams p = make_batch_params(plan, d_work, in, out, nblocks, d_status);
   cudaError_t e = launch_batch_tuned(inverse, plan->log2n, p, (cudaStream_t)stream,
-                                     plan->tune[inverse ? 1 : 0]);
+                                     plan->tune[inverse ? 1 : 0], plan->tail[inverse ? 1 : 0],
+                                     tail_counters(plan, d_work, nblocks));
   if (e == cudaErrorInvalidConfiguration) return HYGT_ERR_UNSUPPORTED;
   return to_status(e);
 }
@@ -621,6 +645,8 @@ hygt_status hygt_batch_set_tuning(hygt_plan plan, int inverse, int warps_per_cta
   if (stage >= 0 && plan->log2n < 4) return HYGT_ERR_UNSUPPORTED;
   if (layout != 0 && (!plan->d_ktabs[layout] || stage == 3)) return HYGT_ERR_UNSUPPORTED;
   if (stage == 4 && !hygt::batch_il_ok(plan->log2n, layout)) return HYGT_ERR_UNSUPPORTED;
+  if (plan->tail[inverse] > 0 && !hygt::batch_dyn_ok(plan->log2n, layout, stage))
+    return HYGT_ERR_UNSUPPORTED;  // a dynamic tail is set: clear it first
   hygt::BatchTune& t = plan->tune[inverse];
   t.warps = warps_per_cta;
   t.ctas_per_sm = ctas_per_sm;
@@ -638,6 +664,22 @@ hygt_status hygt_batch_get_tuning(hygt_plan plan, int inverse, int* warps_per_ct
   if (stage) *stage = t.stage;
   if (layout) *layout = t.layout;
   if (max_warps) *max_warps = hygt::batch_threads(plan->log2n, inverse, t.layout) / 32;
+  return HYGT_OK;
+}
+
+hygt_status hygt_batch_set_tail(hygt_plan plan, int inverse, int tail_64ths) {
+  if (!plan || (inverse != 0 && inverse != 1) || tail_64ths < 0 || tail_64ths > 32)
+    return HYGT_ERR_ARG;
+  const hygt::BatchTune& t = plan->tune[inverse];
+  if (tail_64ths > 0 && !hygt::batch_dyn_ok(plan->log2n, t.layout, t.stage))
+    return HYGT_ERR_UNSUPPORTED;
+  plan->tail[inverse] = tail_64ths;
+  return HYGT_OK;
+}
+
+hygt_status hygt_batch_get_tail(hygt_plan plan, int inverse, int* tail_64ths) {
+  if (!plan || (inverse != 0 && inverse != 1) || !tail_64ths) return HYGT_ERR_ARG;
+  *tail_64ths = plan->tail[inverse];
   return HYGT_OK;
 }
 
@@ -659,9 +701,17 @@ hygt_status hygt_mixed_class_variant(hygt_plan plan, int inverse, int* stage, in
 // How a mixed batch is run (from the classes' `ctas`).
 enum MixedMode { kMixedSequential, kMixedConcurrent, kMixedSeparate };
 
+// How one class runs in separate launches: its plan's tuning and dynamic
+// tail for the direction, and the tail's counters in its workspace.
+struct ClassLaunch {
+  hygt::BatchTune tune;
+  int tail = 0;
+  void* counters = nullptr;
+};
+
 static hygt_status mixed_params(const hygt_mixed_class* cls, int nclasses, bool inverse,
                                 int* d_status, hygt::MixedParams* mp, MixedMode* mode,
-                                hygt::BatchTune* tunes = nullptr) {
+                                ClassLaunch* runs = nullptr) {
   if (!cls || nclasses < 1 || nclasses > hygt::kMaxMixedClasses) return HYGT_ERR_ARG;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return HYGT_ERR_CUDA;
@@ -685,14 +735,18 @@ static hygt_status mixed_params(const hygt_mixed_class* cls, int nclasses, bool 
       if (!in || !out || !aligned16(in) || !aligned16(out) || !k.d_work || !aligned16(k.d_work))
         return HYGT_ERR_ARG;
       const int group = hygt::batch_group(plan->log2n);
-      if (k.work_bytes < hygt::batch_layout(plan->num_sets, k.nblocks, group).total)
+      if (k.work_bytes < hygt_batch_workspace_bytes(plan, k.nblocks))
         return HYGT_ERR_ARG;
     }
     mp->cls[slot] = make_batch_params(plan, k.d_work, in, out, k.nblocks, d_status);
     mp->present[slot] = k.nblocks > 0 ? 1 : 0;
     const hygt::BatchTune& tune = plan->tune[inverse ? 1 : 0];
     mp->variant[slot] = hygt::mixed_variant_of(plan->log2n, tune.stage, tune.layout);
-    if (tunes) tunes[slot] = tune;
+    if (runs) {
+      runs[slot].tune = tune;
+      runs[slot].tail = plan->tail[inverse ? 1 : 0];
+      runs[slot].counters = k.nblocks > 0 ? tail_counters(plan, k.d_work, k.nblocks) : nullptr;
+    }
     slot_ctas[slot] = k.ctas;
     if (k.ctas <= 0) explicit_split = false;
     if (k.ctas != -1) separate = false;
@@ -718,12 +772,13 @@ static hygt_status mixed_params(const hygt_mixed_class* cls, int nclasses, bool 
 // One direction of a mixed batch: the mixed kernel, or (separate mode) the
 // batch kernel of each class in turn.
 static cudaError_t mixed_launch(const hygt::MixedParams& mp, MixedMode mode, bool inverse,
-                                cudaStream_t stream, const hygt::BatchTune* tunes) {
+                                cudaStream_t stream, const ClassLaunch* runs) {
   if (mode != kMixedSeparate) return hygt::launch_mixed(inverse ? 1 : 0, mp, stream);
   for (int k = 0; k < hygt::kMaxMixedClasses; ++k) {
     if (!mp.present[k]) continue;
     const int log2n = hygt::mixed_slot_log2n(k);
-    const cudaError_t e = launch_batch_tuned(inverse, log2n, mp.cls[k], stream, tunes[k]);
+    const cudaError_t e = launch_batch_tuned(inverse, log2n, mp.cls[k], stream, runs[k].tune,
+                                             runs[k].tail, runs[k].counters);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -733,10 +788,12 @@ static hygt_status mixed_call(const hygt_mixed_class* cls, int nclasses, hygt_st
                               int* d_status, bool inverse) {
   hygt::MixedParams mp;
   MixedMode mode;
-  hygt::BatchTune tunes[hygt::kMaxMixedClasses];
-  hygt_status s = mixed_params(cls, nclasses, inverse, d_status, &mp, &mode, tunes);
+  ClassLaunch runs[hygt::kMaxMixedClasses];
+  hygt_status s = mixed_params(cls, nclasses, inverse, d_status, &mp, &mode, runs);
   if (s != HYGT_OK) return s;
-  return to_status(mixed_launch(mp, mode, inverse, (cudaStream_t)stream, tunes));
+  const cudaError_t e = mixed_launch(mp, mode, inverse, (cudaStream_t)stream, runs);
+  if (e == cudaErrorInvalidConfiguration) return HYGT_ERR_UNSUPPORTED;
+  return to_status(e);
 }
 
 hygt_status hygt_forward_mixed(const hygt_mixed_class* classes, int nclasses, hygt_stream stream,
@@ -787,8 +844,8 @@ static cudaError_t capture_schedules(const hygt_mixed_class* classes, int nclass
     cudaStream_t s = br.stream[nb];
     e = cudaStreamWaitEvent(s, br.fork, 0);
     if (e == cudaSuccess)
-      e = hygt::batch_build(k.d_set, k.nblocks, k.plan->num_sets,
-                            hygt::batch_group(k.plan->log2n), k.d_work, s);
+      e = build_schedule(k.d_set, k.nblocks, k.plan->num_sets,
+                         hygt::batch_group(k.plan->log2n), k.d_work, s);
     if (e == cudaSuccess) e = cudaEventRecord(br.join[nb], s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, br.join[nb], 0);
     ++nb;
@@ -802,7 +859,7 @@ hygt_status hygt_mixed_graph_create(hygt_graph* out, const hygt_mixed_class* cla
   *out = nullptr;
   hygt::MixedParams fwd, inv;
   MixedMode mode;
-  hygt::BatchTune tf[hygt::kMaxMixedClasses], ti[hygt::kMaxMixedClasses];
+  ClassLaunch tf[hygt::kMaxMixedClasses], ti[hygt::kMaxMixedClasses];
   hygt_status s = mixed_params(classes, nclasses, false, d_status, &fwd, &mode, tf);
   if (s == HYGT_OK) s = mixed_params(classes, nclasses, true, d_status, &inv, &mode, ti);
   if (s != HYGT_OK) return s;
@@ -1304,8 +1361,7 @@ extern "C" hygt_status hygt_forward_static(hygt_plan plan, const int16_t* d_x, i
   if (plan->is_float) return HYGT_ERR_UNSUPPORTED;
   if (nblocks > kBatchMaxBlocks) return HYGT_ERR_TOO_LARGE;
   const int group = hygt::batch_group(plan->log2n);
-  if (hygt::batch_layout(plan->num_sets, nblocks, group).total > kStaticScratchBytes)
-    return HYGT_ERR_TOO_LARGE;
+  if (hygt_batch_workspace_bytes(plan, nblocks) > kStaticScratchBytes) return HYGT_ERR_TOO_LARGE;
   void* work = nullptr;
   s = static_scratch(&work);
   if (s != HYGT_OK) return s;

@@ -125,6 +125,10 @@ def _load() -> ctypes.CDLL:
     L.hygt_batch_set_tuning.restype = i32
     L.hygt_batch_get_tuning.argtypes = [P, i32] + [ctypes.POINTER(i32)] * 5
     L.hygt_batch_get_tuning.restype = i32
+    L.hygt_batch_set_tail.argtypes = [P, i32, i32]
+    L.hygt_batch_set_tail.restype = i32
+    L.hygt_batch_get_tail.argtypes = [P, i32, ctypes.POINTER(i32)]
+    L.hygt_batch_get_tail.restype = i32
     L.hygt_mixed_ctas.argtypes = []
     L.hygt_mixed_ctas.restype = i32
     L.hygt_mixed_class_variant.argtypes = [P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
@@ -376,6 +380,16 @@ def hygt_batch_get_tuning(plan, inverse):
     _check(_lib.hygt_batch_get_tuning(plan, int(inverse), *[ctypes.byref(v) for v in vals]),
            "hygt_batch_get_tuning")
     return tuple(v.value for v in vals)
+
+
+def hygt_batch_set_tail(plan, inverse, tail_64ths):
+    return int(_lib.hygt_batch_set_tail(plan, int(inverse), int(tail_64ths)))
+
+
+def hygt_batch_get_tail(plan, inverse):
+    v = ctypes.c_int()
+    _check(_lib.hygt_batch_get_tail(plan, int(inverse), ctypes.byref(v)), "hygt_batch_get_tail")
+    return v.value
 
 
 def hygt_mixed_ctas():

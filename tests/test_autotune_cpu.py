@@ -128,8 +128,17 @@ def test_batch_tuner_picks_the_modelled_best(at, monkeypatch):
     def fake_get(plan, inv):
         return state.get(inv, (0, 0, -1, 0)) + (12,)
 
+    tails = {}
+
+    def fake_set_tail(plan, inv, t):
+        if t > 0 and state[inv][2] == 1:  # pretend cp.async points have no dynamic tail
+            return hygt.HYGT_ERR_UNSUPPORTED
+        tails[inv] = t
+        return hygt.HYGT_OK
+
     monkeypatch.setattr(hygt, "hygt_batch_set_tuning", fake_set)
     monkeypatch.setattr(hygt, "hygt_batch_get_tuning", fake_get)
+    monkeypatch.setattr(hygt, "hygt_batch_set_tail", fake_set_tail)
 
     class _P:
         handle, N, rounds, num_sets, log2n = 1, 64, 2, 105, 6
@@ -137,16 +146,23 @@ def test_batch_tuner_picks_the_modelled_best(at, monkeypatch):
     class _B:
         plan, nblocks = _P(), 1000
 
-    def model(direction, cand):
-        w, c, s, lay = cand
+    def model(direction, point):
+        w, c, s, lay = point[:4]
         base = 1.0 + abs(w - 9) * 0.1 + (0.05 if c == 0 else 0.0)
         base -= 0.3 if lay == 1 and direction == "inverse" else 0.0
-        return base - (0.2 if s == 1 and direction == "forward" else 0.0)
+        base -= 0.2 if s == 1 and direction == "forward" else 0.0
+        if len(point) > 4:  # a dynamic tail: 8/64 pays 5%, the others nothing
+            base *= 0.95 if point[4] == 8 else 1.0
+        return base
 
     res = at.tune_batch(_B(), None, None, None, use_cache=False, time_fn=model)
     assert res["forward"][:4] == (9, 1, 1, 0)
     assert res["inverse"][:4] == (9, 1, 0, 1)   # layout 1, first of the equal stages
     assert state[0] == (9, 1, 1, 0) and state[1] == (9, 1, 0, 1)
+    # the forward's point has no tail; the inverse keeps the one that pays
+    assert res["forward"][5] == 0 and tails[0] == 0
+    assert res["inverse"][5] == 8 and tails[1] == 8
+    assert abs(res["inverse"][4] - 0.95 * model("inverse", (9, 1, 0, 1))) < 1e-12
 
 
 def test_batch_candidates_offer_the_interleaved_order_for_4x4_only(at):

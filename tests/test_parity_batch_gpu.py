@@ -355,3 +355,60 @@ def test_batch_interleaved_order_bit_exact(gpu, orc, perm_kind, layout):
     p6 = gpu.Plan(6, 2, inputs.angle_indices(3, 2, 6, seed=1))
     assert gpu.hygt_batch_set_tuning(p6.handle, 0, 0, 0, 4, 0) == gpu.HYGT_ERR_UNSUPPORTED
     p6.close()
+
+
+DYN_POINTS = {6: [(lay, st) for lay in (0, 3) for st in ((0, 1, 2, 3) if lay == 0 else (0, 1, 2))],
+              8: [(lay, st) for lay in (0, 4, 5) for st in ((0, 1, 2, 3) if lay == 0 else (0, 1, 2))]}
+
+
+@pytest.mark.parametrize("log2n,R,S,B", [(6, 2, 105, 20011), (8, 3, 16, 3001)])
+def test_batch_dynamic_tail_bit_exact(gpu, orc, log2n, R, S, B):
+    """The kernels with a dynamic tail (the last t/64 of the sorted order
+    handed out through an atomic counter): the oracle's integers, forward and
+    inverse, at every layout and stage they take, with a quarter-size and a
+    half-size tail, a bad set index, calls repeated without a rebuild (the
+    counter must come back to zero), and a batch of five blocks."""
+    import torch
+    N = 1 << log2n
+    q = inputs.angle_indices(S, R, log2n, seed=91)
+    perms = inputs.permutations(S, R, N, seed=92)
+    plan = gpu.Plan(log2n, R, q, perms)
+    for nb in (B, 5):
+        x = inputs.laplacian_blocks(nb, N, 30.0, -32768, 32767, seed=93 + nb)
+        sets = inputs.set_indices(nb, S, seed=94, skip_frac=0.1)
+        if nb > 100:
+            sets[17] = 999
+        ye, s1 = orc.fwd_int(x, q, log2n, R, perms, sets)
+        xe, _ = orc.inv_int(ye, q, log2n, R, perms, sets)
+        want = gpu.HYGT_ERR_SET_INDEX if s1 else 0
+        b = gpu.Batch(plan, nb).build(_t(sets))
+        dx, dy = _t(x), _t(ye)
+        for lay, st in DYN_POINTS[log2n]:
+            for tail in (16, 32):
+                for inv in (0, 1):
+                    assert gpu.hygt_batch_set_tail(plan.handle, inv, 0) == 0
+                    assert gpu.hygt_batch_set_tuning(plan.handle, inv, 0, 0, st, lay) == 0
+                    assert gpu.hygt_batch_set_tail(plan.handle, inv, tail) == 0
+                    assert gpu.hygt_batch_get_tail(plan.handle, inv) == tail
+                for rep in range(2):  # the second pass runs on the counters the first reset
+                    st_ = torch.zeros(1, dtype=torch.int32, device="cuda")
+                    y = b.forward(dx, status=st_)
+                    xr = b.inverse(dy, status=st_)
+                    torch.cuda.synchronize()
+                    assert int(st_.item()) == want, (nb, lay, st, tail)
+                    assert np.array_equal(y.cpu().numpy(), ye), (nb, lay, st, tail, rep)
+                    assert np.array_equal(xr.cpu().numpy(), xe), (nb, lay, st, tail, rep)
+    for inv in (0, 1):
+        assert gpu.hygt_batch_set_tail(plan.handle, inv, 0) == 0
+    # a tail is refused where no such kernel exists, and so is a tuning that
+    # would leave a set tail without one
+    assert gpu.hygt_batch_set_tail(plan.handle, 0, 33) == gpu.HYGT_ERR_ARG
+    assert gpu.hygt_batch_set_tuning(plan.handle, 0, 0, 0, 0, 2) == 0
+    assert gpu.hygt_batch_set_tail(plan.handle, 0, 8) == gpu.HYGT_ERR_UNSUPPORTED
+    assert gpu.hygt_batch_set_tuning(plan.handle, 0, 0, 0, 0, 0) == 0
+    assert gpu.hygt_batch_set_tail(plan.handle, 0, 8) == 0
+    assert gpu.hygt_batch_set_tuning(plan.handle, 0, 0, 0, 0, 2) == gpu.HYGT_ERR_UNSUPPORTED
+    plan.close()
+    p4 = gpu.Plan(4, 2, inputs.angle_indices(3, 2, 4, seed=1))
+    assert gpu.hygt_batch_set_tail(p4.handle, 0, 8) == gpu.HYGT_ERR_UNSUPPORTED
+    p4.close()

@@ -240,3 +240,31 @@ def test_mixed_layout_variant_mapping(gpu):
     with pytest.raises(RuntimeError):
         gpu.hygt_mixed_class_variant(plan.handle, 0)
     plan.close()
+
+
+def test_mixed_separate_launches_with_dynamic_tails(gpu, orc):
+    """Per-class launches with dynamic tails on the 8x8 and 16x16 classes
+    (and the 4x4 class in the set-interleaved order), graph-replayed twice:
+    every block bit-exact."""
+    import torch
+    from paper_2505_21728_gb300 import workloads
+    w = workloads.get_mixed("mixed_frame_2160p16", scale_down=40)
+    mb, datas = make_mixed(gpu, w)
+    for e in mb.entries:
+        plan = e["plan"]
+        for inv in (0, 1):
+            if plan.log2n == 4:
+                assert gpu.hygt_batch_set_tuning(plan.handle, inv, 4, 0, 4, 2) == 0
+            else:
+                lay = 3 if plan.log2n == 6 else 5
+                assert gpu.hygt_batch_set_tuning(plan.handle, inv, 0, 0, 0, lay) == 0
+                assert gpu.hygt_batch_set_tail(plan.handle, inv, 16) == 0
+    mb.set_split([-1, -1, -1])
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    g = mb.graph(status=st)
+    g.launch()
+    g.launch()
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    check_against_oracle(orc, mb, datas)
+    g.close()
