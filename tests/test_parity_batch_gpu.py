@@ -266,8 +266,9 @@ def test_tune_batch_sets_a_fitting_point(gpu, tmp_path, monkeypatch):
     xr = torch.empty_like(x)
     res = autotune.tune_batch(b, x, y, xr, reps=2)
     for inv, d in ((0, "forward"), (1, "inverse")):
-        w, c, s, lay, ms = res[d]
+        w, c, s, lay, ms, tail = res[d]
         assert gpu.hygt_batch_get_tuning(plan.handle, inv)[:4] == (w, c, s, lay)
+        assert gpu.hygt_batch_get_tail(plan.handle, inv) == tail
         assert ms > 0
     again = autotune.tune_batch(b, x, y, xr, reps=2)  # from the cache
     assert again == {k: tuple(v) for k, v in res.items()}
