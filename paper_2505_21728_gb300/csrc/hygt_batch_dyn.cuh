@@ -6,8 +6,9 @@
 // parts they land on) finish late, and in a short launch -- about a dozen
 // tasks per warp -- a quarter of the warps' time goes to the launch's ramp,
 // its tail and that imbalance.  Here the first (64 - tail) / 64 of the
-// order is split the same way (each CTA caching the tables of the sets its
-// range spans), and the last tail / 64 is handed out one task at a time by
+// order is split into contiguous warp ranges that differ by at most one
+// task (each CTA caching the tables of the sets its range spans), and the
+// last tail / 64 is handed out one task at a time by
 // an atomic counter to the warps that finish their range, so the SMs that
 // are done early take the rest.  The tail of the sorted order is the last
 // sets, the skip bucket and the bad-set bucket; its tasks read their tables
@@ -50,16 +51,18 @@ __global__ void __launch_bounds__(batch_threads(LOG2N, KIND, LAY), 1)
   const long long nstatic = ntasks - ntail;
   const long long cta = blockIdx.x, ncta = gridDim.x;
 
-  // the static part, as the batch kernel over [0, nstatic)
+  // the static part over [0, nstatic): warp gw takes tasks
+  // [gw nstatic / W, (gw + 1) nstatic / W), so that shares differ by at most
+  // one task (whole chunks of ceil(nstatic / W) would leave the last CTAs
+  // short or empty), and each CTA caches the sets of its warps' ranges
   const int wpc = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5;
   const long long warps_total = ncta * wpc;
-  const long long chunk = (nstatic + warps_total - 1) / warps_total;
   const long long gw = cta * wpc + warp;
-  const long long t0 = min(nstatic, gw * chunk);
-  const long long t1 = min(nstatic, t0 + chunk);
-  const long long c0 = min(nstatic, cta * wpc * chunk);
-  const long long c1 = min(nstatic, c0 + (long long)wpc * chunk);
+  const long long t0 = gw * nstatic / warps_total;
+  const long long t1 = (gw + 1) * nstatic / warps_total;
+  const long long c0 = cta * wpc * nstatic / warps_total;
+  const long long c1 = (cta + 1) * wpc * nstatic / warps_total;
   int set_lo = 0, ncache = 0;
   if (c1 > c0) {
     const int bk_lo = bucket_of_slot(p.starts, p.num_sets, (int)(c0 * G));
