@@ -8,9 +8,9 @@
 // its tail and that imbalance.  Here the first (64 - tail) / 64 of the
 // order is split into contiguous warp ranges that differ by at most one
 // task (each CTA caching the tables of the sets its range spans), and the
-// last tail / 64 is handed out one task at a time by
-// an atomic counter to the warps that finish their range, so the SMs that
-// are done early take the rest.  The tail of the sorted order is the last
+// last tail / 64 is handed out one task at a time by an atomic counter to
+// the warps that finish their range, so the SMs that are done early take
+// the rest.  The tail of the sorted order is the last
 // sets, the skip bucket and the bad-set bucket; its tasks read their tables
 // from global memory and run without a stage.  The counter sits in the 16
 // bytes after the schedule (BatchLayout::total), which the schedule build
@@ -29,7 +29,7 @@ namespace hygt {
 // count of warps that are done (32-bit).
 constexpr size_t kDynCounterBytes = 16;
 
-// dyn_*.cu: block sizes, layouts and stages with a dynamic tail, and the
+// dyn.cu: block sizes, layouts and stages with a dynamic tail, and the
 // launcher (kind 0 forward, 1 inverse; tail_64ths 1 .. 32).
 bool batch_dyn_ok(int log2n, int layout, int stage);
 cudaError_t launch_batch_dyn(int kind, int log2n, const BatchParams& p, void* counters,
